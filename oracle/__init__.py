@@ -1,0 +1,188 @@
+"""FP64 CPU oracle for the electromagnetic PIC hot path (numpy front end).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the plain, slow definition the CUDA
+library is checked against.  Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import it; the product package never does,
+and the two share no code.
+
+Every function forwards to the C implementation in pic_oracle.c, which cites
+the method each one restates.  Arrays are numpy float64, C-contiguous.
+Fields are held as one array of shape (9, nx, ny, nz):
+Ex, Ey, Ez, Bx, By, Bz, Jx, Jy, Jz (k fastest).
+"""
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_libs = {}
+
+_dp = ct.POINTER(ct.c_double)
+
+
+class _Grid(ct.Structure):
+    _fields_ = [("n", ct.c_int64 * 3), ("d", ct.c_double * 3)]
+
+
+def _declare(lib):
+    P = ct.c_void_p
+    D = ct.c_double
+    I = ct.c_int
+    L = ct.c_int64
+    G = ct.POINTER(_Grid)
+    sig = {
+        "orc_shape": (D, [I, D]),
+        "orc_gather_many": (None, [G, I, P, L, P, P, P, P]),
+        "orc_boris_many": (None, [D, D, D, L, P, P, P, P]),
+        "orc_deposit_many": (None, [G, I, D, D, L, P, P, P, P, P, P, P, P]),
+        "orc_rho_many": (None, [G, I, D, L, P, P, P, P, P]),
+        "orc_yee_b": (None, [G, D, P, P]),
+        "orc_yee_e": (None, [G, D, P, P, P]),
+        "orc_yee_step": (None, [G, D, P, P, P]),
+        "orc_pic_step": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D]),
+        "orc_div_edge": (None, [G, P, P]),
+        "orc_div_face": (None, [G, P, P]),
+        "orc_field_energy": (D, [G, P]),
+        "orc_kinetic_energy": (D, [D, L, P, P, P, P]),
+        "orc_wrap": (D, [D, D]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+def load(mutant: int = 0):
+    """The oracle library (the default build, or a planted-mistake build)."""
+    with _lock:
+        if mutant not in _libs:
+            path = _build.build(mutant)
+            _libs[mutant] = _declare(ct.CDLL(os.path.abspath(path)))
+        return _libs[mutant]
+
+
+class Oracle:
+    """Thin numpy wrapper over one oracle build."""
+
+    def __init__(self, mutant: int = 0):
+        self.lib = load(mutant)
+
+    # -- helpers -----------------------------------------------------
+    @staticmethod
+    def grid(n, d=(1.0, 1.0, 1.0)):
+        g = _Grid()
+        for a in range(3):
+            g.n[a] = int(n[a])
+            g.d[a] = float(d[a])
+        return g
+
+    @staticmethod
+    def _f64(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a
+
+    @staticmethod
+    def _ptr(a):
+        return a.ctypes.data_as(ct.c_void_p)
+
+    def _ptr_array(self, arrays):
+        arr = (ct.c_void_p * len(arrays))(*[a.ctypes.data for a in arrays])
+        return arr
+
+    # -- method steps ------------------------------------------------
+    def shape(self, p, xi):
+        xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+        f = self.lib.orc_shape
+        return np.array([f(int(p), float(v)) for v in xi.ravel()]).reshape(xi.shape)
+
+    def gather(self, g, p, fields, x, y, z):
+        """E,B at the particle positions; returns (np, 6)."""
+        F = [self._f64(fields[c]) for c in range(6)]
+        x, y, z = self._f64(x), self._f64(y), self._f64(z)
+        out = np.zeros((x.size, 6))
+        self.lib.orc_gather_many(ct.byref(g), int(p), self._ptr_array(F), x.size,
+                                 self._ptr(x), self._ptr(y), self._ptr(z), self._ptr(out))
+        return out
+
+    def boris(self, q, m, dt, EB, ux, uy, uz):
+        """Returns the pushed (ux, uy, uz)."""
+        EB = self._f64(EB)
+        ux, uy, uz = (self._f64(a).copy() for a in (ux, uy, uz))
+        self.lib.orc_boris_many(float(q), float(m), float(dt), ux.size, self._ptr(EB),
+                                self._ptr(ux), self._ptr(uy), self._ptr(uz))
+        return ux, uy, uz
+
+    def deposit(self, g, p, dt, q, x0, y0, z0, x1, y1, z1, w, J=None):
+        """Esirkepov current of all particles; returns J of shape (3, nx, ny, nz)."""
+        n = tuple(g.n)
+        if J is None:
+            J = np.zeros((3,) + n)
+        arrs = [self._f64(a) for a in (x0, y0, z0, x1, y1, z1, w)]
+        Jl = [J[c] for c in range(3)]
+        self.lib.orc_deposit_many(ct.byref(g), int(p), float(dt), float(q), arrs[0].size,
+                                  *[self._ptr(a) for a in arrs], self._ptr_array(Jl))
+        return J
+
+    def rho(self, g, p, q, x, y, z, w):
+        n = tuple(g.n)
+        out = np.zeros(n)
+        arrs = [self._f64(a) for a in (x, y, z, w)]
+        self.lib.orc_rho_many(ct.byref(g), int(p), float(q), arrs[0].size,
+                              *[self._ptr(a) for a in arrs], self._ptr(out))
+        return out
+
+    def yee_b(self, g, h, E, B):
+        self.lib.orc_yee_b(ct.byref(g), float(h), self._ptr_array([E[0], E[1], E[2]]),
+                           self._ptr_array([B[0], B[1], B[2]]))
+
+    def yee_e(self, g, dt, E, B, J):
+        self.lib.orc_yee_e(ct.byref(g), float(dt), self._ptr_array([E[0], E[1], E[2]]),
+                           self._ptr_array([B[0], B[1], B[2]]), self._ptr_array([J[0], J[1], J[2]]))
+
+    def yee_step(self, g, dt, fields):
+        """In place on fields (9, nx, ny, nz)."""
+        self.lib.orc_yee_step(ct.byref(g), float(dt),
+                              self._ptr_array([fields[0], fields[1], fields[2]]),
+                              self._ptr_array([fields[3], fields[4], fields[5]]),
+                              self._ptr_array([fields[6], fields[7], fields[8]]))
+
+    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0):
+        """One PIC step, in place on parts (dict of x,y,z,ux,uy,uz,w float64
+        arrays) and fields (9, nx, ny, nz)."""
+        keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+        for k in keys:
+            assert parts[k].dtype == np.float64 and parts[k].flags.c_contiguous
+        assert fields.dtype == np.float64 and fields.flags.c_contiguous
+        self.lib.orc_pic_step(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
+                              *[self._ptr(parts[k]) for k in keys],
+                              self._ptr_array([fields[c] for c in range(9)]),
+                              float(drive_amp), float(drive_k), float(t))
+
+    # -- diagnostics -------------------------------------------------
+    def div_edge(self, g, F3):
+        out = np.zeros(tuple(g.n))
+        F3 = [self._f64(F3[c]) for c in range(3)]
+        self.lib.orc_div_edge(ct.byref(g), self._ptr_array(F3), self._ptr(out))
+        return out
+
+    def div_face(self, g, F3):
+        out = np.zeros(tuple(g.n))
+        F3 = [self._f64(F3[c]) for c in range(3)]
+        self.lib.orc_div_face(ct.byref(g), self._ptr_array(F3), self._ptr(out))
+        return out
+
+    def field_energy(self, g, fields):
+        F = [self._f64(fields[c]) for c in range(6)]
+        return self.lib.orc_field_energy(ct.byref(g), self._ptr_array(F))
+
+    def kinetic_energy(self, m, ux, uy, uz, w):
+        arrs = [self._f64(a) for a in (ux, uy, uz, w)]
+        return self.lib.orc_kinetic_energy(float(m), arrs[0].size, *[self._ptr(a) for a in arrs])
+
+    def wrap(self, x, L):
+        return self.lib.orc_wrap(float(x), float(L))

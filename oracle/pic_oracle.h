@@ -1,0 +1,34 @@
+/*
+ * FP64 CPU oracle for the electromagnetic PIC hot path: declarations.
+ * TEST INFRASTRUCTURE ONLY (see pic_oracle.c).  Internal to oracle/; the
+ * CUDA library has its own, unrelated header.
+ */
+#ifndef PIC_ORACLE_H
+#define PIC_ORACLE_H
+#include <stdint.h>
+
+typedef struct {
+    int64_t n[3]; /* cells per axis */
+    double d[3];  /* cell size per axis */
+} orc_grid;
+
+double orc_shape(int p, double xi);
+void orc_gather(const orc_grid* g, int p, const double* const F[6], double x, double y, double z, double EB[6]);
+void orc_boris(double q, double m, double dt, const double E[3], const double B[3], double u[3]);
+void orc_advance(double dt, const double u[3], double x[3]);
+double orc_wrap(double x, double L);
+void orc_deposit_esirkepov(const orc_grid* g, int p, double dt, double qw, const double x0[3], const double x1[3],
+                           double* const J[3]);
+void orc_deposit_rho(const orc_grid* g, int p, double qw, const double x[3], double* rho);
+void orc_yee_b(const orc_grid* g, double h, const double* const E[3], double* const B[3]);
+void orc_yee_e(const orc_grid* g, double dt, double* const E[3], const double* const B[3], const double* const J[3]);
+void orc_yee_step(const orc_grid* g, double dt, double* const E[3], double* const B[3], const double* const J[3]);
+void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                  double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                  double drive_amp, double drive_k, double t);
+void orc_div_edge(const orc_grid* g, const double* const F[3], double* out);
+void orc_div_face(const orc_grid* g, const double* const F[3], double* out);
+double orc_field_energy(const orc_grid* g, const double* const F[6]);
+double orc_kinetic_energy(double m, int64_t np, const double* ux, const double* uy, const double* uz,
+                          const double* w);
+#endif

@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle's tests.
+
+This module holds none of the PIC method's arithmetic: it draws counter-based
+random numbers (SplitMix64, see picgen.c) and places particles by the
+uniform-plasma recipe.  Both the CUDA library and the CPU oracle receive the
+arrays it produces, so neither side has to reproduce the other's random
+numbers.
+
+Workload recipes (synthetic stand-ins shaped like the paper's uniform-plasma
+scaling runs of Sec. 4.1 and its 2-particle-per-cell wakefield stage of
+Sec. 4.2; normalised units, electrons q = -1, m = 1, cell size 1):
+
+  uniform_32    32^3, 2 ppc, order 1, u ~ N(0, 0.01) + 1e-3 sin(2 pi x / 32), n = 1, FP64, 50 steps
+  uniform_256   256^3, 8 ppc, order 3, u ~ N(0, 0.05), n = 1, 100 steps, FP64 and FP32-mixed
+  wakefield     128 x 128 x 1024, 2 ppc, order 2, moving window, laser a0 = 2
+  ensemble      96 boxes with edges in {16,24,32,48,64}, 1-8 ppc, n in [0.1, 10], order 1 or 3
+  adjoint_64    64^3, 4 ppc, order 2, external plane-wave drive, 200 steps
+"""
+import ctypes as ct
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(HERE, "_build")
+_SRC = os.path.join(HERE, "picgen.c")
+_lock = threading.Lock()
+_lib = None
+
+# Workload recipes.  `cfl` fixes dt = cfl / sqrt(sum 1/d^2).
+WORKLOADS = {
+    "uniform_32": dict(n=(32, 32, 32), ppc=2, order=1, sigma_u=0.01, density=1.0,
+                       pert_amp=1e-3, pert_k=2 * np.pi / 32, cfl=0.99, steps=50, seed=0),
+    "uniform_256": dict(n=(256, 256, 256), ppc=8, order=3, sigma_u=0.05, density=1.0,
+                        pert_amp=0.0, pert_k=0.0, cfl=0.99, steps=100, seed=1),
+    "adjoint_64": dict(n=(64, 64, 64), ppc=4, order=2, sigma_u=0.05, density=1.0,
+                       pert_amp=0.0, pert_k=0.0, cfl=0.99, steps=200, seed=4),
+}
+
+
+def build(force: bool = False) -> str:
+    out = os.path.join(_BUILD, "libpicgen.so")
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+        return out
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.run(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+                    _SRC, "-o", tmp, "-lm"], check=True)
+    os.replace(tmp, out)
+    return out
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ct.CDLL(build())
+            P, L, D, I, U = ct.c_void_p, ct.c_int64, ct.c_double, ct.c_int, ct.c_uint64
+            lib.pg_uniform.argtypes = [U, L, L, I, P]
+            lib.pg_normal.argtypes = [U, L, L, I, P]
+            lib.pg_uniform_plasma.argtypes = [U, L, L, L, L, D, D, D, D, D, D, D, L, L,
+                                              P, P, P, P, P, P, P]
+            for f in (lib.pg_uniform, lib.pg_normal, lib.pg_uniform_plasma):
+                f.restype = None
+            _lib = lib
+        return _lib
+
+
+def uniform(seed: int, i0: int, n: int, draw: int) -> np.ndarray:
+    """U[0,1) draws for counters [i0, i0+n) at one draw index."""
+    out = np.empty(n)
+    _load().pg_uniform(seed, i0, n, draw, out.ctypes.data_as(ct.c_void_p))
+    return out
+
+
+def normal(seed: int, i0: int, n: int, draw: int) -> np.ndarray:
+    out = np.empty(n)
+    _load().pg_normal(seed, i0, n, draw, out.ctypes.data_as(ct.c_void_p))
+    return out
+
+
+def dt_from_cfl(d, cfl: float) -> float:
+    """dt = cfl * (sum 1/d^2)^(-1/2): the Courant number of the Yee scheme."""
+    return float(cfl) / float(np.sqrt(sum(1.0 / (float(a) ** 2) for a in d)))
+
+
+def uniform_plasma(seed, n, ppc, d=(1.0, 1.0, 1.0), sigma_u=0.0, density=1.0,
+                   pert_amp=0.0, pert_k=0.0, cells=None, out=None):
+    """Uniform plasma particles (dict of float64 arrays x,y,z,ux,uy,uz,w).
+
+    `cells` = (c0, c1) restricts generation to a range of linear cell ids
+    (the same particles a full generation would produce there).  `out` may
+    give preallocated arrays (e.g. pinned host memory) to fill."""
+    nx, ny, nz = (int(a) for a in n)
+    c0, c1 = (0, nx * ny * nz) if cells is None else (int(cells[0]), int(cells[1]))
+    npart = (c1 - c0) * int(ppc)
+    weight = float(density) * d[0] * d[1] * d[2] / int(ppc)
+    keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+    if out is None:
+        out = {k: np.empty(npart) for k in keys}
+    ptrs = []
+    for k in keys:
+        a = out[k]
+        assert a.dtype == np.float64 and a.flags.c_contiguous and a.size >= npart
+        ptrs.append(a.ctypes.data_as(ct.c_void_p))
+    _load().pg_uniform_plasma(int(seed), nx, ny, nz, int(ppc), float(d[0]), float(d[1]), float(d[2]),
+                              float(sigma_u), weight, float(pert_amp), float(pert_k), c0, c1, *ptrs)
+    return out
+
+
+def workload_particles(name: str, cells=None, out=None):
+    w = WORKLOADS[name]
+    return uniform_plasma(w["seed"], w["n"], w["ppc"], sigma_u=w["sigma_u"], density=w["density"],
+                          pert_amp=w["pert_amp"], pert_k=w["pert_k"], cells=cells, out=out)
+
+
+def random_fields(seed: int, n, scale: float = 1.0) -> np.ndarray:
+    """Nine seeded uniform(-scale, scale) field arrays (Ex..Bz, Jx..Jz)."""
+    C = int(n[0]) * int(n[1]) * int(n[2])
+    f = np.empty((9, C))
+    for c in range(9):
+        f[c] = uniform(seed, c * C, C, 9)
+    return ((2.0 * f - 1.0) * scale).reshape((9,) + tuple(int(a) for a in n))

@@ -1,0 +1,431 @@
+"""Pins for the FP64 CPU oracle: checks against what the mathematics fixes.
+
+Every pin is a function of an `oracle.Oracle` instance that raises
+AssertionError when the oracle disagrees with an independent statement of the
+method: closed forms, invariants, a library routine, or brute force.  The
+plain test module runs them on the default oracle; the mutation test runs them
+on oracle builds with one planted mistake each and expects at least one pin to
+fail for every such build.
+
+Methods pinned (the paper names them; the formulas are the textbook ones):
+order-p B-spline shapes (Sec. 4.1.1 uses 3rd order), momentum-conserving
+gather on the Yee lattice (Sec. 2.4), relativistic Boris push, Esirkepov
+current deposition (Sec. 3.4.1), Yee FDTD (Sec. 2.4, Sec. 4.1.1).
+"""
+import numpy as np
+from scipy.interpolate import BSpline
+
+from paper_2101_12149_gb300 import inputs
+
+STAG = np.array([[0.5, 0, 0], [0, 0.5, 0], [0, 0, 0.5], [0, 0.5, 0.5], [0.5, 0, 0.5], [0.5, 0.5, 0]])
+
+
+def bspline(p):
+    """Centred cardinal B-spline of degree p from scipy (zero outside its support)."""
+    knots = np.arange(p + 2, dtype=np.float64) - 0.5 * (p + 1)
+    b = BSpline.basis_element(knots, extrapolate=False)
+
+    def f(x):
+        v = b(np.asarray(x, dtype=np.float64))
+        return np.nan_to_num(v, nan=0.0)
+    return f
+
+
+def _rand(seed, n, lo, hi, draw=0):
+    return lo + (hi - lo) * inputs.uniform(seed, 0, n, draw)
+
+
+# --------------------------------------------------------------------- shapes
+
+def pin_shape_library(O):
+    """The oracle's s_p equals scipy's cardinal B-spline basis element."""
+    xs = _rand(11, 4000, -2.6, 2.6)
+    for p in (1, 2, 3):
+        ref = bspline(p)(xs)
+        got = O.shape(p, xs)
+        assert np.max(np.abs(got - ref)) < 1e-15, f"shape p={p} differs from scipy B-spline"
+
+
+def pin_shape_moments(O):
+    """Partition of unity, linear reproduction, and the second moment
+    sum_i i^2 s_p(x-i) = x^2 + (p+1)/12 for p >= 2 (variance of p+1 unit boxes)."""
+    xs = _rand(12, 3000, -9.0, 9.0)
+    for p in (1, 2, 3):
+        for x in xs[:1000] if p == 1 else xs:
+            i = np.arange(int(np.floor(x)) - 3, int(np.floor(x)) + 5)
+            s = O.shape(p, x - i)
+            assert abs(s.sum() - 1.0) < 1e-15, f"partition of unity p={p} x={x}"
+            assert abs((i * s).sum() - x) < 1e-13, f"linear reproduction p={p} x={x}"
+            if p >= 2:
+                assert abs((i * i * s).sum() - (x * x + (p + 1) / 12.0)) < 1e-12, f"second moment p={p}"
+
+
+def pin_shape_convolution(O):
+    """s_p(x) = integral of s_{p-1} over [x-1/2, x+1/2], with s_0 the unit box
+    (so s_1 is checked against the analytic box integral)."""
+    gl_x, gl_w = np.polynomial.legendre.leggauss(6)
+    xs = _rand(13, 300, -2.4, 2.4)
+    for x in xs:
+        box = max(0.0, min(x + 0.5, 0.5) - max(x - 0.5, -0.5))
+        assert abs(O.shape(1, x)[0] - box) < 1e-15
+        for p in (2, 3):
+            lo, hi = x - 0.5, x + 0.5
+            cuts = np.unique(np.concatenate([[lo, hi], np.arange(-2.5, 2.6, 0.5)]))
+            cuts = cuts[(cuts >= lo) & (cuts <= hi)]
+            acc = 0.0
+            for a, b in zip(cuts[:-1], cuts[1:]):
+                t = 0.5 * (b - a) * gl_x + 0.5 * (a + b)
+                acc += 0.5 * (b - a) * np.dot(gl_w, O.shape(p - 1, t))
+            assert abs(O.shape(p, x)[0] - acc) < 1e-14, f"convolution identity p={p} x={x}"
+
+
+def pin_shape_values(O):
+    """Textbook node values: s1(0)=1; s2(0)=3/4, s2(1)=1/8; s3(0)=2/3, s3(1)=1/6; zero at +-(p+1)/2."""
+    assert O.shape(1, 0.0)[0] == 1.0
+    assert O.shape(2, 0.0)[0] == 0.75 and abs(O.shape(2, 1.0)[0] - 0.125) < 1e-16
+    assert abs(O.shape(3, 0.0)[0] - 2.0 / 3.0) < 1e-16 and abs(O.shape(3, -1.0)[0] - 1.0 / 6.0) < 1e-16
+    for p in (1, 2, 3):
+        assert O.shape(p, 0.5 * (p + 1))[0] == 0.0 and O.shape(p, -0.5 * (p + 1))[0] == 0.0
+
+
+# --------------------------------------------------------------------- gather
+
+def pin_gather_constant(O):
+    """Constant fields are reproduced exactly, including next to the periodic seam."""
+    n = (8, 6, 10)
+    g = O.grid(n, (1.0, 0.9, 1.1))
+    L = np.array(n) * np.array([1.0, 0.9, 1.1])
+    consts = np.array([0.3, -1.2, 2.5, 0.7, -0.4, 1.9])
+    F = np.stack([np.full(n, c) for c in consts])
+    m = 400
+    pos = [_rand(21, m, 0.0, L[a], draw=a) for a in range(3)]
+    pos[0][:20] = np.linspace(0.0, 0.49, 20)
+    pos[1][20:40] = L[1] - np.linspace(1e-9, 0.4, 20)
+    for p in (1, 2, 3):
+        EB = O.gather(g, p, F, *pos)
+        assert np.max(np.abs(EB - consts)) < 1e-14, f"constant field p={p}"
+
+
+def pin_gather_polynomial(O):
+    """A field linear along one axis in its own staggered coordinate is gathered
+    exactly; a quadratic one returns x^2 + (p+1)/12 for p >= 2.  Checks every
+    component's staggering along every axis."""
+    n = (16, 16, 16)
+    d = (1.0, 1.0, 1.0)
+    g = O.grid(n, d)
+    m = 60
+    pos = [_rand(22, m, 5.0, 11.0, draw=a) for a in range(3)]
+    idx = np.indices(n).astype(np.float64)
+    for c in range(6):
+        for a in range(3):
+            coord = idx[a] + STAG[c][a]
+            for p in (1, 2, 3):
+                F = np.zeros((6,) + n)
+                F[c] = 0.25 + 0.5 * coord
+                EB = O.gather(g, p, F, *pos)
+                assert np.max(np.abs(EB[:, c] - (0.25 + 0.5 * pos[a]))) < 1e-13, f"linear comp={c} axis={a} p={p}"
+                others = [o for o in range(6) if o != c]
+                assert np.max(np.abs(EB[:, others])) == 0.0
+                if p >= 2:
+                    F[c] = coord ** 2
+                    EB = O.gather(g, p, F, *pos)
+                    ref = pos[a] ** 2 + (p + 1) / 12.0
+                    assert np.max(np.abs(EB[:, c] - ref)) < 1e-12, f"quadratic comp={c} axis={a} p={p}"
+
+
+# ---------------------------------------------------------------------- Boris
+
+def pin_boris_pure_b(O):
+    """Pure magnetic field: |u| is conserved and u_perp turns by
+    2 atan(|q| B dt / (2 m gamma)) per step, in the sense of -q B."""
+    q, m, dt = -1.0, 1.0, 0.3
+    B = np.array([0.0, 0.0, 1.7])
+    u = np.array([0.4, -0.2, 0.3])
+    gam = np.sqrt(1 + u @ u)
+    theta = 2 * np.arctan(abs(q) * B[2] * dt / (2 * m * gam))
+    EB = np.concatenate([np.zeros(3), B])[None, :]
+    ux, uy, uz = u[:1].copy(), u[1:2].copy(), u[2:].copy()
+    phase0 = np.arctan2(uy[0], ux[0])
+    M = 200
+    for step in range(1, M + 1):
+        ux, uy, uz = O.boris(q, m, dt, EB, ux, uy, uz)
+        un = np.array([ux[0], uy[0], uz[0]])
+        assert abs(np.linalg.norm(un) - np.linalg.norm(u)) < 1e-14 * np.linalg.norm(u)
+        assert abs(uz[0] - u[2]) < 1e-15
+    # q < 0 and B along +z: counter-clockwise rotation seen from +z
+    expect = phase0 + M * theta
+    got = np.arctan2(uy[0], ux[0])
+    diff = (got - expect + np.pi) % (2 * np.pi) - np.pi
+    assert abs(diff) < 1e-11, f"gyro phase {diff}"
+
+
+def pin_boris_pure_e(O):
+    """Pure electric field: u after M steps is u0 + M q E dt / m."""
+    q, m, dt = -1.0, 1.0, 0.4
+    E = np.array([0.3, -0.7, 0.11])
+    EB = np.concatenate([E, np.zeros(3)])[None, :]
+    ux, uy, uz = np.array([0.1]), np.array([0.2]), np.array([-0.05])
+    u0 = np.array([0.1, 0.2, -0.05])
+    M = 50
+    for _ in range(M):
+        ux, uy, uz = O.boris(q, m, dt, EB, ux, uy, uz)
+    ref = u0 + M * q * E * dt / m
+    got = np.array([ux[0], uy[0], uz[0]])
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def pin_boris_exb(O):
+    """Crossed fields |E| << |B|: starting on the drift, u stays at E x B / B^2."""
+    q, m, dt = -1.0, 1.0, 0.05
+    E = np.array([0.0, 1e-3, 0.0])
+    B = np.array([0.0, 0.0, 1.0])
+    vd = np.cross(E, B) / (B @ B)
+    u = vd / np.sqrt(1 - vd @ vd)
+    EB = np.concatenate([E, B])[None, :]
+    ux, uy, uz = u[:1].copy(), u[1:2].copy(), u[2:].copy()
+    acc = np.zeros(3)
+    M = 2000
+    for _ in range(M):
+        ux, uy, uz = O.boris(q, m, dt, EB, ux, uy, uz)
+        un = np.array([ux[0], uy[0], uz[0]])
+        acc += un / np.sqrt(1 + un @ un)
+    v = acc / M
+    assert abs(v[0] - vd[0]) < 1e-4 * abs(vd[0]) and abs(v[1]) < 1e-6
+
+
+# ------------------------------------------------------------------ Esirkepov
+
+def _moves(seed, m, L, maxstep):
+    x0 = [_rand(seed, m, 0.0, L[a], draw=a) for a in range(3)]
+    dx = [_rand(seed, m, -maxstep, maxstep, draw=3 + a) for a in range(3)]
+    return x0, [x0[a] + dx[a] for a in range(3)]
+
+
+def pin_esirkepov_continuity(O):
+    """Discrete continuity (rho1 - rho0)/dt + div J = 0 for single particles
+    and for a cloud, all orders, on a non-cubic grid with non-unit spacing."""
+    n = (7, 9, 8)
+    d = (1.0, 0.8, 1.25)
+    g = O.grid(n, d)
+    L = np.array(n) * np.array(d)
+    dt, q = 0.45, -1.0
+    for p in (1, 2, 3):
+        x0, x1 = _moves(31 + p, 50, L, 0.95 * min(d))
+        w = _rand(40, 50, 0.2, 1.5)
+        for s in list(range(5)) + [slice(None)]:
+            sl = [a[s] if isinstance(s, slice) else a[s:s + 1] for a in x0]
+            sl1 = [a[s] if isinstance(s, slice) else a[s:s + 1] for a in x1]
+            ww = w[s] if isinstance(s, slice) else w[s:s + 1]
+            J = O.deposit(g, p, dt, q, *sl, *sl1, ww)
+            r0 = O.rho(g, p, q, *sl, ww)
+            r1 = O.rho(g, p, q, *sl1, ww)
+            res = (r1 - r0) / dt + O.div_edge(g, J)
+            scale = np.max(np.abs(r1 - r0)) / dt
+            assert np.max(np.abs(res)) <= 1e-13 * scale, f"continuity p={p}"
+
+
+def pin_esirkepov_total_current(O):
+    """sum J_c dV = q w (x1_c - x0_c) / dt per particle."""
+    n = (8, 8, 8)
+    d = (1.0, 1.1, 0.9)
+    g = O.grid(n, d)
+    L = np.array(n) * np.array(d)
+    dt, q = 0.5, -1.0
+    dV = np.prod(d)
+    for p in (1, 2, 3):
+        x0, x1 = _moves(50 + p, 20, L, 0.9)
+        for i in range(20):
+            J = O.deposit(g, p, dt, q, *[a[i:i + 1] for a in x0], *[a[i:i + 1] for a in x1], np.array([0.7]))
+            for c in range(3):
+                ref = q * 0.7 * (x1[c][i] - x0[c][i]) / dt
+                assert abs(J[c].sum() * dV - ref) < 1e-14 * max(1.0, abs(ref)) + 1e-15, f"total current p={p}"
+
+
+def pin_esirkepov_pure_x(O):
+    """Motion along x only deposits no J_y or J_z."""
+    g = O.grid((8, 8, 8))
+    for p in (1, 2, 3):
+        x0 = [np.array([3.3]), np.array([4.71]), np.array([2.05])]
+        x1 = [np.array([3.9]), x0[1].copy(), x0[2].copy()]
+        J = O.deposit(g, p, 0.5, -1.0, *x0, *x1, np.array([1.0]))
+        assert np.all(J[1] == 0.0) and np.all(J[2] == 0.0)
+        assert np.any(J[0] != 0.0)
+
+
+def _brute_force_J(n, d, p, dt, q, x0, x1, w):
+    """Esirkepov current of one particle without any window: shapes on a wide
+    unwrapped node range from scipy's B-spline, Esirkepov's S0/S1 form of W
+    (1/3 S1S1S1 - ... in his 2001 paper), cumulative sums started far left,
+    folded onto the periodic grid."""
+    f = bspline(p)
+    rng, S0, S1 = [], [], []
+    for a in range(3):
+        p0, p1 = x0[a] / d[a], x1[a] / d[a]
+        r = np.arange(int(np.floor(min(p0, p1))) - 6, int(np.floor(max(p0, p1))) + 8)
+        rng.append(r)
+        S0.append(f(p0 - r))
+        S1.append(f(p1 - r))
+    J = np.zeros((3,) + tuple(n))
+    dV = np.prod(d)
+    for c in range(3):
+        a1, a2 = (c + 1) % 3, (c + 2) % 3
+        A0, A1 = S0[c], S1[c]
+        B0, B1 = S0[a1], S1[a1]
+        C0, C1 = S0[a2], S1[a2]
+        o = np.einsum
+        W = (o("i,j,k->ijk", A1 - A0, B1, C1) / 3 + o("i,j,k->ijk", A1 - A0, B0, C1) / 6 +
+             o("i,j,k->ijk", A1 - A0, B1, C0) / 6 + o("i,j,k->ijk", A1 - A0, B0, C0) / 3)
+        Jc = -q * w * d[c] / (dt * dV) * np.cumsum(W, axis=0)
+        # Jc axes are (c, a1, a2); map to (x, y, z) node indices
+        I = np.meshgrid(rng[c], rng[a1], rng[a2], indexing="ij")
+        node = [None, None, None]
+        node[c], node[a1], node[a2] = I
+        flat = ((node[0] % n[0]) * n[1] + (node[1] % n[1])) * n[2] + (node[2] % n[2])
+        np.add.at(J[c].reshape(-1), flat.ravel(), Jc.ravel())
+    return J
+
+
+def pin_esirkepov_brute_force(O):
+    """Windowed deposit equals the window-free brute force on tiny grids,
+    including grids smaller than the stencil (periodic images overlap)."""
+    for n, d in (((4, 4, 4), (1.0, 1.0, 1.0)), ((5, 6, 4), (1.0, 0.7, 1.3)), ((8, 8, 8), (1.0, 1.0, 1.0))):
+        g = O.grid(n, d)
+        L = np.array(n) * np.array(d)
+        for p in (1, 2, 3):
+            x0, x1 = _moves(60 + p + n[1], 12, L, 0.97 * min(d))
+            w = _rand(70, 12, 0.3, 1.2)
+            Jo = O.deposit(g, p, 0.5, -1.0, *x0, *x1, w)
+            Jb = np.zeros_like(Jo)
+            for i in range(12):
+                Jb += _brute_force_J(n, d, p, 0.5, -1.0, [a[i] for a in x0], [a[i] for a in x1], w[i])
+            err = np.linalg.norm(Jo - Jb) / np.linalg.norm(Jb)
+            assert err < 1e-14, f"brute force n={n} p={p} err={err}"
+
+
+# ------------------------------------------------------------------------ Yee
+
+def _levi(a, b, c):
+    return {(0, 1, 2): 1, (1, 2, 0): 1, (2, 0, 1): 1, (0, 2, 1): -1, (2, 1, 0): -1, (1, 0, 2): -1}[(a, b, c)]
+
+
+def pin_yee_plane_waves(O):
+    """Single discrete modes evolve exactly: for k along axis a and E along
+    e != a (h the third axis), with B = 0 at t = 0,
+      E_e = A cos(n w dt) cos(k x_a),
+      B_h = eps(h,a,e) A cos(w dt/2) sin(n w dt) sin(k (x_a + d_a/2)),
+    where sin^2(w dt/2)/dt^2 = sin^2(k d_a/2)/d_a^2 (Yee numerical dispersion)."""
+    n = (10, 8, 12)
+    d = (1.0, 0.8, 1.25)
+    g = O.grid(n, d)
+    dt = 0.95 / np.sqrt(sum(1 / np.array(d) ** 2))
+    M, A = 23, 0.8
+    idx = np.indices(n).astype(np.float64)
+    for a in range(3):
+        m = 2 if n[a] >= 8 else 1
+        k = 2 * np.pi * m / (n[a] * d[a])
+        kappa = 2 * np.sin(k * d[a] / 2) / d[a]
+        w = 2 / dt * np.arcsin(kappa * dt / 2)
+        for e in range(3):
+            if e == a:
+                continue
+            h = 3 - a - e
+            F = np.zeros((9,) + n)
+            F[e] = A * np.cos(k * idx[a] * d[a])
+            for _ in range(M):
+                O.yee_step(g, dt, F)
+            Ee = A * np.cos(M * w * dt) * np.cos(k * idx[a] * d[a])
+            Bh = _levi(h, a, e) * A * np.cos(w * dt / 2) * np.sin(M * w * dt) * np.sin(k * (idx[a] + 0.5) * d[a])
+            assert np.max(np.abs(F[e] - Ee)) < 1e-12, f"E mode a={a} e={e}"
+            assert np.max(np.abs(F[3 + h] - Bh)) < 1e-12, f"B mode a={a} e={e}"
+            rest = [c for c in range(6) if c not in (e, 3 + h)]
+            assert np.max(np.abs(F[rest])) < 1e-13
+
+
+def pin_yee_oblique(O):
+    """Oblique mode E_z = A cos(kx x + ky y): frequency from
+    sin^2(w dt/2)/dt^2 = sum_d sin^2(k_d d_d/2)/d_d^2."""
+    n = (12, 10, 4)
+    d = (1.0, 1.2, 1.0)
+    g = O.grid(n, d)
+    dt = 0.9 / np.sqrt(sum(1 / np.array(d) ** 2))
+    kx, ky = 2 * np.pi * 2 / (n[0] * d[0]), 2 * np.pi * 3 / (n[1] * d[1])
+    s = (np.sin(kx * d[0] / 2) / d[0]) ** 2 + (np.sin(ky * d[1] / 2) / d[1]) ** 2
+    w = 2 / dt * np.arcsin(dt * np.sqrt(s))
+    idx = np.indices(n).astype(np.float64)
+    phase = kx * idx[0] * d[0] + ky * idx[1] * d[1]
+    F = np.zeros((9,) + n)
+    F[2] = np.cos(phase)
+    M = 31
+    for _ in range(M):
+        O.yee_step(g, dt, F)
+    assert np.max(np.abs(F[2] - np.cos(M * w * dt) * np.cos(phase))) < 1e-12
+
+
+def pin_yee_div_b(O):
+    """div B is unchanged by any number of Yee steps with arbitrary E, B, J."""
+    n = (6, 7, 5)
+    g = O.grid(n, (1.0, 0.9, 1.1))
+    F = inputs.random_fields(81, n)
+    db0 = O.div_face(g, F[3:6])
+    for _ in range(10):
+        O.yee_step(g, 0.4, F)
+    assert np.max(np.abs(O.div_face(g, F[3:6]) - db0)) < 1e-13
+
+
+def pin_gauss_with_pic_step(O):
+    """div E - rho is constant across full PIC steps (Esirkepov + Yee share one staggering)."""
+    n = (8, 8, 8)
+    g = O.grid(n)
+    for p in (1, 2, 3):
+        parts = inputs.uniform_plasma(90 + p, n, 1, sigma_u=0.6, density=1.0)
+        F = np.zeros((9,) + n)
+        F[:6] = inputs.random_fields(91, n, 0.05)[:6]
+        q = -1.0
+        r0 = O.rho(g, p, q, parts["x"], parts["y"], parts["z"], parts["w"])
+        g0 = O.div_edge(g, F[0:3]) - r0
+        for s in range(3):
+            O.pic_step(g, p, 0.55, q, 1.0, parts, F)
+        r1 = O.rho(g, p, q, parts["x"], parts["y"], parts["z"], parts["w"])
+        g1 = O.div_edge(g, F[0:3]) - r1
+        assert np.max(np.abs(g1 - g0)) < 1e-13 * np.max(np.abs(r0)), f"Gauss p={p}"
+
+
+ALL_PINS = [
+    pin_shape_library, pin_shape_moments, pin_shape_convolution, pin_shape_values,
+    pin_gather_constant, pin_gather_polynomial,
+    pin_boris_pure_b, pin_boris_pure_e, pin_boris_exb,
+    pin_esirkepov_continuity, pin_esirkepov_total_current, pin_esirkepov_pure_x, pin_esirkepov_brute_force,
+    pin_yee_plane_waves, pin_yee_oblique, pin_yee_div_b, pin_gauss_with_pic_step,
+]
+
+
+def pin_free_streaming(O):
+    """Zero fields: particles move at v = u/gamma, u is unchanged, positions wrap
+    periodically; no current survives a closed orbit of the whole box."""
+    n = (6, 5, 7)
+    d = (1.0, 1.2, 0.9)
+    g = O.grid(n, d)
+    L = np.array(n) * np.array(d)
+    m = 30
+    parts = {
+        "x": _rand(100, m, 0.0, L[0], 0), "y": _rand(100, m, 0.0, L[1], 1), "z": _rand(100, m, 0.0, L[2], 2),
+        "ux": _rand(100, m, -3.0, 3.0, 3), "uy": _rand(100, m, -3.0, 3.0, 4), "uz": _rand(100, m, -3.0, 3.0, 5),
+        "w": np.ones(m),
+    }
+    x0 = {k: v.copy() for k, v in parts.items()}
+    F = np.zeros((9,) + n)
+    dt = 0.5
+    M = 7
+    for _ in range(M):
+        O.pic_step(g, 2, dt, 0.0, 1.0, parts, F)  # q = 0: no force, no current
+    gam = np.sqrt(1 + x0["ux"] ** 2 + x0["uy"] ** 2 + x0["uz"] ** 2)
+    for a, (k, uk) in enumerate((("x", "ux"), ("y", "uy"), ("z", "uz"))):
+        ref = np.mod(x0[k] + M * dt * x0[uk] / gam, L[a])
+        diff = (parts[k] - ref + L[a] / 2) % L[a] - L[a] / 2
+        assert np.max(np.abs(diff)) < 1e-12, f"free streaming axis {a}"
+        assert np.all(parts[k] >= 0.0) and np.all(parts[k] < L[a])
+        assert np.array_equal(parts[uk], x0[uk])
+    assert np.max(np.abs(F)) == 0.0
+
+
+ALL_PINS.append(pin_free_streaming)

@@ -1,0 +1,35 @@
+"""The oracle's pins catch plausible mistakes (CPU only).
+
+Each mutant is the oracle rebuilt with one planted mistake (ORC_MUTANT in
+oracle/pic_oracle.c): a wrong shape piece, a missing staggering offset, a
+dropped Boris half kick, an Esirkepov window off by one node, 1/2 for 1/3 in
+Esirkepov's W, a flipped curl sign, a flipped current sign, momentum used as
+velocity.  Every mutant must fail at least one pin.
+"""
+import pytest
+
+import pins_lib
+from oracle import Oracle
+
+MUTANTS = {
+    1: "cubic shape inner piece",
+    2: "Ex gathered without staggering",
+    3: "Boris second half kick dropped",
+    4: "Esirkepov window start off by one",
+    5: "Esirkepov 1/2 for 1/3",
+    6: "curl sign in the B update",
+    7: "current sign in the E update",
+    8: "momentum used as velocity",
+}
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS), ids=lambda k: MUTANTS[k])
+def test_mutant_is_caught(mutant):
+    O = Oracle(mutant=mutant)
+    failed = []
+    for pin in pins_lib.ALL_PINS:
+        try:
+            pin(O)
+        except AssertionError:
+            failed.append(pin.__name__)
+    assert failed, f"no pin catches mutant {mutant} ({MUTANTS[mutant]})"
