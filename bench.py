@@ -1,0 +1,390 @@
+"""Benchmark of the PIC hot path (sort + gather + push + deposit + Yee) on GB300.
+
+Default workload: the uniform thermal plasma of the paper's scaling runs
+(Sec. 4.1.1): 256^3 periodic cells, 8 particles per cell (134,217,728
+particles), order-3 shapes, u ~ N(0, 0.05), density 1, dt = 0.99 CFL,
+synthetic seeded inputs.  One step = counting sort + fused gather/push/
+deposit tile kernel + Yee update, in FP32-mixed (the headline) and FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs an independent
+replica of the workload on its own GPU (the path has no exchange step on one
+box): value = all ranks' particle-steps / the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "uniform_256"
+METRIC = "particle-steps/s (gather+push+deposit+Yee), FP32-mixed vs FP64 at stated error"
+UNIT = "particle-steps/s"
+# FP32 ALU roof of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# ALU roof of FP64 (CUDA cores) on GB300, public dense FP64 figure
+FP64_PEAK_TFLOPS = 1.25
+
+
+def flops_per_particle(p: int) -> int:
+    """Algorithmic flops of gather + Boris + advance + Esirkepov per particle
+    (FMA = 2).  S = p+1 stencil nodes per axis, NW = p+2 Esirkepov window."""
+    S, NW = p + 1, p + 2
+    shape_cost = {1: 1, 2: 9, 3: 14}[p]
+    gather = 12 * (S ** 3 + S ** 2 + S)
+    weights = 12 * shape_cost
+    boris, advance = 60, 16
+    esirk = 3 * NW + 3 * (2 * (NW - 1) + 8 * NW * NW + 2 * NW * NW * (NW - 1))
+    return gather + weights + boris + advance + esirk
+
+
+def bytes_per_launch(np_, C, prec):
+    """Algorithmic HBM bytes of one fused tile-kernel launch: each particle's
+    state read once and written once (FP32-mixed: key + 3 offsets + 3 u + w
+    read, key + 3 offsets + 3 u written = 60 B; FP64: 7 doubles read, 6
+    written = 104 B), E and B read once and J written once per cell."""
+    if prec == "fp32":
+        return np_ * 60 + C * (24 + 12)
+    return np_ * 104 + C * (48 + 24)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pic_kernels.cu", "pic_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2101_12149_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, prec):
+    """DRAM bytes per launch from the committed ncu summary, or None when the
+    summary is absent or was taken on a different kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}_{prec}.md")
+    if not os.path.exists(path):
+        return None
+    src_hash, traffic = None, None
+    for line in open(path):
+        if line.startswith("kernel_source_hash:"):
+            src_hash = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_launch_full_size:"):
+            traffic = float(line.split(":", 1)[1].strip())
+    if src_hash != kernel_source_hash():
+        return None
+    return traffic
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.uuid}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in self.samples:
+            try:
+                sm.append(float(s[0]))
+                mx.append(float(s[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, s[3:7]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pinned_particles(n_cells_ppc, torch):
+    """Pinned host float64 arrays for the particle SoA (numpy views)."""
+    out, keep = {}, []
+    for k in ("x", "y", "z", "ux", "uy", "uz", "w"):
+        t = torch.empty(n_cells_ppc, dtype=torch.float64, pin_memory=True)
+        keep.append(t)
+        out[k] = t.numpy()
+    return out, keep
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The oracle as it stands on a bounded sample of the workload: the same
+    recipe (8 ppc, order 3, u ~ N(0, 0.05), density 1, dt = 0.99 CFL) on a
+    32^3 periodic box, a few full steps, single host core."""
+    from oracle import Oracle
+    from paper_2101_12149_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    n = (32, 32, 32)
+    O = Oracle()
+    g = O.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+    parts = inputs.uniform_plasma(w["seed"], n, w["ppc"], sigma_u=w["sigma_u"], density=w["density"])
+    F = np.zeros((9,) + n)
+    N = parts["x"].size
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        O.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or steps >= 50:
+            break
+    return {"value": N * steps / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle on the same recipe at 32^3 ({N} particles, order 3, 8 ppc), {steps} steps, "
+                      f"{el:.1f} s, 1 host core"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from __graft_entry__ import build
+    build()
+    base = cpu_baseline(seconds_target=max(5.0, 2.0 * (args.steps + args.warmup)))
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "256^3", "ppc": 8, "order": 3,
+                       "sample": "32^3 box of the same recipe (CPU oracle)"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def timed_run(ctx, steps, stream, torch):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def field_error_statement(torch, steps=100):
+    """FP32-mixed against FP64 on a 64^3 copy of the recipe for `steps` steps
+    (relative L2 of E and B), with the FP64 sensitivity floor: FP64 rerun with
+    momenta perturbed by 1e-7 relative."""
+    from paper_2101_12149_gb300 import inputs, pic
+    w = inputs.WORKLOADS[WORKLOAD]
+    n = (64, 64, 64)
+    parts = inputs.uniform_plasma(w["seed"], n, w["ppc"], sigma_u=w["sigma_u"], density=w["density"])
+    res = {}
+    s = torch.cuda.Stream()
+
+    def run(prec, p):
+        with pic.Context(n, cfl=w["cfl"], order=w["order"], precision=prec, stream=s) as ctx:
+            ctx.load_particles(-1.0, 1.0, p)
+            ctx.step(steps)
+            return ctx.get_fields()[:6]
+
+    F64 = run(pic.FP64, parts)
+    F32 = run(pic.FP32_MIXED, parts)
+    pert = {k: v.copy() for k, v in parts.items()}
+    for k in ("ux", "uy", "uz"):
+        pert[k] *= 1.0 + 1e-7 * (2 * inputs.uniform(99, 0, pert[k].size, 3) - 1)
+    Fp = run(pic.FP64, pert)
+    nrm = np.linalg.norm(F64)
+    res["fp32_field_rel_l2"] = float(np.linalg.norm(F32 - F64) / nrm)
+    res["fp64_floor_rel_l2"] = float(np.linalg.norm(Fp - F64) / nrm)
+    res["steps"] = steps
+    res["grid"] = "64^3 copy of the recipe (8 ppc, order 3)"
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-extras", action="store_true", help="skip FP64, error statement, e2e and CPU legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from __graft_entry__ import build
+    if rank == 0 or world == 1:
+        build()
+    if dist:
+        dist.barrier()
+        build()
+    from paper_2101_12149_gb300 import inputs, pic
+
+    w = inputs.WORKLOADS[WORKLOAD]
+    n, ppc, order = w["n"], w["ppc"], w["order"]
+    C = n[0] * n[1] * n[2]
+    N = C * ppc
+    host, _keep = pinned_particles(N, torch)
+    inputs.uniform_plasma(w["seed"] + rank * 7919, n, ppc, sigma_u=w["sigma_u"], density=w["density"], out=host)
+
+    stream = torch.cuda.Stream()
+
+    def make_ctx(prec):
+        ctx = pic.Context(n, cfl=w["cfl"], order=order, precision=prec, stream=stream)
+        dev = {k: torch.from_numpy(v).to(f"cuda:{local}", non_blocking=False) for k, v in host.items()}
+        ctx.load_particles(-1.0, 1.0, dev)
+        del dev
+        torch.cuda.empty_cache()
+        return ctx
+
+    # ---- headline: FP32-mixed, device-resident inputs ---------------------
+    ctx = make_ctx(pic.FP32_MIXED)
+    ctx.step(args.warmup)
+    ctx.set_timing(True)
+    l0 = ctx.launch_count()
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid) if hasattr(
+        torch.cuda.get_device_properties(local), "uuid") else str(local)
+    if dist:
+        dist.barrier()
+    with ClockSampler(uuid) as clk:
+        t = timed_run(ctx, args.steps, stream, torch)
+    launches = ctx.launch_count() - l0
+    timings = ctx.get_timing()
+    ctx.set_timing(False)
+    if dist:
+        tt = torch.tensor([t], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        dist.barrier()
+    value = world * N * args.steps / t
+    ms_step = 1e3 * t / args.steps
+    ctx.close()
+
+    peaks, peak_kind = measured_peaks()
+    ms_tile, n_tile = timings.get("k_tile_step", (0.0, 0))
+    avg_tile_s = ms_tile / max(n_tile, 1) / 1e3
+    flops = N * flops_per_particle(order)
+    alu_tf = flops / avg_tile_s / 1e12 if avg_tile_s > 0 else None
+    hbm = bytes_per_launch(N, C, "fp32") / avg_tile_s / 1e9 if avg_tile_s > 0 else None
+    alu_frac = alu_tf / FP32_PEAK_TFLOPS if alu_tf else None
+    hbm_frac = hbm / peaks["hbm_gbs"] if hbm else None
+    traffic = profiled_traffic("k_tile_step", "fp32")
+    roof_alu = {"bound": "alu", "achieved": alu_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu_frac,
+                "traffic": traffic, "kernel": "k_tile_step",
+                "note": "FP32 ALU roof derived from 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops "
+                        f"{flops_per_particle(order)} per particle"}
+    roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
+                "traffic": traffic, "kernel": "k_tile_step", "peak_source": f"{peak_kind} hbm_gbs"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32-mixed", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": "256^3", "ppc": ppc, "particles": N, "order": order,
+                   "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": 1, "precision": "fp32_mixed",
+                   "l2": "inputs larger than L2 (4.8 GB of particle state per step)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof_alu if (alu_frac or 0) >= (hbm_frac or 0) else roof_hbm,
+        "roofline_alt": roof_hbm if (alu_frac or 0) >= (hbm_frac or 0) else roof_alu,
+        "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
+        "kernel_share": {k: v[0] / max(sum(x[0] for x in timings.values()), 1e-30) for k, v in timings.items()},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_extras:
+        # ---- FP64 on the same workload -----------------------------------
+        ctx64 = make_ctx(pic.FP64)
+        ctx64.step(1)
+        ctx64.set_timing(True)
+        t64 = timed_run(ctx64, args.fp64_steps, stream, torch)
+        tm64 = ctx64.get_timing()
+        ctx64.close()
+        torch.cuda.empty_cache()
+        ms64, n64 = tm64.get("k_tile_step", (0.0, 0))
+        fl64 = N * flops_per_particle(order) / (ms64 / max(n64, 1) / 1e3) / 1e12 if n64 else None
+        line["fp64"] = {"value": world * N * args.fp64_steps / t64, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                        "steps": args.fp64_steps, "tile_kernel_tflops": fl64,
+                        "tile_kernel_frac_of_fp64_peak": fl64 / FP64_PEAK_TFLOPS if fl64 else None,
+                        "fp32_mixed_speedup": value / (world * N * args.fp64_steps / t64)}
+        # ---- stated error of FP32-mixed ----------------------------------
+        if rank == 0:
+            line["error"] = field_error_statement(torch)
+        # ---- end to end through the C-ABI with host buffers ----------------
+        e2e_steps = args.steps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx2 = pic.Context(n, cfl=w["cfl"], order=order, precision=pic.FP32_MIXED, stream=stream)
+        ctx2.load_particles(-1.0, 1.0, host)
+        for _ in range(e2e_steps):
+            ctx2.step(1)
+            ctx2.diagnostics()
+        ex = ctx2.get_field("Ex")
+        t_e2e = time.perf_counter() - t0
+        ctx2.close()
+        h2d = 7 * 8 * N
+        d2h = e2e_steps * 4 * 8 + ex.nbytes
+        line["e2e"] = {"value": world * N * e2e_steps / t_e2e, "unit": UNIT,
+                       "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
+                       "what": "context creation + pic_load_particles from pinned host FP64 arrays + "
+                               f"{e2e_steps} x (pic_step + pic_diagnostics read-back) + E_x field read-back"}
+        if rank == 0 and world == 1:
+            line["cpu_baseline"] = cpu_baseline()
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

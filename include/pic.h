@@ -1,0 +1,173 @@
+/*
+ * libpic: GB300-native (sm_103a) electromagnetic particle-in-cell hot path.
+ *
+ * One species of macro-particles on a 3-D periodic Yee grid, advanced by the
+ * PIC loop whose GPU port the paper describes (Myers et al., "Porting WarpX
+ * to GPU-accelerated platforms", 2021):
+ *   field gather with order-p B-spline shapes, p = 1..3 (Sec. 4.1.1 runs
+ *     3rd order; fused with the push, Sec. 3.1),
+ *   relativistic Boris push and position advance,
+ *   Esirkepov charge-conserving current deposition (Sec. 3.4.1),
+ *   Yee FDTD update of E and B (Sec. 2.4, Sec. 4.1.1),
+ *   per-step counting sort of the particles by cell (Sec. 3.4.2).
+ *
+ * Conventions.  Normalised units c = eps0 = mu0 = 1.  Node (i,j,k) sits at
+ * (i dx, j dy, k dz); the box is periodic with length n*d per axis.  Field
+ * arrays are nx*ny*nz values, element (i*ny + j)*nz + k (k fastest) holding
+ * the component at its staggered location just above node (i,j,k):
+ *   Ex(i+1/2,j,k) Ey(i,j+1/2,k) Ez(i,j,k+1/2)
+ *   Bx(i,j+1/2,k+1/2) By(i+1/2,j,k+1/2) Bz(i+1/2,j+1/2,k)   J like E.
+ * Particle momentum is u = gamma v (units of m c); u lives at half steps.
+ * One step: gather E^n, B^n at x^n -> Boris u^{n-1/2} -> u^{n+1/2} ->
+ * x^{n+1} = x^n + dt u/gamma -> Esirkepov J^{n+1/2} -> B half step, E full
+ * step with -dt J, B half step.
+ *
+ * Ownership.  The context owns every device buffer; all of them are
+ * allocated by pic_init_grid / pic_load_particles and none inside a step.
+ * Arrays passed in are copied; the caller keeps ownership.  Getters copy out
+ * into caller memory.  `on_device` = 1 means the pointer is device memory of
+ * the context's GPU, 0 means host memory (pageable or pinned).
+ *
+ * Errors.  Every call returns a pic_status; nothing throws across the ABI.
+ * pic_last_error() gives a message for the calling thread's last failure.
+ * Kernels report asynchronous faults (non-finite particle, particle moving a
+ * cell or more per step, a scan wait that ran out) in a device error word that
+ * pic_step and pic_sync check.
+ *
+ * Streams.  All work is queued on the stream given to pic_init_grid
+ * (NULL = the legacy default stream).  Calls return once the work is queued,
+ * except getters to host memory, pic_sync and pic_diagnostics, which wait.
+ */
+#ifndef LIBPIC_PIC_H
+#define LIBPIC_PIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+    PIC_OK = 0,
+    PIC_ERR_ARG = 1,      /* invalid argument (NULL, bad order, extents, sizes) */
+    PIC_ERR_CFL = 2,      /* dt above the Yee Courant limit 1/sqrt(sum 1/d^2) */
+    PIC_ERR_OOM = 3,      /* device allocation failed */
+    PIC_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+    PIC_ERR_STATE = 5,    /* call out of order (e.g. stepping with no particles) */
+    PIC_ERR_PARTICLE = 6, /* a particle became non-finite or moved >= 1 cell in a step */
+    PIC_ERR_TIMEOUT = 7   /* a bounded device-side wait ran out */
+} pic_status;
+
+enum { PIC_FP64 = 0, PIC_FP32_MIXED = 1 };
+
+enum { PIC_EX = 0, PIC_EY, PIC_EZ, PIC_BX, PIC_BY, PIC_BZ, PIC_JX, PIC_JY, PIC_JZ };
+
+/* Grid and method description (the problem statement of the paper's
+ * uniform-plasma runs, Sec. 4.1.1: extents, cell size, dt at a stated
+ * Courant number, shape order). */
+typedef struct {
+    int32_t n[3];        /* cells per axis, each >= order + 2 */
+    double d[3];         /* cell size per axis, > 0 */
+    double dt;           /* time step; 0 selects dt = cfl / sqrt(sum 1/d^2) */
+    double cfl;          /* Courant number used when dt == 0, in (0, 1] */
+    int32_t precision;   /* PIC_FP64 or PIC_FP32_MIXED */
+    int32_t order;       /* shape order 1..3 */
+    int32_t sort_every;  /* counting sort every this many steps (>= 1) */
+    int32_t window_axis; /* -1 (no moving window); reserved */
+    double window_speed; /* reserved */
+    uint64_t seed;       /* reserved for generators that run inside the library */
+    int32_t tile[3];     /* cells per tile per axis (powers of two dividing n); 0 = automatic */
+} pic_grid_desc;
+
+/* Create a context: validates the description (PIC_ERR_ARG, PIC_ERR_CFL),
+ * allocates the nine field arrays (zeroed) on the current CUDA device and
+ * binds `cuda_stream` (a cudaStream_t, may be NULL).  *out receives the
+ * context; on failure *out is NULL. */
+pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx** out);
+
+/* Load one species: charge q and mass m per unit weight, n particles with
+ * positions x,y,z (inside [0, n*d) per axis; values outside are wrapped),
+ * momenta ux,uy,uz = gamma v at t = -dt/2, weights w (FP64 arrays of n).
+ * Replaces any previous particles, allocates the particle buffers for n,
+ * assigns ids 0..n-1 in input order and sorts the particles by cell.
+ * PIC_ERR_ARG if n < 0 or n >= 2^31, a pointer is NULL with n > 0, or a
+ * value is non-finite. */
+pic_status pic_load_particles(pic_ctx* ctx, double q, double m, int64_t n,
+                              const double* x, const double* y, const double* z,
+                              const double* ux, const double* uy, const double* uz,
+                              const double* w, int on_device);
+
+/* Gather E,B at the particles, Boris push and position advance (one
+ * particle per thread, fields read from global memory).  Saves the old
+ * positions for pic_deposit.  Does not sort. */
+pic_status pic_gather_push(pic_ctx* ctx);
+
+/* Zero J and deposit the Esirkepov current of the move made by the last
+ * pic_gather_push (one particle per thread, global atomics).
+ * PIC_ERR_STATE if no pic_gather_push preceded it. */
+pic_status pic_deposit(pic_ctx* ctx);
+
+/* Yee update with the current J: B half step, E full step, B half step. */
+pic_status pic_yee_step(pic_ctx* ctx);
+
+/* nsteps full PIC steps: counting sort (at the sort cadence), fused tile
+ * kernel (gather + push + advance + Esirkepov into shared memory, one flush
+ * per tile), Yee update.  Checks the device error word at the end. */
+pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/* Copy one field component (PIC_EX..PIC_JZ) out as FP64 / in from FP64. */
+pic_status pic_get_field(pic_ctx* ctx, int32_t which, double* dst, int on_device);
+pic_status pic_set_field(pic_ctx* ctx, int32_t which, const double* src, int on_device);
+
+/* Number of particles held. */
+pic_status pic_num_particles(pic_ctx* ctx, int64_t* n);
+
+/* Copy particle state out as FP64 (positions in [0, L)), in the library's
+ * current (cell-sorted) order; `id` gives each particle's load index.  Any
+ * pointer may be NULL to skip that array. */
+pic_status pic_get_particles(pic_ctx* ctx, double* x, double* y, double* z,
+                             double* ux, double* uy, double* uz, double* w,
+                             int32_t* id, int on_device);
+
+/* External drive added to the gathered E at each particle (not to the grid):
+ * E_y += amp * cos(k x - k t_n), t_n = n dt the time of the gather.  amp = 0
+ * switches it off. */
+pic_status pic_set_external_drive(pic_ctx* ctx, double amp, double k);
+
+/* Simulation time step count and time (t = steps * dt). */
+pic_status pic_get_time(pic_ctx* ctx, int64_t* steps, double* t);
+
+/* Diagnostics (FP64 reductions on the device): out[0] = field energy
+ * 1/2 sum(|E|^2+|B|^2) dV, out[1] = kinetic energy sum w m (gamma - 1),
+ * out[2] = sum of charge q w, out[3] = max |div B| dV^(1/3).  Waits. */
+pic_status pic_diagnostics(pic_ctx* ctx, double out[4]);
+
+/* Wait for queued work; returns the device error word's status. */
+pic_status pic_sync(pic_ctx* ctx);
+
+/* Per-kernel timing: when on, pic_step launches its kernels directly (no
+ * graph) between CUDA events on the context stream and accumulates their
+ * durations.  pic_get_timing fills up to `cap` entries: kernel name
+ * (pointer to a static string), total milliseconds and launch count, and
+ * returns the number of kernel kinds in *count.  Waits. */
+pic_status pic_set_timing(pic_ctx* ctx, int32_t on);
+pic_status pic_get_timing(pic_ctx* ctx, int32_t cap, const char** names, double* ms,
+                          int64_t* launches, int32_t* count);
+
+/* Number of kernels this context has launched (graph replays counted per
+ * kernel node). */
+pic_status pic_launch_count(pic_ctx* ctx, int64_t* n);
+
+/* Release every buffer of the context (NULL is allowed). */
+pic_status pic_destroy(pic_ctx* ctx);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBPIC_PIC_H */

@@ -1,0 +1,621 @@
+// C-ABI of libpic: context lifetime, validation, particle loading, the step
+// loop (CUDA-graph replay per step kind), getters/setters, diagnostics,
+// per-kernel timing.  Declarations and the contract: include/pic.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pic_ctx.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pic_status fail(pic_status s, const std::string& msg) {
+    g_last_error = msg;
+    return s;
+}
+
+pic_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(PIC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define PIC_CUDA(call)                                          \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+void free_particles(pic_ctx* c) {
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(c->P[b].a[0]);
+        c->P[b] = pic::PartBuf();
+    }
+    cudaFree(c->old[0]);
+    for (auto& o : c->old) o = nullptr;
+    c->oldkey = nullptr;
+    c->np = c->cap = 0;
+    c->have_old = false;
+}
+
+// One allocation per particle buffer: 7 real arrays, key, id.
+cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
+    const size_t rs = c->rsize;
+    const size_t cap = size_t(n < 1 ? 1 : n);
+    auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t per = align(cap * rs);
+    const size_t ints = align(cap * sizeof(int));
+    for (int b = 0; b < 2; ++b) {
+        char* base = nullptr;
+        cudaError_t e = cudaMalloc(&base, 7 * per + 2 * ints);
+        if (e != cudaSuccess) return e;
+        for (int i = 0; i < 7; ++i) c->P[b].a[i] = base + i * per;
+        c->P[b].key = reinterpret_cast<int*>(base + 7 * per);
+        c->P[b].id = reinterpret_cast<int*>(base + 7 * per + ints);
+    }
+    char* ob = nullptr;
+    cudaError_t e = cudaMalloc(&ob, 6 * per + ints);
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 6; ++i) c->old[i] = ob + i * per;
+    c->oldkey = reinterpret_cast<int*>(ob + 6 * per);
+    c->cap = int64_t(cap);
+    return cudaSuccess;
+}
+
+// ---- kernel launch bookkeeping (counts, optional timing) -------------------
+// In timing mode every launch is bracketed by a pair of events from a pool on
+// the context stream; the pairs are resolved into per-kernel totals when the
+// timings are read.
+struct PendingTiming {
+    cudaEvent_t a, b;
+    int timer;
+};
+std::vector<PendingTiming>& pending(pic_ctx* c);
+cudaEvent_t pool_event(pic_ctx* c);
+
+struct Launch {
+    pic_ctx* c;
+    int timer = -1;
+    cudaEvent_t a = nullptr;
+    Launch(pic_ctx* ctx, const char* name) : c(ctx) {
+        if (!c->timing) return;
+        for (int i = 0; i < c->ntimers; ++i)
+            if (std::strcmp(c->timers[i].name, name) == 0) timer = i;
+        if (timer < 0 && c->ntimers < 16) {
+            timer = c->ntimers++;
+            c->timers[timer] = {name, 0.0, 0};
+        }
+        a = pool_event(c);
+        if (a) cudaEventRecord(a, c->stream);
+    }
+    cudaError_t done(cudaError_t e) {
+        if (e != cudaSuccess || !c->timing || !a || timer < 0) return e;
+        cudaEvent_t b = pool_event(c);
+        if (!b) return e;
+        cudaEventRecord(b, c->stream);
+        pending(c).push_back({a, b, timer});
+        return e;
+    }
+};
+
+int g_capture_kernels = 0;
+bool g_capturing = false;
+
+cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)(pic_ctx*)) {
+    Launch l(c, name);
+    cudaError_t e = l.done(fn(c));
+    if (e == cudaSuccess) {
+        if (g_capturing) g_capture_kernels += kernels;
+        else c->launches += kernels;
+    }
+    return e;
+}
+
+cudaError_t run_sort(pic_ctx* c) {
+    cudaError_t e;
+    if ((e = counted(c, "k_hist", 1, pic::launch_hist)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_scan", 1, pic::launch_scan)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_scatter", 1, pic::launch_scatter)) != cudaSuccess) return e;
+    c->cur = 1 - c->cur;
+    return cudaSuccess;
+}
+
+cudaError_t yee_b_half(pic_ctx* c) { return pic::launch_yee_b(c, 0.5 * c->dt); }
+
+cudaError_t run_yee(pic_ctx* c) {
+    cudaError_t e;
+    if ((e = counted(c, "k_yee_b", 1, yee_b_half)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_yee_e", 1, pic::launch_yee_e)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_yee_b", 1, yee_b_half)) != cudaSuccess) return e;
+    return counted(c, "k_step_counter", 1, pic::launch_step_counter);
+}
+
+// One full step as queued work.  `with_sort` runs the counting sort first.
+cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
+    cudaError_t e;
+    if (with_sort && (e = run_sort(c)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_tile_step", 1, pic::launch_tile_step)) != cudaSuccess) return e;
+    return run_yee(c);
+}
+
+pic_status read_error_word(pic_ctx* c) {
+    unsigned h = 0;
+    PIC_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    if (h == 0) return PIC_OK;
+    PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    if (h & pic::ERRBIT_TIMEOUT) return fail(PIC_ERR_TIMEOUT, "a bounded device-side wait ran out");
+    if (h & pic::ERRBIT_RANGE) return fail(PIC_ERR_STATE, "a particle cell key was out of range");
+    return fail(PIC_ERR_PARTICLE, "a particle became non-finite or moved a cell or more in one step");
+}
+
+pic_status check_ctx(pic_ctx* c) {
+    if (!c) return fail(PIC_ERR_ARG, "null context");
+    return PIC_OK;
+}
+
+struct TimingState {
+    std::vector<PendingTiming> pend;
+    std::vector<cudaEvent_t> free_ev;
+    std::vector<cudaEvent_t> all;
+};
+
+TimingState& tstate(pic_ctx* c) {
+    if (!c->tstate) c->tstate = new TimingState();
+    return *static_cast<TimingState*>(c->tstate);
+}
+
+std::vector<PendingTiming>& pending(pic_ctx* c) { return tstate(c).pend; }
+
+cudaEvent_t pool_event(pic_ctx* c) {
+    TimingState& t = tstate(c);
+    if (t.free_ev.empty()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        t.all.push_back(e);
+        return e;
+    }
+    cudaEvent_t e = t.free_ev.back();
+    t.free_ev.pop_back();
+    return e;
+}
+
+// Call after the stream has drained.
+void resolve_timings(pic_ctx* c) {
+    if (!c->tstate) return;
+    TimingState& t = tstate(c);
+    for (const PendingTiming& p : t.pend) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess && p.timer < c->ntimers) {
+            c->timers[p.timer].ms += ms;
+            c->timers[p.timer].launches += 1;
+        }
+        t.free_ev.push_back(p.a);
+        t.free_ev.push_back(p.b);
+    }
+    t.pend.clear();
+}
+
+void destroy_timing(pic_ctx* c) {
+    if (!c->tstate) return;
+    TimingState& t = tstate(c);
+    for (cudaEvent_t e : t.all) cudaEventDestroy(e);
+    delete &t;
+    c->tstate = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pic_last_error(void) { return g_last_error.c_str(); }
+
+pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx** out) {
+    if (!out) return fail(PIC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!desc) return fail(PIC_ERR_ARG, "desc is NULL");
+    const pic_grid_desc& D = *desc;
+    if (D.order < 1 || D.order > 3) return fail(PIC_ERR_ARG, "order must be 1, 2 or 3");
+    if (D.precision != PIC_FP64 && D.precision != PIC_FP32_MIXED) return fail(PIC_ERR_ARG, "unknown precision");
+    if (D.sort_every < 1) return fail(PIC_ERR_ARG, "sort_every must be >= 1");
+    if (D.window_axis != -1) return fail(PIC_ERR_ARG, "moving window not supported by this entry point");
+    int64_t C = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (D.n[a] < D.order + 2 || D.n[a] < 3) return fail(PIC_ERR_ARG, "each extent must be >= order + 2 and >= 3");
+        if (!(D.d[a] > 0.0) || !std::isfinite(D.d[a])) return fail(PIC_ERR_ARG, "cell sizes must be finite and > 0");
+        C *= D.n[a];
+    }
+    if (C >= (int64_t(1) << 31)) return fail(PIC_ERR_ARG, "too many cells (limit 2^31 - 1)");
+    const double cfl_dt = 1.0 / std::sqrt(1.0 / (D.d[0] * D.d[0]) + 1.0 / (D.d[1] * D.d[1]) + 1.0 / (D.d[2] * D.d[2]));
+    double dt = D.dt;
+    if (dt == 0.0) {
+        if (!(D.cfl > 0.0 && D.cfl <= 1.0)) return fail(PIC_ERR_ARG, "cfl must be in (0, 1] when dt == 0");
+        dt = D.cfl * cfl_dt;
+    }
+    if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PIC_ERR_ARG, "dt must be finite and > 0");
+    if (dt > cfl_dt) return fail(PIC_ERR_CFL, "dt exceeds the Yee Courant limit 1/sqrt(sum 1/d^2)");
+
+    pic_ctx* c = new pic_ctx();
+    c->dt = dt;
+    c->prec = D.precision;
+    c->order = D.order;
+    c->sort_every = D.sort_every;
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+    c->rsize = D.precision == PIC_FP64 ? 8 : 4;
+    cudaGetDevice(&c->device);
+    pic::Geom& g = c->g;
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = D.n[a];
+        g.d[a] = D.d[a];
+        g.L[a] = D.n[a] * D.d[a];
+        int T = D.tile[a];
+        if (T == 0) {
+            T = 8;
+            while (T > 1 && D.n[a] % T != 0) T >>= 1;
+        }
+        if (!is_pow2(T) || D.n[a] % T != 0 || T > 64) {
+            delete c;
+            return fail(PIC_ERR_ARG, "tile extents must be powers of two (<= 64) dividing the grid");
+        }
+        g.T[a] = T;
+        g.lT[a] = ilog2(T);
+        g.nt[a] = D.n[a] / T;
+    }
+    g.cpt = g.T[0] * g.T[1] * g.T[2];
+    g.C = C;
+    g.ntiles = int64_t(g.nt[0]) * g.nt[1] * g.nt[2];
+
+    auto bail = [&](cudaError_t e, const char* what) {
+        pic_destroy(c);
+        return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, what) : cuda_fail(e, what);
+    };
+    cudaError_t e;
+    char* fb = nullptr;
+    if ((e = cudaMalloc(&fb, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field allocation");
+    for (int i = 0; i < 9; ++i) c->F[i] = fb + i * C * c->rsize;
+    if ((e = cudaMemset(fb, 0, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field zeroing");
+    if ((e = cudaMalloc(&c->count, C * sizeof(int))) != cudaSuccess) return bail(e, "count allocation");
+    if ((e = cudaMemset(c->count, 0, C * sizeof(int))) != cudaSuccess) return bail(e, "count zeroing");
+    if ((e = cudaMalloc(&c->offsets, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "offsets allocation");
+    if ((e = cudaMemset(c->offsets, 0, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "offsets zeroing");
+    c->scan_chunks = int(pic::scan_status_words(C) - 1);
+    if ((e = cudaMalloc(&c->scan_status, pic::scan_status_words(C) * sizeof(unsigned long long))) != cudaSuccess)
+        return bail(e, "scan state allocation");
+    if ((e = cudaMalloc(&c->err, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
+    if ((e = cudaMemset(c->err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaMalloc(&c->d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter allocation");
+    if ((e = cudaMemset(c->d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
+    if ((e = cudaMalloc(&c->dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");
+    *out = c;
+    return PIC_OK;
+}
+
+pic_status pic_destroy(pic_ctx* c) {
+    if (!c) return PIC_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_particles(c);
+    cudaFree(c->F[0]);
+    cudaFree(c->count);
+    cudaFree(c->offsets);
+    cudaFree(c->scan_status);
+    cudaFree(c->err);
+    cudaFree(c->d_step);
+    cudaFree(c->dsum);
+    destroy_timing(c);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    delete c;
+    return PIC_OK;
+}
+
+pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const double* x, const double* y,
+                              const double* z, const double* ux, const double* uy, const double* uz, const double* w,
+                              int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (n < 0 || n >= (int64_t(1) << 31)) return fail(PIC_ERR_ARG, "particle count must be in [0, 2^31)");
+    if (!std::isfinite(q) || !std::isfinite(m) || !(m > 0.0)) return fail(PIC_ERR_ARG, "q must be finite, m > 0");
+    const double* src[7] = {x, y, z, ux, uy, uz, w};
+    if (n > 0)
+        for (auto p : src)
+            if (!p) return fail(PIC_ERR_ARG, "particle array is NULL");
+    PIC_CUDA(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (n > c->cap || c->cap == 0) {
+        free_particles(c);
+        cudaError_t e = alloc_particles(c, n);
+        if (e != cudaSuccess) {
+            free_particles(c);
+            return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "particle allocation") : cuda_fail(e, "alloc");
+        }
+    }
+    c->q = q;
+    c->m = m;
+    c->np = n;
+    c->cur = 0;
+    c->have_old = false;
+    double* staged = nullptr;
+    const double* dsrc[7];
+    if (n > 0 && !on_device) {
+        PIC_CUDA(cudaMalloc(&staged, 7 * size_t(n) * sizeof(double)));
+        for (int i = 0; i < 7; ++i) {
+            cudaError_t e = cudaMemcpyAsync(staged + i * n, src[i], n * sizeof(double), cudaMemcpyHostToDevice,
+                                            c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(staged);
+                return cuda_fail(e, "particle upload");
+            }
+            dsrc[i] = staged + i * n;
+        }
+    } else {
+        for (int i = 0; i < 7; ++i) dsrc[i] = src[i];
+    }
+    PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    cudaError_t e = pic::launch_load_particles(c, dsrc, n);
+    if (e == cudaSuccess) c->launches += n > 0 ? 1 : 0;
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (staged) cudaFree(staged);
+    if (e != cudaSuccess) return cuda_fail(e, "particle load");
+    unsigned h = 0;
+    PIC_CUDA(cudaMemcpy(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (h) {
+        cudaMemset(c->err, 0, sizeof(unsigned));
+        c->np = 0;
+        return fail(PIC_ERR_ARG, "non-finite particle value");
+    }
+    e = run_sort(c);
+    if (e != cudaSuccess) return cuda_fail(e, "initial sort");
+    c->since_sort = 0;
+    c->sorted = true;
+    return read_error_word(c);
+}
+
+pic_status pic_gather_push(pic_ctx* c) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
+    PIC_CUDA(counted(c, "k_gather_push", 1, pic::launch_gather_push_global));
+    c->have_old = true;
+    return PIC_OK;
+}
+
+pic_status pic_deposit(pic_ctx* c) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!c->have_old) return fail(PIC_ERR_STATE, "pic_deposit needs a preceding pic_gather_push");
+    PIC_CUDA(counted(c, "k_deposit", 1, pic::launch_deposit_global));
+    return PIC_OK;
+}
+
+pic_status pic_yee_step(pic_ctx* c) {
+    if (pic_status s = check_ctx(c)) return s;
+    PIC_CUDA(run_yee(c));
+    c->step += 1;
+    c->since_sort += 1;
+    return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx* c, int32_t nsteps) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (nsteps < 0) return fail(PIC_ERR_ARG, "nsteps < 0");
+    if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
+    int32_t left = nsteps;
+    // With a sort every step, two consecutive steps return the particle
+    // double buffer to its starting role, so a captured pair of steps can be
+    // replayed as one graph launch.
+    const bool use_graph = c->stream != nullptr && !c->timing && c->sort_every == 1;
+    if (use_graph) {
+        while (left >= 2) {
+            if (!c->graph || c->graph_cur != c->cur) {
+                if (c->graph) {
+                    cudaGraphExecDestroy(c->graph);
+                    c->graph = nullptr;
+                }
+                const int cur0 = c->cur;
+                PIC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+                g_capturing = true;
+                g_capture_kernels = 0;
+                cudaError_t e1 = enqueue_step(c, true);
+                if (e1 == cudaSuccess) e1 = enqueue_step(c, true);
+                g_capturing = false;
+                cudaGraph_t graph = nullptr;
+                cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
+                c->cur = cur0;
+                if (e1 != cudaSuccess) {
+                    if (graph) cudaGraphDestroy(graph);
+                    return cuda_fail(e1, "step capture");
+                }
+                if (e2 != cudaSuccess) return cuda_fail(e2, "end capture");
+                cudaError_t e3 = cudaGraphInstantiate(&c->graph, graph, 0);
+                cudaGraphDestroy(graph);
+                if (e3 != cudaSuccess) return cuda_fail(e3, "graph instantiate");
+                c->graph_cur = cur0;
+                c->graph_kernels = g_capture_kernels;
+            }
+            PIC_CUDA(cudaGraphLaunch(c->graph, c->stream));
+            c->launches += c->graph_kernels;
+            c->step += 2;
+            c->since_sort = 1;
+            left -= 2;
+        }
+    }
+    for (; left > 0; --left) {
+        const bool sort_now = c->since_sort >= c->sort_every;
+        PIC_CUDA(enqueue_step(c, sort_now));
+        if (sort_now) c->since_sort = 0;
+        c->since_sort += 1;
+        c->step += 1;
+    }
+    c->have_old = false;
+    return read_error_word(c);
+}
+
+pic_status pic_get_field(pic_ctx* c, int32_t which, double* dst, int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (which < 0 || which > 8 || !dst) return fail(PIC_ERR_ARG, "bad field index or NULL destination");
+    const size_t bytes = c->g.C * sizeof(double);
+    if (on_device) {
+        PIC_CUDA(pic::launch_field_to_f64(c, which, dst));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    if (c->prec == PIC_FP64) {
+        PIC_CUDA(cudaMemcpyAsync(dst, c->F[which], bytes, cudaMemcpyDeviceToHost, c->stream));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    double* tmp = nullptr;
+    PIC_CUDA(cudaMalloc(&tmp, bytes));
+    cudaError_t e = pic::launch_field_to_f64(c, which, tmp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "get field");
+    return PIC_OK;
+}
+
+pic_status pic_set_field(pic_ctx* c, int32_t which, const double* src, int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (which < 0 || which > 8 || !src) return fail(PIC_ERR_ARG, "bad field index or NULL source");
+    const size_t bytes = c->g.C * sizeof(double);
+    if (on_device) {
+        PIC_CUDA(pic::launch_field_from_f64(c, which, src));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    if (c->prec == PIC_FP64) {
+        PIC_CUDA(cudaMemcpyAsync(c->F[which], src, bytes, cudaMemcpyHostToDevice, c->stream));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    double* tmp = nullptr;
+    PIC_CUDA(cudaMalloc(&tmp, bytes));
+    cudaError_t e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = pic::launch_field_from_f64(c, which, tmp);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "set field");
+    return PIC_OK;
+}
+
+pic_status pic_num_particles(pic_ctx* c, int64_t* n) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!n) return fail(PIC_ERR_ARG, "NULL output");
+    *n = c->np;
+    return PIC_OK;
+}
+
+pic_status pic_get_particles(pic_ctx* c, double* x, double* y, double* z, double* ux, double* uy, double* uz,
+                             double* w, int32_t* id, int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    double* dst[7] = {x, y, z, ux, uy, uz, w};
+    if (c->np == 0) return PIC_OK;
+    if (on_device) {
+        PIC_CUDA(pic::launch_get_particles(c, dst, id));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+        return PIC_OK;
+    }
+    const int64_t n = c->np;
+    char* tmp = nullptr;
+    PIC_CUDA(cudaMalloc(&tmp, 7 * n * sizeof(double) + n * sizeof(int32_t)));
+    double* ddst[7];
+    for (int i = 0; i < 7; ++i) ddst[i] = dst[i] ? reinterpret_cast<double*>(tmp) + i * n : nullptr;
+    int32_t* did = id ? reinterpret_cast<int32_t*>(tmp + 7 * n * sizeof(double)) : nullptr;
+    cudaError_t e = pic::launch_get_particles(c, ddst, did);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+        if (dst[i]) e = cudaMemcpyAsync(dst[i], ddst[i], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && id) e = cudaMemcpyAsync(id, did, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(e, "get particles");
+    return PIC_OK;
+}
+
+pic_status pic_set_external_drive(pic_ctx* c, double amp, double k) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!std::isfinite(amp) || !std::isfinite(k)) return fail(PIC_ERR_ARG, "drive parameters must be finite");
+    c->drive_amp = amp;
+    c->drive_k = k;
+    if (c->graph) {  // kernel arguments are baked into the graph
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    return PIC_OK;
+}
+
+pic_status pic_get_time(pic_ctx* c, int64_t* steps, double* t) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (steps) *steps = c->step;
+    if (t) *t = double(c->step) * c->dt;
+    return PIC_OK;
+}
+
+pic_status pic_diagnostics(pic_ctx* c, double out[4]) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!out) return fail(PIC_ERR_ARG, "NULL output");
+    PIC_CUDA(cudaMemsetAsync(c->dsum, 0, 8 * sizeof(double), c->stream));
+    PIC_CUDA(pic::launch_diagnostics(c, c->dsum));
+    c->launches += c->np > 0 ? 3 : 2;
+    double h[4];
+    PIC_CUDA(cudaMemcpyAsync(h, c->dsum, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    const double dV = c->g.d[0] * c->g.d[1] * c->g.d[2];
+    out[0] = h[0] * dV;
+    out[1] = h[1];
+    out[2] = h[2];
+    unsigned long long bits;
+    std::memcpy(&bits, &h[3], sizeof(bits));
+    double mx;
+    std::memcpy(&mx, &bits, sizeof(mx));
+    out[3] = mx;
+    return read_error_word(c);
+}
+
+pic_status pic_sync(pic_ctx* c) {
+    if (pic_status s = check_ctx(c)) return s;
+    return read_error_word(c);
+}
+
+pic_status pic_set_timing(pic_ctx* c, int32_t on) {
+    if (pic_status s = check_ctx(c)) return s;
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    resolve_timings(c);
+    c->timing = on != 0;
+    c->ntimers = 0;
+    return PIC_OK;
+}
+
+pic_status pic_get_timing(pic_ctx* c, int32_t cap, const char** names, double* ms, int64_t* launches,
+                          int32_t* count) {
+    if (pic_status s = check_ctx(c)) return s;
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    resolve_timings(c);
+    for (int i = 0; i < c->ntimers && i < cap; ++i) {
+        if (names) names[i] = c->timers[i].name;
+        if (ms) ms[i] = c->timers[i].ms;
+        if (launches) launches[i] = c->timers[i].launches;
+    }
+    if (count) *count = c->ntimers;
+    return PIC_OK;
+}
+
+pic_status pic_launch_count(pic_ctx* c, int64_t* n) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!n) return fail(PIC_ERR_ARG, "NULL output");
+    *n = c->launches;
+    return PIC_OK;
+}
+
+}  // extern "C"

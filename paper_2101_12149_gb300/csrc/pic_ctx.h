@@ -1,0 +1,117 @@
+// Host-side context of libpic and the launchers shared between its
+// translation units.  Not part of the public C-ABI (see include/pic.h).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+// Error bits of the device error word.
+enum : unsigned {
+    ERRBIT_PARTICLE = 1u,  // non-finite particle or a move of >= 1 cell
+    ERRBIT_TIMEOUT = 2u,   // a bounded wait ran out
+    ERRBIT_RANGE = 4u,     // a sort key outside [0, C)
+};
+
+// Particle storage (structure of arrays).  FP64: a[0..6] = x,y,z,ux,uy,uz,w
+// (double), key = tile-major cell key.  FP32-mixed: key = tile-major cell key
+// (the integer part of the position), a[0..6] = ox,oy,oz (in-cell offsets in
+// [0,1)), ux,uy,uz, w (float).  id = load index.
+struct PartBuf {
+    void* a[7] = {nullptr};
+    int* key = nullptr;
+    int* id = nullptr;
+};
+
+// Grid geometry shared by all kernels.
+struct Geom {
+    int n[3];      // cells per axis
+    int T[3];      // cells per tile per axis (powers of two)
+    int lT[3];     // log2 T
+    int nt[3];     // tiles per axis
+    int cpt;       // cells per tile
+    int64_t C;     // cells
+    int64_t ntiles;
+    double d[3];
+    double L[3];
+};
+
+struct Timer {
+    const char* name;
+    double ms;
+    int64_t launches;
+};
+
+}  // namespace pic
+
+struct pic_ctx {
+    pic::Geom g;
+    double dt = 0.0;
+    int prec = PIC_FP64;
+    int order = 1;
+    int sort_every = 1;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    size_t rsize = 8;  // bytes per real (8 FP64, 4 FP32-mixed)
+
+    void* F[9] = {nullptr};  // Ex Ey Ez Bx By Bz Jx Jy Jz
+
+    int64_t np = 0, cap = 0;
+    double q = 0.0, m = 1.0;
+    pic::PartBuf P[2];
+    int cur = 0;
+    void* old[3] = {nullptr};  // FP64: x0,y0,z0; FP32-mixed: offsets of the old position
+    int* oldkey = nullptr;     // FP32-mixed: key of the old position
+    bool have_old = false;
+
+    int* count = nullptr;    // per-cell particle counts [C]
+    int* offsets = nullptr;  // exclusive scan of count [C+1]; tile t owns [offsets[t*cpt], offsets[(t+1)*cpt])
+    unsigned long long* scan_status = nullptr;  // look-back words + ticket
+    int scan_chunks = 0;
+    bool sorted = false;       // particles are in tile order of the current offsets
+    int since_sort = 0;
+
+    unsigned* err = nullptr;       // device error word
+    long long* d_step = nullptr;   // device copy of the step counter (drive time)
+    double* dsum = nullptr;        // diagnostics scratch
+    int64_t step = 0;
+    double drive_amp = 0.0, drive_k = 0.0;
+
+    bool timing = false;
+    pic::Timer timers[16];
+    int ntimers = 0;
+    void* tstate = nullptr;  // pending event pairs and the event pool
+
+    cudaGraphExec_t graph = nullptr;
+    int graph_cur = 0;
+    int graph_kernels = 0;
+    int64_t launches = 0;
+};
+
+namespace pic {
+
+// launchers (pic_kernels.cu)
+cudaError_t launch_zero_fields(pic_ctx* c, int first, int count);
+cudaError_t launch_tile_step(pic_ctx* c);        // fused gather+push+deposit, tile kernel
+cudaError_t launch_gather_push_global(pic_ctx* c);
+cudaError_t launch_deposit_global(pic_ctx* c);
+cudaError_t launch_yee_b(pic_ctx* c, double h);
+cudaError_t launch_yee_e(pic_ctx* c);
+cudaError_t launch_step_counter(pic_ctx* c);
+cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n);
+cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id);
+cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst);
+cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src);
+cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
+
+// sort (pic_sort.cu)
+cudaError_t launch_hist(pic_ctx* c);
+cudaError_t launch_scan(pic_ctx* c);
+cudaError_t launch_scatter(pic_ctx* c);
+size_t scan_status_words(int64_t C);
+
+}  // namespace pic

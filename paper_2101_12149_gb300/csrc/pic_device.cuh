@@ -1,0 +1,168 @@
+// Device building blocks of the PIC hot path: shape weights, Boris push,
+// Esirkepov current weights.  Templated on the arithmetic type R (double for
+// the FP64 path, float for FP32-mixed) and the shape order P (1..3).
+//
+// Positions enter as (integer node, fraction) pairs in cell units, so the
+// same code serves the FP64 path (fraction = x/dx - floor(x/dx), exact) and
+// the FP32-mixed path (int32 cell + float in-cell offset).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "pic_ctx.h"
+
+namespace pic {
+
+__device__ __forceinline__ void raise_error(unsigned* err, unsigned bit) { atomicOr(err, bit); }
+
+__device__ __forceinline__ int wrap_once(int i, int n) {
+    // i is within one period of [0, n)
+    return i < 0 ? i + n : (i >= n ? i - n : i);
+}
+
+__device__ __forceinline__ int wrap_any(int i, int n) {
+    // any i, n > 0
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename R> __device__ __forceinline__ R rfloor(R v);
+template <> __device__ __forceinline__ double rfloor<double>(double v) { return floor(v); }
+template <> __device__ __forceinline__ float rfloor<float>(float v) { return floorf(v); }
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R v);
+template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
+
+// ---------------------------------------------------------------------------
+// Order-P cardinal B-spline weights.
+//
+// A position at node i0 + f (f in [0,1)) has non-zero weights on P+1
+// consecutive nodes.  `first` receives the first node relative to i0 and
+// w[0..P] the weights s_P(i0 + f - node).  The pieces are the B-spline's
+// polynomial pieces written in f.
+// ---------------------------------------------------------------------------
+template <int P, typename R> struct Shape;
+
+template <typename R> struct Shape<1, R> {
+    __device__ __forceinline__ static void weights(R f, int& first, R w[2]) {
+        first = 0;
+        w[0] = R(1) - f;
+        w[1] = f;
+    }
+};
+
+template <typename R> struct Shape<2, R> {
+    __device__ __forceinline__ static void weights(R f, int& first, R w[3]) {
+        // nearest node c (0 or 1), g = f - c in [-1/2, 1/2)
+        const bool up = f >= R(0.5);
+        const R g = up ? f - R(1) : f;
+        first = up ? 0 : -1;
+        const R a = R(0.5) - g, b = R(0.5) + g;
+        w[0] = R(0.5) * a * a;
+        w[1] = R(0.75) - g * g;
+        w[2] = R(0.5) * b * b;
+    }
+};
+
+template <typename R> struct Shape<3, R> {
+    __device__ __forceinline__ static void weights(R f, int& first, R w[4]) {
+        first = -1;
+        const R f2 = f * f, f3 = f2 * f;
+        const R g = R(1) - f;
+        const R sixth = R(1) / R(6);
+        w[0] = g * g * g * sixth;
+        w[1] = (R(4) - R(6) * f2 + R(3) * f3) * sixth;
+        w[2] = (R(1) + R(3) * f + R(3) * f2 - R(3) * f3) * sixth;
+        w[3] = f3 * sixth;
+    }
+};
+
+// Weights for a component staggered by half a cell along this axis: the
+// position relative to the staggered lattice is (i0 + f) - 1/2.
+template <int P, typename R>
+__device__ __forceinline__ void staggered_weights(R f, int& first, R w[P + 1]) {
+    const bool hi = f >= R(0.5);
+    const R g = hi ? f - R(0.5) : f + R(0.5);
+    Shape<P, R>::weights(g, first, w);
+    if (!hi) first -= 1;
+}
+
+// ---------------------------------------------------------------------------
+// Relativistic Boris push (u = gamma v):
+//   k = q dt / (2 m);  u- = u + k E;  g- = sqrt(1 + |u-|^2);  t = k B / g-;
+//   s = 2 t / (1 + |t|^2);  u' = u- + u- x t;  u+ = u- + u' x s;  u = u+ + k E.
+// The FP32 instantiation switches to FP64 for g-, t, s and the rotation when
+// g- > 1e3 (ultra-relativistic particles).
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ void boris_rotate(R k, const R B[3], R um[3], R gm) {
+    const R t0 = k * B[0] / gm, t1 = k * B[1] / gm, t2 = k * B[2] / gm;
+    const R tt = t0 * t0 + t1 * t1 + t2 * t2;
+    const R sc = R(2) / (R(1) + tt);
+    const R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;
+    const R p0 = um[0] + (um[1] * t2 - um[2] * t1);
+    const R p1 = um[1] + (um[2] * t0 - um[0] * t2);
+    const R p2 = um[2] + (um[0] * t1 - um[1] * t0);
+    um[0] += p1 * s2 - p2 * s1;
+    um[1] += p2 * s0 - p0 * s2;
+    um[2] += p0 * s1 - p1 * s0;
+}
+
+template <typename R>
+__device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
+    R um[3] = {u[0] + k * E[0], u[1] + k * E[1], u[2] + k * E[2]};
+    const R g2 = R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
+    if (sizeof(R) == 4 && g2 > R(1e6)) {
+        double umd[3] = {double(um[0]), double(um[1]), double(um[2])};
+        const double Bd[3] = {double(B[0]), double(B[1]), double(B[2])};
+        const double gmd = sqrt(1.0 + umd[0] * umd[0] + umd[1] * umd[1] + umd[2] * umd[2]);
+        boris_rotate<double>(double(k), Bd, umd, gmd);
+        um[0] = R(umd[0]);
+        um[1] = R(umd[1]);
+        um[2] = R(umd[2]);
+    } else {
+        boris_rotate<R>(k, B, um, rsqrt_<R>(g2));
+    }
+    u[0] = um[0] + k * E[0];
+    u[1] = um[1] + k * E[1];
+    u[2] = um[2] + k * E[2];
+}
+
+// ---------------------------------------------------------------------------
+// Esirkepov (2001) weights along one axis.
+//
+// The particle moves from i0 + f0 to i0 + f1 (cell units, |f1 - f0| < 1).
+// The common window of P+2 nodes starts at node i0 + b with
+// b = floor(min(f0,f1) - (P+1)/2) + 1; S0 / dS hold s_P at the old position
+// and the change s_P(new) - s_P(old) on the window.  Both shapes start at
+// window slot 0 or 1, placed with selects so the arrays stay in registers.
+// ---------------------------------------------------------------------------
+template <int P, typename R> struct EsirkAxis {
+    static constexpr int NW = P + 2;
+    int b;
+    R S0[NW];
+    R dS[NW];
+
+    __device__ __forceinline__ void init(R f0, R f1) {
+        const R mn = f0 < f1 ? f0 : f1;
+        b = int(rfloor<R>(mn - R(0.5) * R(P + 1))) + 1;
+        int first0, first1;
+        R w0[P + 1], w1[P + 1];
+        Shape<P, R>::weights(f0, first0, w0);
+        const R fl1 = rfloor<R>(f1);
+        const int i1 = int(fl1);
+        Shape<P, R>::weights(f1 - fl1, first1, w1);
+        const int off0 = first0 - b;       // 0 or 1
+        const int off1 = i1 + first1 - b;  // 0 or 1
+#pragma unroll
+        for (int a = 0; a < NW; ++a) {
+            const R s0 = off0 == 0 ? (a <= P ? w0[a] : R(0)) : (a >= 1 ? w0[a - 1] : R(0));
+            const R s1 = off1 == 0 ? (a <= P ? w1[a] : R(0)) : (a >= 1 ? w1[a - 1] : R(0));
+            S0[a] = s0;
+            dS[a] = s1 - s0;
+        }
+    }
+};
+
+}  // namespace pic

@@ -1,0 +1,1119 @@
+// Particle and field kernels of libpic (sm_103a).
+//
+//  k_tile_step      fused gather + Boris + advance + Esirkepov for one tile
+//                   of cells per CTA: E/B of the tile and its halo staged in
+//                   shared memory, J accumulated in shared memory, one
+//                   vectorised atomic flush per tile (Sec. 3.1 fuses gather
+//                   and push; Sec. 3.4 discusses shared-memory buffers).
+//  k_gather_push    one particle per thread, fields read from global memory.
+//  k_deposit        one particle per thread, Esirkepov with global atomics
+//                   (the paper's GPU deposit, Sec. 3.4.1).
+//  k_yee_b/k_yee_e  Yee FDTD half-step of B / full step of E (Sec. 2.4).
+//  conversions, particle load/store, diagnostics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pic_ctx.h"
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr int kBlock = 256;
+
+// ---------------------------------------------------------------------------
+// cell keys: tile-major, k fastest inside a tile
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int key_of(const Geom& g, int i, int j, int k) {
+    const int ti = i >> g.lT[0], tj = j >> g.lT[1], tk = k >> g.lT[2];
+    const int li = i & (g.T[0] - 1), lj = j & (g.T[1] - 1), lk = k & (g.T[2] - 1);
+    const int t = (ti * g.nt[1] + tj) * g.nt[2] + tk;
+    const int l = (li << (g.lT[1] + g.lT[2])) | (lj << g.lT[2]) | lk;
+    return t * g.cpt + l;
+}
+
+__device__ __forceinline__ void tile_origin(const Geom& g, int t, int& oi, int& oj, int& ok) {
+    const int tk = t % g.nt[2];
+    const int r = t / g.nt[2];
+    const int tj = r % g.nt[1];
+    const int ti = r / g.nt[1];
+    oi = ti << g.lT[0];
+    oj = tj << g.lT[1];
+    ok = tk << g.lT[2];
+}
+
+__device__ __forceinline__ void cell_of(const Geom& g, int key, int& i, int& j, int& k) {
+    const int lcpt = g.lT[0] + g.lT[1] + g.lT[2];
+    const int t = key >> lcpt, l = key & (g.cpt - 1);
+    int oi, oj, ok;
+    tile_origin(g, t, oi, oj, ok);
+    i = oi + (l >> (g.lT[1] + g.lT[2]));
+    j = oj + ((l >> g.lT[2]) & (g.T[1] - 1));
+    k = ok + (l & (g.T[2] - 1));
+}
+
+// Periodic wrap of a position: x >= L -> x - L, x < 0 -> x + L, and a value
+// that rounds to L maps to 0.
+__device__ __forceinline__ double wrap_pos(double x, double L) {
+    if (x >= L) x -= L;
+    else if (x < 0.0) x += L;
+    if (x >= L) x = 0.0;
+    return x;
+}
+
+// ---------------------------------------------------------------------------
+// kernel arguments
+// ---------------------------------------------------------------------------
+template <typename R> struct StepArgs {
+    Geom g;
+    R kq;        // q dt / (2 m)
+    R dtc[3];    // dt / d  (FP32-mixed: cell units per unit velocity)
+    R jc[3];     // -q / (dt * d_t1 * d_t2): current per unit weight and unit Esirkepov sum
+    double dt;
+    const R* E[3];
+    const R* B[3];
+    R* J[3];
+    R* pa[7];    // particle arrays (see PartBuf)
+    int* key;
+    R* old[6];   // split API: old position (3) and displacement (3)
+    int* oldkey;
+    const int* offsets;
+    unsigned* err;
+    const long long* step;
+    double drive_amp, drive_k;
+    int64_t np;
+};
+
+template <typename R> StepArgs<R> make_args(pic_ctx* c) {
+    StepArgs<R> a;
+    a.g = c->g;
+    a.kq = R(c->q * c->dt / (2.0 * c->m));
+    for (int d = 0; d < 3; ++d) {
+        a.dtc[d] = R(c->dt / c->g.d[d]);
+        const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+        a.jc[d] = R(-c->q / (c->dt * c->g.d[t1] * c->g.d[t2]));
+        a.E[d] = static_cast<const R*>(c->F[d]);
+        a.B[d] = static_cast<const R*>(c->F[3 + d]);
+        a.J[d] = static_cast<R*>(c->F[6 + d]);
+    }
+    a.dt = c->dt;
+    const PartBuf& P = c->P[c->cur];
+    for (int i = 0; i < 7; ++i) a.pa[i] = static_cast<R*>(P.a[i]);
+    a.key = P.key;
+    for (int i = 0; i < 6; ++i) a.old[i] = static_cast<R*>(c->old[i]);
+    a.oldkey = c->oldkey;
+    a.offsets = c->offsets;
+    a.err = c->err;
+    a.step = c->d_step;
+    a.drive_amp = c->drive_amp;
+    a.drive_k = c->drive_k;
+    a.np = c->np;
+    return a;
+}
+
+// ---------------------------------------------------------------------------
+// field sources / current targets: offset tables per axis, plain or wrapped
+// ---------------------------------------------------------------------------
+template <int P, typename R>
+__device__ __forceinline__ R interp(const R* __restrict__ F, const int* ox, const int* oy, const int* oz,
+                                    const R* wx, const R* wy, const R* wz) {
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+        R ay = R(0);
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+            R az = R(0);
+            const R* row = F + ox[i] + oy[j];
+#pragma unroll
+            for (int k = 0; k <= P; ++k) az += wz[k] * row[oz[k]];
+            ay += wy[j] * az;
+        }
+        acc += wx[i] * ay;
+    }
+    return acc;
+}
+
+// Per-axis gather weights and offsets for node-centred (n) and staggered (s)
+// components.  Offsets are element offsets into the source arrays.
+template <int P, typename R> struct GatherW {
+    R wn[3][P + 1], ws[3][P + 1];
+    int on[3][P + 1], os[3][P + 1];
+};
+
+// Momentum-conserving gather of E and B (order P along every axis at each
+// component's staggered location).
+template <int P, typename R>
+__device__ __forceinline__ void gather6(const GatherW<P, R>& G, const R* const E[3], const R* const B[3], R EB[6]) {
+    EB[0] = interp<P, R>(E[0], G.os[0], G.on[1], G.on[2], G.ws[0], G.wn[1], G.wn[2]);
+    EB[1] = interp<P, R>(E[1], G.on[0], G.os[1], G.on[2], G.wn[0], G.ws[1], G.wn[2]);
+    EB[2] = interp<P, R>(E[2], G.on[0], G.on[1], G.os[2], G.wn[0], G.wn[1], G.ws[2]);
+    EB[3] = interp<P, R>(B[0], G.on[0], G.os[1], G.os[2], G.wn[0], G.ws[1], G.ws[2]);
+    EB[4] = interp<P, R>(B[1], G.os[0], G.on[1], G.os[2], G.ws[0], G.wn[1], G.ws[2]);
+    EB[5] = interp<P, R>(B[2], G.os[0], G.os[1], G.on[2], G.ws[0], G.ws[1], G.wn[2]);
+}
+
+// Weights from the in-cell fractions; offsets either into a staged tile
+// (cell at local index l + halo, strides st) or into the global arrays with
+// periodic wrap.
+template <int P, typename R>
+__device__ __forceinline__ void gather_weights(const R f[3], GatherW<P, R>& G, int first_n[3], int first_s[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        Shape<P, R>::weights(f[a], first_n[a], G.wn[a]);
+        staggered_weights<P, R>(f[a], first_s[a], G.ws[a]);
+    }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void offsets_local(GatherW<P, R>& G, const int base[3], const int st[3],
+                                              const int first_n[3], const int first_s[3]) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int r = 0; r <= P; ++r) {
+            G.on[a][r] = (base[a] + first_n[a] + r) * st[a];
+            G.os[a][r] = (base[a] + first_s[a] + r) * st[a];
+        }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void offsets_global(GatherW<P, R>& G, const Geom& g, const int cell[3],
+                                               const int first_n[3], const int first_s[3]) {
+    const int st[3] = {g.n[1] * g.n[2], g.n[2], 1};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int r = 0; r <= P; ++r) {
+            G.on[a][r] = wrap_once(cell[a] + first_n[a] + r, g.n[a]) * st[a];
+            G.os[a][r] = wrap_once(cell[a] + first_s[a] + r, g.n[a]) * st[a];
+        }
+}
+
+// Current target in the global arrays: node (cell + b + slot) per axis,
+// wrapped periodically (the "SumBoundary" fold of Sec. 2.4 on one box).
+template <int P, typename R> struct JTarget {
+    R* J[3];
+    int cx, cy, cz;  // first window node per axis (unwrapped)
+    int nx, ny, nz;
+    __device__ __forceinline__ void add(int c, int i, int j, int k, R v) const {
+        const int gi = wrap_once(cx + i, nx), gj = wrap_once(cy + j, ny), gk = wrap_once(cz + k, nz);
+        atomicAdd(J[c] + ((int64_t)gi * ny + gj) * nz + gk, v);
+    }
+};
+
+// Esirkepov deposit of one particle: J_c at slot (i,j,k) of the window gets
+// coef_c * (sum over the cumulative axis of dS) * Q over the transverse axes,
+// Q(a,b) = S0a S0b + dSa S0b/2 + S0a dSb/2 + dSa dSb/3.  The last slot of the
+// cumulative sum is zero (sum of dS vanishes) and is not written.
+template <int P, typename R>
+__device__ __forceinline__ void esirkepov_deposit(const EsirkAxis<P, R>* ax, const R* coef,
+                                                  const JTarget<P, R>& t) {
+    constexpr int NW = P + 2;
+    R A[3][NW], Bq[3][NW];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            A[a][w] = ax[a].S0[w] + R(0.5) * ax[a].dS[w];
+            Bq[a][w] = R(0.5) * ax[a].S0[w] + R(1.0 / 3.0) * ax[a].dS[w];
+        }
+    // J_x: cumulative along x, transverse y, z
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const R Q = ax[1].S0[j] * A[2][k] + ax[1].dS[j] * Bq[2][k];
+#pragma unroll
+                for (int i = 0; i < NW - 1; ++i) t.add(0, i, j, k, cum[i] * Q);
+            }
+    }
+    // J_y: cumulative along y, transverse x, z
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const R Q = ax[0].S0[i] * A[2][k] + ax[0].dS[i] * Bq[2][k];
+#pragma unroll
+                for (int j = 0; j < NW - 1; ++j) t.add(1, i, j, k, cum[j] * Q);
+            }
+    }
+    // J_z: cumulative along z, transverse x, y
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                const R Q = ax[0].S0[i] * A[1][j] + ax[0].dS[i] * Bq[1][j];
+#pragma unroll
+                for (int k = 0; k < NW - 1; ++k) t.add(2, i, j, k, cum[k] * Q);
+            }
+    }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void jtarget_global(JTarget<P, R>& t, const Geom& g, R* const J[3], const int cell[3],
+                                               const EsirkAxis<P, R>* ax) {
+    for (int c = 0; c < 3; ++c) t.J[c] = J[c];
+    t.cx = cell[0] + ax[0].b;
+    t.cy = cell[1] + ax[1].b;
+    t.cz = cell[2] + ax[2].b;
+    t.nx = g.n[0];
+    t.ny = g.n[1];
+    t.nz = g.n[2];
+}
+
+// ---------------------------------------------------------------------------
+// particle state access (FP64 and FP32-mixed)
+// ---------------------------------------------------------------------------
+// FP64: positions are global coordinates; cell = floor(x/d), fraction exact.
+__device__ __forceinline__ void split_pos(double x, double d, int n, int& cell, double& f) {
+    const double p = x / d;
+    double fl = floor(p);
+    int c = int(fl);
+    if (c >= n) c = n - 1, fl = double(n - 1);
+    if (c < 0) c = 0, fl = 0.0;
+    cell = c;
+    f = p - fl;
+}
+
+// One particle through gather, push and advance.  `f0` is the fraction
+// inside the old cell, `f1` the new position relative to the old cell (cell
+// units).  For FP64 the advance is done in global coordinates with the same
+// operation order as the definition (x += (dt u) / gamma), then f1 follows
+// exactly from the new global position.
+template <typename R> struct Moved {
+    R u[3];
+    R f0[3], f1[3];
+    double xg1[3];  // FP64: unwrapped new global position
+    bool ok;
+};
+
+template <int P, typename R>
+__device__ __forceinline__ void push_particle(const StepArgs<R>& A, R EB[6], const int cell[3], const R f0[3],
+                                              const double xg0[3], R u[3], Moved<R>& mv) {
+    if (A.drive_amp != 0.0) {
+        const double t = double(*A.step) * A.dt;
+        const double xp = sizeof(R) == 8 ? xg0[0] : (double(cell[0]) + double(f0[0])) * A.g.d[0];
+        EB[1] += R(A.drive_amp * cos(A.drive_k * xp - A.drive_k * t));
+    }
+    boris<R>(A.kq, EB, EB + 3, u);
+    mv.ok = true;
+    if (sizeof(R) == 8) {
+        const double gi = 1.0 / sqrt(1.0 + double(u[0]) * double(u[0]) + double(u[1]) * double(u[1]) +
+                                     double(u[2]) * double(u[2]));
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double dx = __dmul_rn(__dmul_rn(A.dt, double(u[a])), gi);
+            mv.xg1[a] = __dadd_rn(xg0[a], dx);
+            const double p1 = mv.xg1[a] / A.g.d[a];
+            mv.f1[a] = R(p1 - double(cell[a]));
+            mv.f0[a] = f0[a];
+            if (!(fabs(double(mv.f1[a] - f0[a])) < 1.0)) mv.ok = false;
+        }
+    } else {
+        const R gi = R(1) / rsqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            mv.f0[a] = f0[a];
+            mv.f1[a] = f0[a] + A.dtc[a] * u[a] * gi;
+            mv.xg1[a] = 0.0;
+            if (!(fabsf(float(mv.f1[a] - f0[a])) < 1.0f)) mv.ok = false;
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) mv.u[a] = u[a];
+}
+
+// New cell and fraction of a move, FP32-mixed: cell += floor(f1), f -= floor(f1),
+// cell wrapped periodically.
+__device__ __forceinline__ void renormalise(float f1, int cell, int n, int& ncell, float& nf) {
+    const float fl = floorf(f1);
+    float f = f1 - fl;
+    int c = cell + int(fl);
+    if (f >= 1.0f) { f -= 1.0f; c += 1; }
+    ncell = wrap_once(c, n);
+    nf = f;
+}
+
+// Slow paths of the tile kernel for a particle whose cell lies outside the
+// CTA's tile (possible only between sorts): global gather / global atomics.
+// Kept out of line so they do not add to the register pressure of the
+// shared-memory fast path.
+template <int P, typename R>
+__device__ __noinline__ void gather_global_slow(const StepArgs<R>& A, const int cell[3], const R f0[3], R EB[6]) {
+    GatherW<P, R> G;
+    int fn[3], fs[3];
+    gather_weights<P, R>(f0, G, fn, fs);
+    offsets_global<P, R>(G, A.g, cell, fn, fs);
+    gather6<P, R>(G, A.E, A.B, EB);
+}
+
+template <int P, typename R>
+__device__ __noinline__ void deposit_global_slow(const StepArgs<R>& A, const int cell[3], const EsirkAxis<P, R>* ax,
+                                                  const R* coef) {
+    JTarget<P, R> jt;
+    jtarget_global<P, R>(jt, A.g, A.J, cell, ax);
+    esirkepov_deposit<P, R>(ax, coef, jt);
+}
+
+// ---------------------------------------------------------------------------
+// fused tile kernel
+// ---------------------------------------------------------------------------
+// Shared-memory layout of one tile, sized for the largest tile (8 cells per
+// axis); smaller tiles use the low corner of the same boxes, so all strides
+// are compile-time constants and every shared access is base + immediate.
+//   E/B box: cells [-2, T+2) per axis  -> 12 x 12 x 12 per component
+//   J box:   x, y [-2, T+3), z [-4, T+4) -> 13 x 13 x 16 per component
+// (z padded so the flush moves aligned float4s).
+constexpr int kMaxTile = 8;
+constexpr int kSE = kMaxTile + 4;
+constexpr int kSEx = kSE * kSE, kSEy = kSE;
+constexpr int kSEvol = kSE * kSE * kSE;
+constexpr int kSJxy = kMaxTile + 5;
+constexpr int kSJz = kMaxTile + 8;
+constexpr int kSJx = kSJxy * kSJz, kSJy = kSJz;
+constexpr int kSJvol = kSJxy * kSJxy * kSJz;
+
+template <typename R> constexpr size_t tile_smem_bytes() { return sizeof(R) * (6 * size_t(kSEvol) + 3 * size_t(kSJvol)); }
+
+// Gather of one component from the staged box: `base` points at the first
+// stencil node; strides are compile-time.
+template <int P, typename R>
+__device__ __forceinline__ R interp_smem(const R* __restrict__ base, const R* wx, const R* wy, const R* wz) {
+    R acc = R(0);
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+        R ay = R(0);
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+            R az = R(0);
+#pragma unroll
+            for (int k = 0; k <= P; ++k) az += wz[k] * base[i * kSEx + j * kSEy + k];
+            ay += wy[j] * az;
+        }
+        acc += wx[i] * ay;
+    }
+    return acc;
+}
+
+// Esirkepov deposit of one particle into the staged J box; `base` is the
+// element offset of window slot (0,0,0).  Same arithmetic as
+// esirkepov_deposit, with compile-time strides.
+template <int P, typename R>
+__device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict__ J1, R* __restrict__ J2, int base,
+                                               const EsirkAxis<P, R> ax[3], const R coef[3]) {
+    constexpr int NW = P + 2;
+    R* jx = J0 + base;
+    R* jy = J1 + base;
+    R* jz = J2 + base;
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const R Az = ax[2].S0[k] + R(0.5) * ax[2].dS[k];
+                const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
+                const R Q = ax[1].S0[j] * Az + ax[1].dS[j] * Bz;
+#pragma unroll
+                for (int i = 0; i < NW - 1; ++i) atomicAdd(jx + i * kSJx + j * kSJy + k, cum[i] * Q);
+            }
+    }
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                const R Az = ax[2].S0[k] + R(0.5) * ax[2].dS[k];
+                const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
+                const R Q = ax[0].S0[i] * Az + ax[0].dS[i] * Bz;
+#pragma unroll
+                for (int j = 0; j < NW - 1; ++j) atomicAdd(jy + i * kSJx + j * kSJy + k, cum[j] * Q);
+            }
+    }
+    {
+        R cum[NW - 1];
+        R run = R(0);
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                const R Ay = ax[1].S0[j] + R(0.5) * ax[1].dS[j];
+                const R By = R(0.5) * ax[1].S0[j] + R(1.0 / 3.0) * ax[1].dS[j];
+                const R Q = ax[0].S0[i] * Ay + ax[0].dS[i] * By;
+#pragma unroll
+                for (int k = 0; k < NW - 1; ++k) atomicAdd(jz + i * kSJx + j * kSJy + k, cum[k] * Q);
+            }
+    }
+}
+
+template <int P, typename R>
+__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(StepArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    const Geom& g = A.g;
+    R* sEB = sm;               // 6 * kSEvol
+    R* sJ = sm + 6 * kSEvol;   // 3 * kSJvol
+
+    const int t = blockIdx.x;
+    const int lcpt = g.lT[0] + g.lT[1] + g.lT[2];
+    const int beg = A.offsets[(int64_t)t * g.cpt];
+    const int end = A.offsets[(int64_t)(t + 1) * g.cpt];
+    if (end <= beg) return;
+    int oi, oj, ok;
+    tile_origin(g, t, oi, oj, ok);
+
+    // stage E, B of the tile and a halo of 2 (wrapped) into the fixed-stride box
+    {
+        const int ex = g.T[0] + 4, ey = g.T[1] + 4, ez = g.T[2] + 4;
+        const int vol = ex * ey * ez;
+        for (int e = threadIdx.x; e < 6 * vol; e += blockDim.x) {
+            const int c = e / vol;
+            int r = e - c * vol;
+            const int a = r / (ey * ez);
+            r -= a * ey * ez;
+            const int b = r / ez;
+            const int kk = r - b * ez;
+            const int gi = wrap_any(oi - 2 + a, g.n[0]);
+            const int gj = wrap_any(oj - 2 + b, g.n[1]);
+            const int gk = wrap_any(ok - 2 + kk, g.n[2]);
+            const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+            sEB[c * kSEvol + a * kSEx + b * kSEy + kk] = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+        }
+        for (int e = threadIdx.x; e < 3 * kSJvol; e += blockDim.x) sJ[e] = R(0);
+    }
+    __syncthreads();
+
+    // contiguous chunk of the tile's (cell-sorted) particles per thread
+    const int cnt = end - beg;
+    const int per = (cnt + blockDim.x - 1) / blockDim.x;
+    const int s0 = beg + threadIdx.x * per;
+    const int s1 = min(s0 + per, end);
+    for (int p = s0; p < s1; ++p) {
+        int cell[3];
+        R f0[3];
+        double xg0[3] = {0.0, 0.0, 0.0};
+        if (sizeof(R) == 8) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                xg0[a] = double(A.pa[a][p]);
+                double f;
+                split_pos(xg0[a], g.d[a], g.n[a], cell[a], f);
+                f0[a] = R(f);
+            }
+        } else {
+            cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) f0[a] = A.pa[a][p];
+        }
+        R u[3] = {A.pa[3][p], A.pa[4][p], A.pa[5][p]};
+        const R wq = A.pa[6][p];
+        const bool inside = (key_of(g, cell[0], cell[1], cell[2]) >> lcpt) == t;
+
+        R EB[6];
+        if (inside) {
+            GatherW<P, R> G;
+            int fn[3], fs[3];
+            gather_weights<P, R>(f0, G, fn, fs);
+            const int li = cell[0] - oi + 2, lj = cell[1] - oj + 2, lk = cell[2] - ok + 2;
+            // per component: first stencil node (node-centred n / staggered s per axis)
+            const int bnx = (li + fn[0]) * kSEx, bsx = (li + fs[0]) * kSEx;
+            const int bny = (lj + fn[1]) * kSEy, bsy = (lj + fs[1]) * kSEy;
+            const int bnz = lk + fn[2], bsz = lk + fs[2];
+            EB[0] = interp_smem<P, R>(sEB + 0 * kSEvol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
+            EB[1] = interp_smem<P, R>(sEB + 1 * kSEvol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
+            EB[2] = interp_smem<P, R>(sEB + 2 * kSEvol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
+            EB[3] = interp_smem<P, R>(sEB + 3 * kSEvol + bnx + bsy + bsz, G.wn[0], G.ws[1], G.ws[2]);
+            EB[4] = interp_smem<P, R>(sEB + 4 * kSEvol + bsx + bny + bsz, G.ws[0], G.wn[1], G.ws[2]);
+            EB[5] = interp_smem<P, R>(sEB + 5 * kSEvol + bsx + bsy + bnz, G.ws[0], G.ws[1], G.wn[2]);
+        } else {
+            gather_global_slow<P, R>(A, cell, f0, EB);
+        }
+        Moved<R> mv;
+        push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+        if (!mv.ok) {
+            raise_error(A.err, ERRBIT_PARTICLE);
+            continue;
+        }
+        EsirkAxis<P, R> ax[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
+        const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+        if (inside) {
+            const int base = (cell[0] - oi + 2 + ax[0].b) * kSJx + (cell[1] - oj + 2 + ax[1].b) * kSJy +
+                             (cell[2] - ok + 4 + ax[2].b);
+            esirkepov_smem<P, R>(sJ, sJ + kSJvol, sJ + 2 * kSJvol, base, ax, coef);
+        } else {
+            deposit_global_slow<P, R>(A, cell, ax, coef);
+        }
+
+        // store the new state in place
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A.pa[3 + a][p] = mv.u[a];
+        int nc[3];
+        if (sizeof(R) == 8) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const double xw = wrap_pos(mv.xg1[a], g.L[a]);
+                A.pa[a][p] = R(xw);
+                double f;
+                split_pos(xw, g.d[a], g.n[a], nc[a], f);
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                float nf;
+                renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
+                A.pa[a][p] = R(nf);
+            }
+        }
+        A.key[p] = key_of(g, nc[0], nc[1], nc[2]);
+    }
+    __syncthreads();
+
+    // flush the tile's current into the global arrays (periodic fold)
+    const int jx = g.T[0] + 5, jy = g.T[1] + 5, jz = g.T[2] + 8;
+    if (sizeof(R) == 4 && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
+        const int q4 = jz / 4;
+        const int rows = jx * jy;
+        for (int e = threadIdx.x; e < 3 * rows * q4; e += blockDim.x) {
+            const int c = e / (rows * q4);
+            int r = e - c * rows * q4;
+            const int row = r / q4;
+            const int q = r - row * q4;
+            const int a = row / jy;
+            const int b = row - a * jy;
+            const float4 v =
+                *reinterpret_cast<const float4*>(sJ + c * kSJvol + a * kSJx + b * kSJy + 4 * q);
+            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+            const int gi = wrap_any(oi - 2 + a, g.n[0]);
+            const int gj = wrap_any(oj - 2 + b, g.n[1]);
+            const int gk = wrap_any(ok - 4 + 4 * q, g.n[2]);
+            float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+            atomicAdd(reinterpret_cast<float4*>(dst), v);
+        }
+    } else {
+        const int vol = jx * jy * jz;
+        for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) {
+            const int c = e / vol;
+            int r = e - c * vol;
+            const int a = r / (jy * jz);
+            r -= a * jy * jz;
+            const int b = r / jz;
+            const int kk = r - b * jz;
+            const R v = sJ[c * kSJvol + a * kSJx + b * kSJy + kk];
+            if (v == R(0)) continue;
+            const int gi = wrap_any(oi - 2 + a, g.n[0]);
+            const int gj = wrap_any(oj - 2 + b, g.n[1]);
+            const int gk = wrap_any(ok - 4 + kk, g.n[2]);
+            atomicAdd(A.J[c] + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk, v);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// split API: gather+push with global loads; Esirkepov with global atomics
+// ---------------------------------------------------------------------------
+template <int P, typename R>
+__global__ void __launch_bounds__(kBlock) k_gather_push(StepArgs<R> A) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    int cell[3];
+    R f0[3];
+    double xg0[3] = {0.0, 0.0, 0.0};
+    if (sizeof(R) == 8) {
+        for (int a = 0; a < 3; ++a) {
+            xg0[a] = double(A.pa[a][p]);
+            double f;
+            split_pos(xg0[a], g.d[a], g.n[a], cell[a], f);
+            f0[a] = R(f);
+        }
+    } else {
+        cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
+        for (int a = 0; a < 3; ++a) f0[a] = A.pa[a][p];
+    }
+    R u[3] = {A.pa[3][p], A.pa[4][p], A.pa[5][p]};
+    GatherW<P, R> G;
+    int fn[3], fs[3];
+    gather_weights<P, R>(f0, G, fn, fs);
+    offsets_global<P, R>(G, g, cell, fn, fs);
+    R EB[6];
+    gather6<P, R>(G, A.E, A.B, EB);
+    Moved<R> mv;
+    push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+    if (!mv.ok) {
+        raise_error(A.err, ERRBIT_PARTICLE);
+        // keep the particle where it was; the deposit sees no move
+        for (int a = 0; a < 3; ++a) {
+            A.old[a][p] = sizeof(R) == 8 ? R(xg0[a]) : f0[a];
+            A.old[3 + a][p] = R(0);
+        }
+        if (sizeof(R) == 4) A.oldkey[p] = A.key[p];
+        return;
+    }
+    for (int a = 0; a < 3; ++a) A.pa[3 + a][p] = mv.u[a];
+    int nc[3];
+    if (sizeof(R) == 8) {
+        for (int a = 0; a < 3; ++a) {
+            A.old[a][p] = R(xg0[a]);
+            A.old[3 + a][p] = R(mv.xg1[a] - xg0[a]);  // exact: the unwrapped move
+            const double xw = wrap_pos(mv.xg1[a], g.L[a]);
+            A.pa[a][p] = R(xw);
+            double f;
+            split_pos(xw, g.d[a], g.n[a], nc[a], f);
+        }
+    } else {
+        A.oldkey[p] = A.key[p];
+        for (int a = 0; a < 3; ++a) {
+            A.old[a][p] = f0[a];
+            A.old[3 + a][p] = mv.f1[a] - f0[a];
+            float nf;
+            renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
+            A.pa[a][p] = R(nf);
+        }
+    }
+    A.key[p] = key_of(g, nc[0], nc[1], nc[2]);
+}
+
+template <int P, typename R>
+__global__ void __launch_bounds__(kBlock) k_deposit(StepArgs<R> A) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    int cell[3];
+    R f0[3], f1[3];
+    if (sizeof(R) == 8) {
+        for (int a = 0; a < 3; ++a) {
+            const double x0 = double(A.old[a][p]);
+            double f;
+            split_pos(x0, g.d[a], g.n[a], cell[a], f);
+            const double x1 = __dadd_rn(x0, double(A.old[3 + a][p]));
+            f0[a] = R(f);
+            f1[a] = R(x1 / g.d[a] - double(cell[a]));
+        }
+    } else {
+        cell_of(g, A.oldkey[p], cell[0], cell[1], cell[2]);
+        for (int a = 0; a < 3; ++a) {
+            f0[a] = A.old[a][p];
+            f1[a] = f0[a] + A.old[3 + a][p];
+        }
+    }
+    EsirkAxis<P, R> ax[3];
+    for (int a = 0; a < 3; ++a) ax[a].init(f0[a], f1[a]);
+    const R wq = A.pa[6][p];
+    const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+    JTarget<P, R> jt;
+    jtarget_global<P, R>(jt, g, A.J, cell, ax);
+    esirkepov_deposit<P, R>(ax, coef, jt);
+}
+
+// ---------------------------------------------------------------------------
+// Yee FDTD
+// ---------------------------------------------------------------------------
+template <typename R> struct YeeArgs {
+    R* E[3];
+    R* B[3];
+    const R* J[3];
+    int n[3];
+    R inv[3];
+    R h;
+    long long* step;  // advanced by one thread when non-null
+};
+
+// B <- B - h curl E (forward differences: B sits half a cell above E).
+template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<R> Y) {
+    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (Y.step && c == 0) *Y.step += 1;
+    if (c >= C) return;
+    const int k = int(c % Y.n[2]);
+    const int j = int((c / Y.n[2]) % Y.n[1]);
+    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+    const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
+    const int64_t ip = c + (i + 1 == Y.n[0] ? -(int64_t)(Y.n[0] - 1) * sx : sx);
+    const int64_t jp = c + (j + 1 == Y.n[1] ? -(int64_t)(Y.n[1] - 1) * sy : sy);
+    const int64_t kp = c + (k + 1 == Y.n[2] ? -(int64_t)(Y.n[2] - 1) : 1);
+    const R ex = Y.E[0][c], ey = Y.E[1][c], ez = Y.E[2][c];
+    const R dEz_dy = (Y.E[2][jp] - ez) * Y.inv[1];
+    const R dEy_dz = (Y.E[1][kp] - ey) * Y.inv[2];
+    const R dEx_dz = (Y.E[0][kp] - ex) * Y.inv[2];
+    const R dEz_dx = (Y.E[2][ip] - ez) * Y.inv[0];
+    const R dEy_dx = (Y.E[1][ip] - ey) * Y.inv[0];
+    const R dEx_dy = (Y.E[0][jp] - ex) * Y.inv[1];
+    Y.B[0][c] -= Y.h * (dEz_dy - dEy_dz);
+    Y.B[1][c] -= Y.h * (dEx_dz - dEz_dx);
+    Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
+}
+
+// E <- E + dt (curl B - J) (backward differences).
+template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
+    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int k = int(c % Y.n[2]);
+    const int j = int((c / Y.n[2]) % Y.n[1]);
+    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+    const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
+    const int64_t im = c - (i == 0 ? -(int64_t)(Y.n[0] - 1) * sx : sx);
+    const int64_t jm = c - (j == 0 ? -(int64_t)(Y.n[1] - 1) * sy : sy);
+    const int64_t km = c - (k == 0 ? -(int64_t)(Y.n[2] - 1) : 1);
+    const R bx = Y.B[0][c], by = Y.B[1][c], bz = Y.B[2][c];
+    const R dBz_dy = (bz - Y.B[2][jm]) * Y.inv[1];
+    const R dBy_dz = (by - Y.B[1][km]) * Y.inv[2];
+    const R dBx_dz = (bx - Y.B[0][km]) * Y.inv[2];
+    const R dBz_dx = (bz - Y.B[2][im]) * Y.inv[0];
+    const R dBy_dx = (by - Y.B[1][im]) * Y.inv[0];
+    const R dBx_dy = (bx - Y.B[0][jm]) * Y.inv[1];
+    Y.E[0][c] += Y.h * ((dBz_dy - dBy_dz) - Y.J[0][c]);
+    Y.E[1][c] += Y.h * ((dBx_dz - dBz_dx) - Y.J[1][c]);
+    Y.E[2][c] += Y.h * ((dBy_dx - dBx_dy) - Y.J[2][c]);
+}
+
+template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
+    YeeArgs<R> Y;
+    for (int d = 0; d < 3; ++d) {
+        Y.E[d] = static_cast<R*>(c->F[d]);
+        Y.B[d] = static_cast<R*>(c->F[3 + d]);
+        Y.J[d] = static_cast<const R*>(c->F[6 + d]);
+        Y.n[d] = c->g.n[d];
+        Y.inv[d] = R(1.0 / c->g.d[d]);
+    }
+    Y.h = R(h);
+    Y.step = nullptr;
+    return Y;
+}
+
+// ---------------------------------------------------------------------------
+// particle load / store, field conversion, diagnostics
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void k_load(StepArgs<R> A, const double* x, const double* y, const double* z, const double* ux,
+                       const double* uy, const double* uz, const double* w, int* id) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    const double xs[3] = {x[p], y[p], z[p]};
+    const double us[3] = {ux[p], uy[p], uz[p]};
+    bool ok = isfinite(w[p]);
+    int cell[3];
+    for (int a = 0; a < 3; ++a) {
+        ok = ok && isfinite(xs[a]) && isfinite(us[a]);
+        double xv = isfinite(xs[a]) ? xs[a] : 0.0;
+        xv = fmod(xv, g.L[a]);
+        xv = wrap_pos(xv, g.L[a]);
+        double f;
+        split_pos(xv, g.d[a], g.n[a], cell[a], f);
+        if (sizeof(R) == 8) {
+            A.pa[a][p] = R(xv);
+        } else {
+            float ff = float(f);
+            if (ff >= 1.0f) {  // rounds up to the next cell
+                ff = 0.0f;
+                cell[a] = wrap_once(cell[a] + 1, g.n[a]);
+            }
+            A.pa[a][p] = R(ff);
+        }
+        A.pa[3 + a][p] = R(us[a]);
+    }
+    A.pa[6][p] = R(w[p]);
+    A.key[p] = key_of(g, cell[0], cell[1], cell[2]);
+    id[p] = int(p);
+    if (!ok) raise_error(A.err, ERRBIT_PARTICLE);
+}
+
+template <typename R>
+__global__ void k_store(StepArgs<R> A, double* x, double* y, double* z, double* ux, double* uy, double* uz,
+                        double* w, const int* idsrc, int32_t* id) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    double* xs[3] = {x, y, z};
+    double* us[3] = {ux, uy, uz};
+    int cell[3];
+    if (sizeof(R) == 4) cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
+    for (int a = 0; a < 3; ++a) {
+        if (xs[a]) {
+            double v = sizeof(R) == 8 ? double(A.pa[a][p]) : (double(cell[a]) + double(A.pa[a][p])) * g.d[a];
+            xs[a][p] = wrap_pos(v, g.L[a]);
+        }
+        if (us[a]) us[a][p] = double(A.pa[3 + a][p]);
+    }
+    if (w) w[p] = double(A.pa[6][p]);
+    if (id) id[p] = idsrc[p];
+}
+
+template <typename S, typename D> __global__ void k_convert(const S* src, D* dst, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = D(src[i]);
+}
+
+// out[0] += sum |F|^2 / 2 over Ex..Bz (times dV on the host), out[1] kinetic,
+// out[2] charge, out[3] max |div B| (as a bit pattern, max via atomicMax).
+template <typename R>
+__global__ void k_diag_fields(const R* const* F, int64_t C, double* out) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x)
+        for (int c = 0; c < 6; ++c) {
+            const double v = double(F[c][i]);
+            s += v * v;
+        }
+    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    __shared__ double red[kBlock / 32];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(out, 0.5 * t);
+    }
+}
+
+template <typename R>
+__global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out) {
+    double ke = 0.0, ch = 0.0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double u0 = A.pa[3][p], u1 = A.pa[4][p], u2 = A.pa[5][p], w = A.pa[6][p];
+        ke += w * m * (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0);
+        ch += q * w;
+    }
+    for (int o = 16; o; o >>= 1) {
+        ke += __shfl_down_sync(0xffffffffu, ke, o);
+        ch += __shfl_down_sync(0xffffffffu, ch, o);
+    }
+    __shared__ double red[2][kBlock / 32];
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = ke;
+        red[1][threadIdx.x >> 5] = ch;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[0][w], b += red[1][w];
+        atomicAdd(out + 1, a);
+        atomicAdd(out + 2, b);
+    }
+}
+
+template <typename R>
+__global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int ny, int nz, double dx, double dy,
+                            double dz, unsigned long long* out) {
+    const int64_t C = (int64_t)nx * ny * nz;
+    double mx = 0.0;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
+        const int k = int(c % nz), j = int((c / nz) % ny), i = int(c / ((int64_t)ny * nz));
+        const int64_t ip = ((int64_t)wrap_once(i + 1, nx) * ny + j) * nz + k;
+        const int64_t jp = ((int64_t)i * ny + wrap_once(j + 1, ny)) * nz + k;
+        const int64_t kp = ((int64_t)i * ny + j) * nz + wrap_once(k + 1, nz);
+        const double v = (double(Bx[ip]) - double(Bx[c])) / dx + (double(By[jp]) - double(By[c])) / dy +
+                         (double(Bz[kp]) - double(Bz[c])) / dz;
+        mx = fmax(mx, fabs(v));
+    }
+    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+static inline unsigned blocks_for(int64_t n) { return unsigned((n + kBlock - 1) / kBlock); }
+
+template <typename R, int P> cudaError_t tile_step_impl(pic_ctx* c) {
+    StepArgs<R> A = make_args<R>(c);
+    const size_t smem = tile_smem_bytes<R>();
+    static thread_local size_t configured = 0;
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_tile_step<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             int(smem));
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    k_tile_step<P, R><<<unsigned(c->g.ntiles), kBlock, smem, c->stream>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
+    switch (c->order) {
+    case 1: return tile_step_impl<R, 1>(c);
+    case 2: return tile_step_impl<R, 2>(c);
+    default: return tile_step_impl<R, 3>(c);
+    }
+}
+
+cudaError_t launch_tile_step(pic_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
+    if (e != cudaSuccess) return e;
+    // J is one allocation of three components (see pic_api.cu)
+    return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
+}
+
+template <typename R, int P> cudaError_t gp_impl(pic_ctx* c) {
+    StepArgs<R> A = make_args<R>(c);
+    if (c->np == 0) return cudaSuccess;
+    k_gather_push<P, R><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A);
+    return cudaGetLastError();
+}
+
+template <typename R, int P> cudaError_t dep_impl(pic_ctx* c) {
+    StepArgs<R> A = make_args<R>(c);
+    if (c->np == 0) return cudaSuccess;
+    k_deposit<P, R><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_push_global(pic_ctx* c) {
+    if (c->prec == PIC_FP64) {
+        switch (c->order) {
+        case 1: return gp_impl<double, 1>(c);
+        case 2: return gp_impl<double, 2>(c);
+        default: return gp_impl<double, 3>(c);
+        }
+    }
+    switch (c->order) {
+    case 1: return gp_impl<float, 1>(c);
+    case 2: return gp_impl<float, 2>(c);
+    default: return gp_impl<float, 3>(c);
+    }
+}
+
+cudaError_t launch_deposit_global(pic_ctx* c) {
+    cudaError_t e = cudaMemsetAsync(c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
+    if (e != cudaSuccess) return e;
+    if (c->prec == PIC_FP64) {
+        switch (c->order) {
+        case 1: return dep_impl<double, 1>(c);
+        case 2: return dep_impl<double, 2>(c);
+        default: return dep_impl<double, 3>(c);
+        }
+    }
+    switch (c->order) {
+    case 1: return dep_impl<float, 1>(c);
+    case 2: return dep_impl<float, 2>(c);
+    default: return dep_impl<float, 3>(c);
+    }
+}
+
+cudaError_t launch_yee_b(pic_ctx* c, double h) {
+    if (c->prec == PIC_FP64) {
+        auto Y = make_yee<double>(c, h);
+        k_yee_b<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+    } else {
+        auto Y = make_yee<float>(c, h);
+        k_yee_b<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_e(pic_ctx* c) {
+    if (c->prec == PIC_FP64) {
+        auto Y = make_yee<double>(c, c->dt);
+        k_yee_e<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+    } else {
+        auto Y = make_yee<float>(c, c->dt);
+        k_yee_e<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+    }
+    return cudaGetLastError();
+}
+
+__global__ void k_step_counter(long long* s) { *s += 1; }
+
+cudaError_t launch_step_counter(pic_ctx* c) {
+    k_step_counter<<<1, 1, 0, c->stream>>>(c->d_step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n) {
+    if (n == 0) return cudaSuccess;
+    if (c->prec == PIC_FP64) {
+        auto A = make_args<double>(c);
+        k_load<double><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
+                                                               src[6], c->P[c->cur].id);
+    } else {
+        auto A = make_args<float>(c);
+        k_load<float><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
+                                                              src[6], c->P[c->cur].id);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id) {
+    if (c->np == 0) return cudaSuccess;
+    if (c->prec == PIC_FP64) {
+        auto A = make_args<double>(c);
+        k_store<double><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
+                                                                    dst[5], dst[6], c->P[c->cur].id, id);
+    } else {
+        auto A = make_args<float>(c);
+        k_store<float><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
+                                                                   dst[5], dst[6], c->P[c->cur].id, id);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst) {
+    if (c->prec == PIC_FP64)
+        return cudaMemcpyAsync(dst, c->F[which], c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    k_convert<float, double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(static_cast<const float*>(c->F[which]),
+                                                                         dst, c->g.C);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src) {
+    if (c->prec == PIC_FP64)
+        return cudaMemcpyAsync(c->F[which], src, c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+    k_convert<double, float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(src, static_cast<float*>(c->F[which]),
+                                                                         c->g.C);
+    return cudaGetLastError();
+}
+
+template <typename R> cudaError_t diag_impl(pic_ctx* c, double* d_out) {
+    // F pointer table lives in the scratch after the four outputs
+    const R** tab = reinterpret_cast<const R**>(d_out + 8);
+    const R* host_tab[6];
+    for (int i = 0; i < 6; ++i) host_tab[i] = static_cast<const R*>(c->F[i]);
+    cudaError_t e = cudaMemcpyAsync(tab, host_tab, sizeof(host_tab), cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return e;
+    const unsigned nb = 152 * 4;
+    k_diag_fields<R><<<nb, kBlock, 0, c->stream>>>(tab, c->g.C, d_out);
+    if (c->np > 0) {
+        auto A = make_args<R>(c);
+        k_diag_particles<R><<<nb, kBlock, 0, c->stream>>>(A, c->m, c->q, d_out);
+    }
+    k_diag_divb<R><<<nb, kBlock, 0, c->stream>>>(static_cast<const R*>(c->F[3]), static_cast<const R*>(c->F[4]),
+                                                 static_cast<const R*>(c->F[5]), c->g.n[0], c->g.n[1], c->g.n[2],
+                                                 c->g.d[0], c->g.d[1], c->g.d[2],
+                                                 reinterpret_cast<unsigned long long*>(d_out + 3));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_diagnostics(pic_ctx* c, double* d_out) {
+    return c->prec == PIC_FP64 ? diag_impl<double>(c, d_out) : diag_impl<float>(c, d_out);
+}
+
+}  // namespace pic

@@ -1,0 +1,212 @@
+// Counting sort of the particles by tile-major cell key (Sec. 3.4.2: bin by
+// cell, then reorder the particle data; AMReX builds its GPU counting sort on
+// the single-pass prefix sum of Merrill and Garland).
+//
+//  k_hist     count[key] += 1, warp-aggregated (__match_any_sync) atomics
+//  k_scan     exclusive prefix sum of count into offsets in one pass:
+//             each CTA takes the next chunk ticket, publishes its aggregate,
+//             and looks back over its predecessors' published words
+//             (decoupled look-back, Merrill & Garland 2016).  Every wait is
+//             bounded; a wait that runs out sets the device error word.
+//  k_scatter  each particle takes a slot in its cell's range by decrementing
+//             count (warp-aggregated), then all its arrays move to the other
+//             buffer.  count returns to zero, ready for the next histogram.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "pic_ctx.h"
+#include "pic_device.cuh"
+
+namespace pic {
+
+constexpr int kSortBlock = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kSortBlock * kScanItems;
+constexpr int kSpinLimit = 1 << 20;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_hist(const int* __restrict__ key, int64_t np, int* count, int64_t C,
+                                                     unsigned* err) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = -1;
+    if (p < np) {
+        k = key[p];
+        if (k < 0 || k >= C) {
+            raise_error(err, ERRBIT_RANGE);
+            k = -1;
+        }
+    }
+    const unsigned mask = __match_any_sync(0xffffffffu, k);
+    if (k >= 0) {
+        const int lane = threadIdx.x & 31;
+        if (lane == __ffs(mask) - 1) atomicAdd(count + k, __popc(mask));
+    }
+}
+
+// status word: bits 32..33 flag (0 empty, 1 aggregate, 2 inclusive prefix), low 32 bits value
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_status(unsigned long long* p, unsigned flag, unsigned value) {
+    const unsigned long long v = ((unsigned long long)flag << 32) | value;
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ count, int* offsets, int64_t C,
+                                                     unsigned long long* status, int nchunks, unsigned* err) {
+    __shared__ int s_chunk;
+    __shared__ int s_warp[kSortBlock / 32];
+    __shared__ int s_prefix;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_chunk = int(atomicAdd(reinterpret_cast<unsigned long long*>(status + nchunks), 1ull));
+    __syncthreads();
+    const int chunk = s_chunk;
+    if (chunk >= nchunks) return;
+    const int64_t base = (int64_t)chunk * kScanChunk + (int64_t)tid * kScanItems;
+
+    int v[kScanItems];
+    int tsum = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        v[i] = idx < C ? count[idx] : 0;
+        tsum += v[i];
+    }
+    // block exclusive scan of the per-thread sums
+    int incl = tsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int wv = lane < kSortBlock / 32 ? s_warp[lane] : 0;
+        int wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < kSortBlock / 32) s_warp[lane] = wi - wv;  // exclusive warp offsets
+        // the chunk aggregate is the last inclusive value
+        const int agg = __shfl_sync(0xffffffffu, wi, kSortBlock / 32 - 1);
+        // decoupled look-back by warp 0
+        int excl = 0;
+        if (chunk == 0) {
+            if (lane == 0) st_status(status + chunk, 2u, unsigned(agg));
+        } else {
+            if (lane == 0) st_status(status + chunk, 1u, unsigned(agg));
+            int j = chunk - 1;  // highest predecessor not yet summed
+            bool done = false;
+            while (!done) {
+                const int idx = j - lane;
+                unsigned long long s = 0;
+                if (idx >= 0) {
+                    int spins = 0;
+                    s = ld_status(status + idx);
+                    while ((s >> 32) == 0ull) {
+                        if (++spins > kSpinLimit) {
+                            raise_error(err, ERRBIT_TIMEOUT);
+                            s = 2ull << 32;  // give up: treat as a zero prefix
+                            break;
+                        }
+                        __nanosleep(32);
+                        s = ld_status(status + idx);
+                    }
+                } else {
+                    s = 2ull << 32;  // before chunk 0: empty prefix
+                }
+                const unsigned flag = unsigned(s >> 32);
+                const unsigned incl_mask = __ballot_sync(0xffffffffu, flag == 2u);
+                // lanes up to and including the nearest inclusive word contribute
+                const int stop = incl_mask ? __ffs(incl_mask) - 1 : 31;
+                int contrib = lane <= stop ? int(unsigned(s)) : 0;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) contrib += __shfl_xor_sync(0xffffffffu, contrib, o);
+                excl += contrib;
+                if (incl_mask) done = true;
+                else j -= 32;
+            }
+            if (lane == 0) st_status(status + chunk, 2u, unsigned(excl + agg));
+        }
+        if (lane == 0) {
+            s_prefix = excl;
+            if (chunk == nchunks - 1) offsets[C] = excl + agg;
+        }
+    }
+    __syncthreads();
+    int run = s_prefix + s_warp[warp] + (incl - tsum);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t idx = base + i;
+        if (idx < C) offsets[idx] = run;
+        run += v[i];
+    }
+}
+
+template <typename E>
+__global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst, int64_t np, const int* offsets,
+                                                        int* count, int64_t C) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = -1;
+    if (p < np) {
+        k = src.key[p];
+        if (k < 0 || k >= C) k = -1;
+    }
+    const unsigned mask = __match_any_sync(0xffffffffu, k);
+    if (k < 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    const int ng = __popc(mask);
+    int old = 0;
+    if (lane == leader) old = atomicSub(count + k, ng);
+    old = __shfl_sync(mask, old, leader);
+    const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
+#pragma unroll
+    for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = static_cast<const E*>(src.a[i])[p];
+    dst.key[dest] = k;
+    dst.id[dest] = src.id[p];
+}
+
+size_t scan_status_words(int64_t C) { return size_t((C + kScanChunk - 1) / kScanChunk) + 1; }
+
+cudaError_t launch_hist(pic_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
+    k_hist<<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur].key, c->np, c->count, c->g.C, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(pic_ctx* c) {
+    cudaError_t e =
+        cudaMemsetAsync(c->scan_status, 0, (size_t(c->scan_chunks) + 1) * sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    k_scan<<<unsigned(c->scan_chunks), kSortBlock, 0, c->stream>>>(c->count, c->offsets, c->g.C, c->scan_status,
+                                                                  c->scan_chunks, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(pic_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
+    if (c->prec == PIC_FP64)
+        k_scatter<double><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
+                                                            c->count, c->g.C);
+    else
+        k_scatter<float><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
+                                                           c->count, c->g.C);
+    return cudaGetLastError();
+}
+
+}  // namespace pic

@@ -1,0 +1,247 @@
+"""Thin ctypes binding of libpic (include/pic.h).  Argument marshalling only:
+every step of the PIC path runs in the CUDA library.
+
+Arrays may be numpy arrays (host memory) or torch CUDA tensors (device
+memory of the context's GPU); float64 unless stated.  The binding fails
+loudly if libpic has not been built: there is no CPU fallback.
+"""
+import ctypes as ct
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpic.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pic.h")
+
+PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_STATE, PIC_ERR_PARTICLE, PIC_ERR_TIMEOUT = range(8)
+STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CFL", 3: "PIC_ERR_OOM", 4: "PIC_ERR_CUDA",
+                5: "PIC_ERR_STATE", 6: "PIC_ERR_PARTICLE", 7: "PIC_ERR_TIMEOUT"}
+FP64, FP32_MIXED = 0, 1
+FIELDS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
+PARTICLE_KEYS = ("x", "y", "z", "ux", "uy", "uz", "w")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class PicError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class GridDesc(ct.Structure):
+    _fields_ = [("n", ct.c_int32 * 3), ("d", ct.c_double * 3), ("dt", ct.c_double), ("cfl", ct.c_double),
+                ("precision", ct.c_int32), ("order", ct.c_int32), ("sort_every", ct.c_int32),
+                ("window_axis", ct.c_int32), ("window_speed", ct.c_double), ("seed", ct.c_uint64),
+                ("tile", ct.c_int32 * 3)]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpic; raises if it is missing (build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpic is not built ({path} missing): run paper_2101_12149_gb300.build.build()")
+        lib = ct.CDLL(path)
+        P, I32, I64, D = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
+        sigs = {
+            "pic_init_grid": [ct.POINTER(GridDesc), P, ct.POINTER(P)],
+            "pic_load_particles": [P, D, D, I64, P, P, P, P, P, P, P, ct.c_int],
+            "pic_gather_push": [P],
+            "pic_deposit": [P],
+            "pic_yee_step": [P],
+            "pic_step": [P, I32],
+            "pic_get_field": [P, I32, P, ct.c_int],
+            "pic_set_field": [P, I32, P, ct.c_int],
+            "pic_num_particles": [P, ct.POINTER(I64)],
+            "pic_get_particles": [P, P, P, P, P, P, P, P, P, ct.c_int],
+            "pic_set_external_drive": [P, D, D],
+            "pic_get_time": [P, ct.POINTER(I64), ct.POINTER(D)],
+            "pic_diagnostics": [P, P],
+            "pic_sync": [P],
+            "pic_set_timing": [P, I32],
+            "pic_get_timing": [P, I32, P, P, P, ct.POINTER(I32)],
+            "pic_launch_count": [P, ct.POINTER(I64)],
+            "pic_destroy": [P],
+        }
+        for name, args in sigs.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ct.c_int
+        lib.pic_last_error.argtypes = []
+        lib.pic_last_error.restype = ct.c_char_p
+        _lib = lib
+        return lib
+
+
+def declared_symbols(header: str = HEADER):
+    """Names of the functions include/pic.h declares."""
+    import re
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:pic_status|const char\*)\s+(pic_\w+)\s*\(", text, re.M)))
+
+
+def _check(status):
+    if status != PIC_OK:
+        msg = _lib.pic_last_error().decode() if _lib is not None else ""
+        raise PicError(status, msg)
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        assert a.flags.c_contiguous
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+class Context:
+    """One PIC simulation: grid, fields and one particle species on one GPU."""
+
+    def __init__(self, n, d=(1.0, 1.0, 1.0), dt=0.0, cfl=0.99, precision=FP64, order=1, sort_every=1,
+                 tile=(0, 0, 0), stream=None):
+        self.lib = load_library()
+        desc = GridDesc()
+        for a in range(3):
+            desc.n[a] = int(n[a])
+            desc.d[a] = float(d[a])
+            desc.tile[a] = int(tile[a])
+        desc.dt = float(dt)
+        desc.cfl = float(cfl)
+        desc.precision = int(precision)
+        desc.order = int(order)
+        desc.sort_every = int(sort_every)
+        desc.window_axis = -1
+        desc.window_speed = 0.0
+        desc.seed = 0
+        self.n = tuple(int(v) for v in n)
+        self.C = self.n[0] * self.n[1] * self.n[2]
+        h = ct.c_void_p()
+        s = None
+        if stream is not None:
+            s = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(self.lib.pic_init_grid(ct.byref(desc), s, ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- particles ---------------------------------------------------
+    def load_particles(self, q, m, parts):
+        arrs = [parts[k] for k in PARTICLE_KEYS]
+        n = int(arrs[0].shape[0]) if hasattr(arrs[0], "shape") else len(arrs[0])
+        ptrs = [_ptr(a) for a in arrs]
+        on_dev = {p[1] for p in ptrs}
+        assert len(on_dev) == 1, "all particle arrays must be on the same side"
+        _check(self.lib.pic_load_particles(self.h, float(q), float(m), n, *[p[0] for p in ptrs], on_dev.pop()))
+
+    def num_particles(self):
+        v = ct.c_int64()
+        _check(self.lib.pic_num_particles(self.h, ct.byref(v)))
+        return v.value
+
+    def get_particles(self, out=None):
+        """dict of float64 arrays x..w plus int32 id (numpy unless `out` gives device tensors)."""
+        n = self.num_particles()
+        if out is None:
+            out = {k: np.empty(n) for k in PARTICLE_KEYS}
+            out["id"] = np.empty(n, dtype=np.int32)
+        ptrs = [_ptr(out.get(k)) for k in PARTICLE_KEYS + ("id",)]
+        sides = {p[1] for p in ptrs if p[1] is not None}
+        assert len(sides) == 1
+        _check(self.lib.pic_get_particles(self.h, *[p[0] for p in ptrs], sides.pop()))
+        return out
+
+    # -- steps -------------------------------------------------------
+    def gather_push(self):
+        _check(self.lib.pic_gather_push(self.h))
+
+    def deposit(self):
+        _check(self.lib.pic_deposit(self.h))
+
+    def yee_step(self):
+        _check(self.lib.pic_yee_step(self.h))
+
+    def step(self, nsteps=1):
+        _check(self.lib.pic_step(self.h, int(nsteps)))
+
+    # -- fields ------------------------------------------------------
+    def get_field(self, which, out=None):
+        w = FIELDS.index(which) if isinstance(which, str) else int(which)
+        if out is None:
+            out = np.empty(self.n)
+        p, dev = _ptr(out)
+        _check(self.lib.pic_get_field(self.h, w, p, dev))
+        return out
+
+    def get_fields(self):
+        return np.stack([self.get_field(i) for i in range(9)])
+
+    def set_field(self, which, arr):
+        w = FIELDS.index(which) if isinstance(which, str) else int(which)
+        if isinstance(arr, np.ndarray):
+            arr = np.ascontiguousarray(arr, dtype=np.float64)
+        p, dev = _ptr(arr)
+        _check(self.lib.pic_set_field(self.h, w, p, dev))
+
+    def set_fields(self, F):
+        for i in range(F.shape[0]):
+            self.set_field(i, F[i])
+
+    # -- misc --------------------------------------------------------
+    def set_external_drive(self, amp, k):
+        _check(self.lib.pic_set_external_drive(self.h, float(amp), float(k)))
+
+    def time(self):
+        s, t = ct.c_int64(), ct.c_double()
+        _check(self.lib.pic_get_time(self.h, ct.byref(s), ct.byref(t)))
+        return s.value, t.value
+
+    def diagnostics(self):
+        out = (ct.c_double * 4)()
+        _check(self.lib.pic_diagnostics(self.h, out))
+        return {"field_energy": out[0], "kinetic_energy": out[1], "charge": out[2], "max_div_b": out[3]}
+
+    def sync(self):
+        _check(self.lib.pic_sync(self.h))
+
+    def set_timing(self, on=True):
+        _check(self.lib.pic_set_timing(self.h, 1 if on else 0))
+
+    def get_timing(self):
+        cap = 16
+        names = (ct.c_char_p * cap)()
+        ms = (ct.c_double * cap)()
+        cnt = (ct.c_int64 * cap)()
+        n = ct.c_int32()
+        _check(self.lib.pic_get_timing(self.h, cap, names, ms, cnt, ct.byref(n)))
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(n.value, cap))}
+
+    def launch_count(self):
+        v = ct.c_int64()
+        _check(self.lib.pic_launch_count(self.h, ct.byref(v)))
+        return v.value

@@ -1,0 +1,157 @@
+"""CUDA path (through the C-ABI) against the FP64 CPU oracle on the same seeded
+inputs.  FP64: 1e-12 relative L2 after one step, 1e-9 after the 50-step
+32^3 run (atomic summation order is the only allowed difference).
+FP32-mixed: error stated against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from gpu_helpers import Case, rel_l2
+from paper_2101_12149_gb300 import inputs, pic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ONE_STEP_CASES = [
+    # n, order, ppc, sigma_u, seed, d, tile
+    ((16, 8, 24), 1, 3, 0.3, 1, (1.0, 1.0, 1.0), (0, 0, 0)),
+    ((16, 8, 24), 2, 3, 0.3, 2, (1.0, 1.0, 1.0), (0, 0, 0)),
+    ((16, 8, 24), 3, 3, 0.3, 3, (1.0, 1.0, 1.0), (0, 0, 0)),
+    ((12, 20, 8), 3, 2, 0.5, 4, (1.0, 0.9, 1.1), (0, 0, 0)),   # tiles 4x4x8, non-unit cells
+    ((5, 6, 7), 3, 2, 0.5, 5, (1.0, 1.0, 1.0), (0, 0, 0)),     # tiles of 1 cell, grid barely > stencil
+    ((16, 16, 16), 2, 4, 0.8, 6, (1.0, 1.0, 1.0), (2, 4, 8)),  # non-cubic tiles, relativistic
+]
+
+
+@pytest.mark.parametrize("case", ONE_STEP_CASES, ids=lambda c: f"n{c[0]}-p{c[1]}")
+def test_fp64_one_step_fused(case):
+    n, p, ppc, sig, seed, d, tile = case
+    c = Case(n, p, ppc, sig, seed, d=d, tile=tile, field_scale=0.05)
+    c.ctx.step(1)
+    c.oracle_steps(1)
+    e = c.errors()
+    assert e["EB"] < 1e-12 and e["J"] < 1e-12 and e["pos"] < 1e-12 and e["mom"] < 1e-12, e
+
+
+@pytest.mark.parametrize("case", ONE_STEP_CASES[:4], ids=lambda c: f"n{c[0]}-p{c[1]}")
+def test_fp64_one_step_split_api(case):
+    """pic_gather_push + pic_deposit + pic_yee_step (global-memory kernels)."""
+    n, p, ppc, sig, seed, d, tile = case
+    c = Case(n, p, ppc, sig, seed, d=d, tile=tile, field_scale=0.05)
+    c.ctx.gather_push()
+    c.ctx.deposit()
+    c.ctx.yee_step()
+    c.oracle_steps(1)
+    e = c.errors()
+    assert e["EB"] < 1e-12 and e["J"] < 1e-12 and e["pos"] < 1e-12 and e["mom"] < 1e-12, e
+
+
+@pytest.mark.parametrize("sort_every", [1, 3])
+def test_fp64_multi_step(sort_every):
+    """Ten steps with and without a sort every step (between sorts particles
+    leave their tile and take the global path)."""
+    c = Case((16, 16, 8), 3, 4, 0.4, 11, field_scale=0.02, sort_every=sort_every)
+    c.ctx.step(10)
+    c.oracle_steps(10)
+    e = c.errors()
+    assert max(e.values()) < 1e-11, e
+
+
+def test_uniform_32_full_run_fp64():
+    """The 32^3, 2 ppc, order-1 workload, 50 steps: 1e-9 relative L2."""
+    w = inputs.WORKLOADS["uniform_32"]
+    s = torch.cuda.Stream()
+    c = Case(w["n"], w["order"], w["ppc"], w["sigma_u"], w["seed"], pert=(w["pert_amp"], w["pert_k"]), stream=s)
+    c.ctx.step(w["steps"])
+    c.oracle_steps(w["steps"])
+    e = c.errors()
+    assert max(e.values()) < 1e-9, e
+
+
+def test_graph_replay_matches_direct():
+    """Graph-replayed steps (caller stream) give the direct launches' result."""
+    s = torch.cuda.Stream()
+    a = Case((16, 8, 8), 2, 4, 0.3, 21, field_scale=0.03, stream=s)
+    b = Case((16, 8, 8), 2, 4, 0.3, 21, field_scale=0.03, stream=None)
+    a.ctx.step(6)
+    b.ctx.step(6)
+    Fa, Fb = a.ctx.get_fields(), b.ctx.get_fields()
+    assert rel_l2(Fa, Fb) < 1e-13
+    assert a.ctx.launch_count() > 0
+
+
+def test_external_drive_fp64():
+    c = Case((16, 8, 8), 2, 2, 0.05, 31)
+    k = 2 * np.pi / 16
+    c.ctx.set_external_drive(0.07, k)
+    c.ctx.step(4)
+    c.oracle_steps(4, drive=(0.07, k))
+    e = c.errors()
+    assert max(e.values()) < 1e-11, e
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_fp32_mixed_one_step_error(p):
+    """FP32-mixed after one step: field and particle error against the FP64 oracle."""
+    c = Case((16, 16, 16), p, 4, 0.3, 40 + p, precision=pic.FP32_MIXED, field_scale=0.05)
+    c.ctx.step(1)
+    c.oracle_steps(1)
+    e = c.errors()
+    assert e["EB"] < 2e-6 and e["J"] < 2e-5 and e["pos"] < 1e-6 and e["mom"] < 2e-6, e
+
+
+def test_fp32_mixed_split_api():
+    c = Case((16, 16, 16), 3, 4, 0.3, 50, precision=pic.FP32_MIXED, field_scale=0.05)
+    c.ctx.gather_push()
+    c.ctx.deposit()
+    c.ctx.yee_step()
+    c.oracle_steps(1)
+    e = c.errors()
+    assert e["EB"] < 2e-6 and e["J"] < 2e-5 and e["pos"] < 1e-6 and e["mom"] < 2e-6, e
+
+
+def test_particles_sorted_by_tile_after_step():
+    c = Case((16, 16, 16), 1, 3, 0.5, 60, precision=pic.FP32_MIXED)
+    c.ctx.step(3)
+    parts = c.ctx.get_particles()
+    T = 8
+    ci = np.floor(parts["x"]).astype(int) // T
+    cj = np.floor(parts["y"]).astype(int) // T
+    ck = np.floor(parts["z"]).astype(int) // T
+    tile = (ci * 2 + cj) * 2 + ck
+    # after the last step particles moved; the order is the one of the last sort,
+    # so the tile sequence is non-decreasing up to particles that left their tile
+    moved = np.mean(np.diff(tile) < 0)
+    assert moved < 0.05
+    assert np.array_equal(np.sort(parts["id"]), np.arange(parts["id"].size))
+
+
+def test_diagnostics_match_oracle():
+    c = Case((16, 8, 8), 3, 2, 0.2, 70, field_scale=0.05)
+    c.ctx.step(2)
+    c.oracle_steps(2)
+    dg = c.ctx.diagnostics()
+    fe = c.O.field_energy(c.g, c.Fref)
+    ke = c.O.kinetic_energy(1.0, c.ref["ux"], c.ref["uy"], c.ref["uz"], c.ref["w"])
+    assert abs(dg["field_energy"] - fe) < 1e-12 * fe
+    assert abs(dg["kinetic_energy"] - ke) < 1e-12 * ke
+    assert abs(dg["charge"] - (-c.ref["w"].sum())) < 1e-12 * c.ref["w"].sum()
+
+
+def test_empty_and_bad_inputs():
+    ctx = pic.Context((8, 8, 8), order=1)
+    with pytest.raises(pic.PicError) as ei:
+        ctx.step(1)
+    assert ei.value.status == pic.PIC_ERR_STATE
+    parts = inputs.uniform_plasma(1, (8, 8, 8), 1)
+    parts["ux"][5] = np.nan
+    with pytest.raises(pic.PicError) as ei:
+        ctx.load_particles(-1.0, 1.0, parts)
+    assert ei.value.status == pic.PIC_ERR_ARG
+    with pytest.raises(pic.PicError) as ei:
+        ctx.deposit()
+    assert ei.value.status == pic.PIC_ERR_STATE
+    # zero particles is a valid load; fields still advance
+    empty = {k: np.zeros(0) for k in pic.PARTICLE_KEYS}
+    ctx.load_particles(-1.0, 1.0, empty)
+    assert ctx.num_particles() == 0
+    ctx.yee_step()
