@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -112,9 +113,33 @@ struct Launch {
 int g_capture_kernels = 0;
 bool g_capturing = false;
 
+// Stale errors of earlier, already handled runtime calls would otherwise be
+// picked up by the cudaGetLastError() that follows each launch.
+cudaError_t clear_stale(const char* where) {
+    cudaError_t s = cudaGetLastError();
+    if (s != cudaSuccess) {
+        g_last_error = std::string("stale CUDA error before ") + where + ": " + cudaGetErrorString(s);
+        if (std::getenv("PIC_DEBUG_SYNC")) std::fprintf(stderr, "libpic: %s\n", g_last_error.c_str());
+    }
+    return s;
+}
+
+bool debug_sync() {
+    static const bool on = std::getenv("PIC_DEBUG_SYNC") != nullptr;
+    return on;
+}
+
 cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)(pic_ctx*)) {
+    clear_stale(name);
     Launch l(c, name);
     cudaError_t e = l.done(fn(c));
+    if (e == cudaSuccess && debug_sync() && !g_capturing) {
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) {
+            g_last_error = std::string("kernel ") + name + ": " + cudaGetErrorString(e);
+            std::fprintf(stderr, "libpic: %s\n", g_last_error.c_str());
+        }
+    }
     if (e == cudaSuccess) {
         if (g_capturing) g_capture_kernels += kernels;
         else c->launches += kernels;
@@ -122,6 +147,8 @@ cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)
     return e;
 }
 
+// With PIC_DEBUG_SYNC set, every counted launch is followed by a stream
+// synchronisation and a failure names the kernel on stderr.
 cudaError_t run_sort(pic_ctx* c) {
     cudaError_t e;
     if ((e = counted(c, "k_hist", 1, pic::launch_hist)) != cudaSuccess) return e;
@@ -365,11 +392,12 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
         for (int i = 0; i < 7; ++i) dsrc[i] = src[i];
     }
     PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    clear_stale("k_load");
     cudaError_t e = pic::launch_load_particles(c, dsrc, n);
     if (e == cudaSuccess) c->launches += n > 0 ? 1 : 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (staged) cudaFree(staged);
-    if (e != cudaSuccess) return cuda_fail(e, "particle load");
+    if (e != cudaSuccess) return cuda_fail(e, n > 0 ? "particle load kernel" : "particle load");
     unsigned h = 0;
     PIC_CUDA(cudaMemcpy(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
     if (h) {
@@ -466,6 +494,7 @@ pic_status pic_get_field(pic_ctx* c, int32_t which, double* dst, int on_device) 
     if (pic_status s = check_ctx(c)) return s;
     if (which < 0 || which > 8 || !dst) return fail(PIC_ERR_ARG, "bad field index or NULL destination");
     const size_t bytes = c->g.C * sizeof(double);
+    clear_stale("field read");
     if (on_device) {
         PIC_CUDA(pic::launch_field_to_f64(c, which, dst));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
@@ -490,6 +519,7 @@ pic_status pic_set_field(pic_ctx* c, int32_t which, const double* src, int on_de
     if (pic_status s = check_ctx(c)) return s;
     if (which < 0 || which > 8 || !src) return fail(PIC_ERR_ARG, "bad field index or NULL source");
     const size_t bytes = c->g.C * sizeof(double);
+    clear_stale("field write");
     if (on_device) {
         PIC_CUDA(pic::launch_field_from_f64(c, which, src));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
@@ -522,6 +552,7 @@ pic_status pic_get_particles(pic_ctx* c, double* x, double* y, double* z, double
     if (pic_status s = check_ctx(c)) return s;
     double* dst[7] = {x, y, z, ux, uy, uz, w};
     if (c->np == 0) return PIC_OK;
+    clear_stale("particle read");
     if (on_device) {
         PIC_CUDA(pic::launch_get_particles(c, dst, id));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
@@ -566,6 +597,7 @@ pic_status pic_diagnostics(pic_ctx* c, double out[4]) {
     if (pic_status s = check_ctx(c)) return s;
     if (!out) return fail(PIC_ERR_ARG, "NULL output");
     PIC_CUDA(cudaMemsetAsync(c->dsum, 0, 8 * sizeof(double), c->stream));
+    clear_stale("diagnostics");
     PIC_CUDA(pic::launch_diagnostics(c, c->dsum));
     c->launches += c->np > 0 ? 3 : 2;
     double h[4];

@@ -64,7 +64,7 @@ struct pic_ctx {
     double q = 0.0, m = 1.0;
     pic::PartBuf P[2];
     int cur = 0;
-    void* old[3] = {nullptr};  // FP64: x0,y0,z0; FP32-mixed: offsets of the old position
+    void* old[6] = {nullptr};  // split API: old position (3 arrays: FP64 x,y,z / FP32-mixed offsets) and move (3)
     int* oldkey = nullptr;     // FP32-mixed: key of the old position
     bool have_old = false;
 
