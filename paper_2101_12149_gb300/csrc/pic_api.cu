@@ -177,12 +177,18 @@ cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
 }
 
 pic_status read_error_word(pic_ctx* c) {
-    unsigned h = 0;
-    PIC_CUDA(cudaMemcpyAsync(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    unsigned hw[4] = {0, 0, 0, 0};
+    PIC_CUDA(cudaMemcpyAsync(hw, c->err, sizeof(hw), cudaMemcpyDeviceToHost, c->stream));
     PIC_CUDA(cudaStreamSynchronize(c->stream));
+    const unsigned h = hw[0];
     if (h == 0) return PIC_OK;
-    PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(hw), c->stream));
     PIC_CUDA(cudaStreamSynchronize(c->stream));
+    if (h & pic::ERRBIT_CHECK) {
+        char buf[160];
+        std::snprintf(buf, sizeof(buf), "self-check failed at site %u, value 0x%08x%08x", hw[1], hw[3], hw[2]);
+        return fail(PIC_ERR_STATE, buf);
+    }
     if (h & pic::ERRBIT_TIMEOUT) return fail(PIC_ERR_TIMEOUT, "a bounded device-side wait ran out");
     if (h & pic::ERRBIT_RANGE) return fail(PIC_ERR_STATE, "a particle cell key was out of range");
     return fail(PIC_ERR_PARTICLE, "a particle became non-finite or moved a cell or more in one step");
@@ -320,8 +326,8 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     c->scan_chunks = int(pic::scan_status_words(C) - 1);
     if ((e = cudaMalloc(&c->scan_status, pic::scan_status_words(C) * sizeof(unsigned long long))) != cudaSuccess)
         return bail(e, "scan state allocation");
-    if ((e = cudaMalloc(&c->err, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
-    if ((e = cudaMemset(c->err, 0, sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaMalloc(&c->err, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
+    if ((e = cudaMemset(c->err, 0, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
     if ((e = cudaMalloc(&c->d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter allocation");
     if ((e = cudaMemset(c->d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMalloc(&c->dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");

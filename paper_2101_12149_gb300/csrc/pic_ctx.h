@@ -15,7 +15,12 @@ enum : unsigned {
     ERRBIT_PARTICLE = 1u,  // non-finite particle or a move of >= 1 cell
     ERRBIT_TIMEOUT = 2u,   // a bounded wait ran out
     ERRBIT_RANGE = 4u,     // a sort key outside [0, C)
+    ERRBIT_CHECK = 8u,     // a self-check of a checking build failed (see check word)
 };
+
+// Checking builds (-DPIC_CHECK) verify indices before memory accesses; the
+// first failure stores {site, value} in err[1], err[2] and the access is
+// skipped.  The error word allocation holds 4 words.
 
 // Particle storage (structure of arrays).  FP64: a[0..6] = x,y,z,ux,uy,uz,w
 // (double), key = tile-major cell key.  FP32-mixed: key = tile-major cell key

@@ -15,6 +15,28 @@ namespace pic {
 
 __device__ __forceinline__ void raise_error(unsigned* err, unsigned bit) { atomicOr(err, bit); }
 
+__device__ __forceinline__ void check_failed(unsigned* err, unsigned site, long long value) {
+    if ((atomicOr(err, ERRBIT_CHECK) & ERRBIT_CHECK) == 0) {
+        err[1] = site;
+        err[2] = unsigned(value);
+        err[3] = unsigned(value >> 32);
+    }
+}
+
+#ifdef PIC_CHECK
+#define PIC_CHECK_OR(cond, err, site, value, action) \
+    do {                                            \
+        if (!(cond)) {                              \
+            ::pic::check_failed(err, site, value);  \
+            action;                                 \
+        }                                           \
+    } while (0)
+#else
+#define PIC_CHECK_OR(cond, err, site, value, action) \
+    do {                                            \
+    } while (0)
+#endif
+
 __device__ __forceinline__ int wrap_once(int i, int n) {
     // i is within one period of [0, n)
     return i < 0 ? i + n : (i >= n ? i - n : i);
@@ -134,9 +156,14 @@ __device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
 //
 // The particle moves from i0 + f0 to i0 + f1 (cell units, |f1 - f0| < 1).
 // The common window of P+2 nodes starts at node i0 + b with
-// b = floor(min(f0,f1) - (P+1)/2) + 1; S0 / dS hold s_P at the old position
-// and the change s_P(new) - s_P(old) on the window.  Both shapes start at
-// window slot 0 or 1, placed with selects so the arrays stay in registers.
+// b = floor(min(f0,f1) - (P+1)/2) + 1, which equals the smaller of the first
+// support nodes of the old and the new shape.  b is taken in that second form,
+// from the same (node, fraction) split that places the weights: the
+// subtraction in the first form rounds for fractions within an ulp of a node
+// (FP32 offsets near 1) and would shift the window by one node.  Both shapes
+// then start at window slot 0 or 1 and are placed with selects so the arrays
+// stay in registers.  S0 / dS hold s_P at the old position and the change
+// s_P(new) - s_P(old) on the window.
 // ---------------------------------------------------------------------------
 template <int P, typename R> struct EsirkAxis {
     static constexpr int NW = P + 2;
@@ -145,16 +172,17 @@ template <int P, typename R> struct EsirkAxis {
     R dS[NW];
 
     __device__ __forceinline__ void init(R f0, R f1) {
-        const R mn = f0 < f1 ? f0 : f1;
-        b = int(rfloor<R>(mn - R(0.5) * R(P + 1))) + 1;
         int first0, first1;
         R w0[P + 1], w1[P + 1];
         Shape<P, R>::weights(f0, first0, w0);
         const R fl1 = rfloor<R>(f1);
-        const int i1 = int(fl1);
         Shape<P, R>::weights(f1 - fl1, first1, w1);
-        const int off0 = first0 - b;       // 0 or 1
-        const int off1 = i1 + first1 - b;  // 0 or 1
+        first1 += int(fl1);
+        b = first0 < first1 ? first0 : first1;
+        // 0 or 1 each when |f1 - f0| < 1; clamped so a violated precondition
+        // cannot index outside the window
+        const int off0 = min(first0 - b, 1);
+        const int off1 = min(first1 - b, 1);
 #pragma unroll
         for (int a = 0; a < NW; ++a) {
             const R s0 = off0 == 0 ? (a <= P ? w0[a] : R(0)) : (a >= 1 ? w0[a - 1] : R(0));

@@ -485,6 +485,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
     const int beg = A.offsets[(int64_t)t * g.cpt];
     const int end = A.offsets[(int64_t)(t + 1) * g.cpt];
     if (end <= beg) return;
+    PIC_CHECK_OR(beg >= 0 && end <= A.np, A.err, 1, ((long long)beg << 32) | unsigned(end), return);
     int oi, oj, ok;
     tile_origin(g, t, oi, oj, ok);
 
@@ -503,6 +504,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 2 + kk, g.n[2]);
             const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+            PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < kSE && b < kSE && kk < kSE, A.err, 2, gidx, continue);
             sEB[c * kSEvol + a * kSEx + b * kSEy + kk] = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
         }
         for (int e = threadIdx.x; e < 3 * kSJvol; e += blockDim.x) sJ[e] = R(0);
@@ -533,7 +535,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
         }
         R u[3] = {A.pa[3][p], A.pa[4][p], A.pa[5][p]};
         const R wq = A.pa[6][p];
-        const bool inside = (key_of(g, cell[0], cell[1], cell[2]) >> lcpt) == t;
+        bool inside = (key_of(g, cell[0], cell[1], cell[2]) >> lcpt) == t;
+#ifdef PIC_CHECK
+        if (inside && !(cell[0] - oi >= 0 && cell[0] - oi < g.T[0] && cell[1] - oj >= 0 && cell[1] - oj < g.T[1] &&
+                        cell[2] - ok >= 0 && cell[2] - ok < g.T[2])) {
+            check_failed(A.err, 3, ((long long)(cell[0] - oi) << 40) | ((long long)(cell[1] - oj) << 20) | (cell[2] - ok));
+            inside = false;
+        }
+#endif
 
         R EB[6];
         if (inside) {
@@ -567,6 +576,15 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
         if (inside) {
             const int base = (cell[0] - oi + 2 + ax[0].b) * kSJx + (cell[1] - oj + 2 + ax[1].b) * kSJy +
                              (cell[2] - ok + 4 + ax[2].b);
+#ifdef PIC_CHECK
+            {
+                const int x0 = cell[0] - oi + 2 + ax[0].b, y0 = cell[1] - oj + 2 + ax[1].b, z0 = cell[2] - ok + 4 + ax[2].b;
+                if (!(x0 >= 0 && x0 + P + 1 < kSJxy && y0 >= 0 && y0 + P + 1 < kSJxy && z0 >= 0 && z0 + P + 1 < kSJz)) {
+                    check_failed(A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8));
+                    continue;
+                }
+            }
+#endif
             esirkepov_smem<P, R>(sJ, sJ + kSJvol, sJ + 2 * kSJvol, base, ax, coef);
         } else {
             deposit_global_slow<P, R>(A, cell, ax, coef);
@@ -614,6 +632,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 4 + 4 * q, g.n[2]);
+            PIC_CHECK_OR(gk + 3 < g.n[2] && ((gk & 3) == 0), A.err, 6, gk, continue);
             float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
             atomicAdd(reinterpret_cast<float4*>(dst), v);
         }

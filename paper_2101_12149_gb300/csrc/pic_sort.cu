@@ -147,6 +147,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ cou
     }
     __syncthreads();
     int run = s_prefix + s_warp[warp] + (incl - tsum);
+    PIC_CHECK_OR(run >= 0, err, 7, run, run = 0);
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t idx = base + i;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ cou
 
 template <typename E>
 __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst, int64_t np, const int* offsets,
-                                                        int* count, int64_t C) {
+                                                        int* count, int64_t C, unsigned* err) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int k = -1;
     if (p < np) {
@@ -173,6 +174,12 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     if (lane == leader) old = atomicSub(count + k, ng);
     old = __shfl_sync(mask, old, leader);
     const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
+#ifdef PIC_CHECK
+    if (!(dest >= 0 && dest < np)) {
+        check_failed(err, 8, dest);
+        return;
+    }
+#endif
 #pragma unroll
     for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = static_cast<const E*>(src.a[i])[p];
     dst.key[dest] = k;
@@ -202,10 +209,10 @@ cudaError_t launch_scatter(pic_ctx* c) {
     const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
     if (c->prec == PIC_FP64)
         k_scatter<double><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                            c->count, c->g.C);
+                                                            c->count, c->g.C, c->err);
     else
         k_scatter<float><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                           c->count, c->g.C);
+                                                           c->count, c->g.C, c->err);
     return cudaGetLastError();
 }
 

@@ -12,7 +12,9 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libpic.so")
+# PIC_LIBRARY may name another build of the same library (e.g. the
+# self-checking libpic_check.so).
+LIB_PATH = os.environ.get("PIC_LIBRARY") or os.path.join(HERE, "_build", "libpic.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pic.h")
 
 PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_STATE, PIC_ERR_PARTICLE, PIC_ERR_TIMEOUT = range(8)

@@ -159,3 +159,30 @@ def test_empty_and_bad_inputs():
     ctx.load_particles(-1.0, 1.0, empty)
     assert ctx.num_particles() == 0
     ctx.yee_step()
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_positions_at_node_boundaries(precision, p):
+    """Offsets within an ulp of a node or a half node (where a rounded window
+    start would shift the Esirkepov stencil) deposit like the oracle."""
+    n = (8, 8, 8)
+    eps = 2.0 ** -24 if precision == pic.FP32_MIXED else 2.0 ** -52
+    fr = np.array([1 - eps, eps, 0.5 - eps, 0.5, 0.5 + eps, 1 - 2 * eps, 0.0, 0.25])
+    m = fr.size
+    base = np.arange(m) % 8
+    parts = {
+        "x": base + fr, "y": (base + 3) % 8 + fr[::-1], "z": (base + 5) % 8 + np.roll(fr, 3),
+        "ux": np.tile([0.3, -0.3], m // 2), "uy": np.tile([-0.2, 0.25], m // 2), "uz": np.tile([1e-3, -1e-3], m // 2),
+        "w": np.full(m, 0.5),
+    }
+    parts = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in parts.items()}
+    c = Case(n, p, 1, 0.0, 80, precision=precision)
+    c.parts = parts
+    c.ref = {k: v.copy() for k, v in parts.items()}
+    c.ctx.load_particles(c.q, c.m, parts)
+    c.ctx.step(1)
+    c.oracle_steps(1)
+    e = c.errors()
+    tol = 1e-12 if precision == pic.FP64 else 1e-5
+    assert max(e.values()) < tol, e
