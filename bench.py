@@ -247,6 +247,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-extras", action="store_true", help="skip FP64, error statement, e2e and CPU legs")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="run the same recipe on an N^3 grid instead of 256^3 (small cases for profiling)")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
+                    help="precision of the timed headline run")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -272,6 +276,8 @@ def main():
 
     w = inputs.WORKLOADS[WORKLOAD]
     n, ppc, order = w["n"], w["ppc"], w["order"]
+    if args.grid:
+        n = (args.grid,) * 3
     C = n[0] * n[1] * n[2]
     N = C * ppc
     host, _keep = pinned_particles(N, torch)
@@ -288,7 +294,8 @@ def main():
         return ctx
 
     # ---- headline: FP32-mixed, device-resident inputs ---------------------
-    ctx = make_ctx(pic.FP32_MIXED)
+    head_prec = pic.FP32_MIXED if args.precision == "fp32" else pic.FP64
+    ctx = make_ctx(head_prec)
     ctx.step(args.warmup)
     ctx.set_timing(True)
     l0 = ctx.launch_count()
@@ -314,23 +321,27 @@ def main():
     ms_tile, n_tile = timings.get("k_tile_step", (0.0, 0))
     avg_tile_s = ms_tile / max(n_tile, 1) / 1e3
     flops = N * flops_per_particle(order)
+    alu_peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
     alu_tf = flops / avg_tile_s / 1e12 if avg_tile_s > 0 else None
-    hbm = bytes_per_launch(N, C, "fp32") / avg_tile_s / 1e9 if avg_tile_s > 0 else None
-    alu_frac = alu_tf / FP32_PEAK_TFLOPS if alu_tf else None
+    hbm = bytes_per_launch(N, C, args.precision) / avg_tile_s / 1e9 if avg_tile_s > 0 else None
+    alu_frac = alu_tf / alu_peak if alu_tf else None
     hbm_frac = hbm / peaks["hbm_gbs"] if hbm else None
-    traffic = profiled_traffic("k_tile_step", "fp32")
-    roof_alu = {"bound": "alu", "achieved": alu_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": alu_frac,
+    traffic = profiled_traffic("k_tile_step", args.precision) if not args.grid else None
+    roof_alu = {"bound": "alu", "achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
                 "traffic": traffic, "kernel": "k_tile_step",
-                "note": "FP32 ALU roof derived from 152 SMs x 128 lanes x 2 x 2.07 GHz; algorithmic flops "
-                        f"{flops_per_particle(order)} per particle"}
+                "note": ("FP32 ALU roof derived from 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
+                         else "FP64 roof: GB300 dense FP64 1.25 TFLOP/s") +
+                        f"; algorithmic flops {flops_per_particle(order)} per particle"}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
                 "traffic": traffic, "kernel": "k_tile_step", "peak_source": f"{peak_kind} hbm_gbs"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32-mixed", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": "256^3", "ppc": ppc, "particles": N, "order": order,
-                   "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": 1, "precision": "fp32_mixed",
+        "vs_baseline": None, "dtype": "f32-mixed" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD if not args.grid else f"{WORKLOAD} recipe at {args.grid}^3",
+                   "grid": f"{n[0]}^3", "ppc": ppc, "particles": N, "order": order,
+                   "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": 1,
+                   "precision": "fp32_mixed" if args.precision == "fp32" else "fp64",
                    "l2": "inputs larger than L2 (4.8 GB of particle state per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof_alu if (alu_frac or 0) >= (hbm_frac or 0) else roof_hbm,
