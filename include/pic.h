@@ -160,6 +160,35 @@ pic_status pic_get_timing(pic_ctx* ctx, int32_t cap, const char** names, double*
  * kernel node). */
 pic_status pic_launch_count(pic_ctx* ctx, int64_t* n);
 
+/* Counting sort of caller-owned keys that allocates nothing.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, e.g. code running while a CUDA stream is
+ * being captured (where cudaMalloc is not allowed), or hosts that hand a
+ * library only the buffers it may touch.  It runs the same histogram,
+ * single-pass scan and scatter as the particle sort of pic_step on
+ * caller arrays, with its scratch (per-bin counts, the scan's look-back
+ * words, an error word) in one static device array of about 16 MiB that
+ * every GPU loading the library holds until the process exits.
+ *
+ * keys: n int32 bin indices in [0, nbins) (device memory).
+ * offsets: nbins+1 int32 (device, written): offsets[b] is the first slot of
+ *   bin b, offsets[nbins] = n (exclusive prefix sum of the histogram).
+ * perm: n int32 (device, written): perm[slot] = index of the key placed
+ *   there; bin b holds slots [offsets[b], offsets[b+1]), in no set order.
+ * nbins: 1 .. 4,194,304 (the scratch limit); larger values give PIC_ERR_ARG.
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call clears what it uses and waits for
+ * completion.  All calls share the one scratch array, so calls that overlap
+ * on the GPU (other threads or streams) race: serialise them.
+ * PIC_ERR_ARG: bad sizes, NULL arrays, or a key outside [0, nbins);
+ * PIC_ERR_TIMEOUT: a bounded device-side wait ran out. */
+pic_status pic_sort_keys_noalloc(const int32_t* keys, int64_t n, int32_t nbins, int32_t* offsets,
+                                 int32_t* perm, void* cuda_stream);
+
 /* Release every buffer of the context (NULL is allowed). */
 pic_status pic_destroy(pic_ctx* ctx);
 

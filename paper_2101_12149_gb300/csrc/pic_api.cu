@@ -251,6 +251,11 @@ void destroy_timing(pic_ctx* c) {
 
 }  // namespace
 
+namespace pic {
+// lets other translation units report through pic_last_error()
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pic
+
 extern "C" {
 
 const char* pic_last_error(void) { return g_last_error.c_str(); }

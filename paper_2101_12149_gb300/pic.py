@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
             "pic_get_timing": [P, I32, P, P, P, ct.POINTER(I32)],
             "pic_launch_count": [P, ct.POINTER(I64)],
             "pic_destroy": [P],
+            "pic_sort_keys_noalloc": [P, I64, I32, P, P, P],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -247,3 +248,15 @@ class Context:
         v = ct.c_int64()
         _check(self.lib.pic_launch_count(self.h, ct.byref(v)))
         return v.value
+
+
+def sort_keys_noalloc(keys, nbins, offsets, perm, stream=None):
+    """pic_sort_keys_noalloc on device int32 tensors: offsets (nbins+1) and
+    perm (len(keys)) are written.  The call allocates no device memory."""
+    lib = load_library()
+    n = int(keys.numel())
+    s = None
+    if stream is not None:
+        s = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib.pic_sort_keys_noalloc(ct.c_void_p(keys.data_ptr()), n, int(nbins), ct.c_void_p(offsets.data_ptr()),
+                                     ct.c_void_p(perm.data_ptr()), s))
