@@ -46,6 +46,7 @@ void free_particles(pic_ctx* c) {
     cudaFree(c->old[0]);
     for (auto& o : c->old) o = nullptr;
     c->oldkey = nullptr;
+    c->outl = nullptr;
     c->np = c->cap = 0;
     c->have_old = false;
 }
@@ -66,10 +67,11 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
         c->P[b].id = reinterpret_cast<int*>(base + 7 * per + ints);
     }
     char* ob = nullptr;
-    cudaError_t e = cudaMalloc(&ob, 6 * per + ints);
+    cudaError_t e = cudaMalloc(&ob, 6 * per + 2 * ints);
     if (e != cudaSuccess) return e;
     for (int i = 0; i < 6; ++i) c->old[i] = ob + i * per;
     c->oldkey = reinterpret_cast<int*>(ob + 6 * per);
+    c->outl = reinterpret_cast<int*>(ob + 6 * per + ints);
     c->cap = int64_t(cap);
     return cudaSuccess;
 }
@@ -172,7 +174,7 @@ cudaError_t run_yee(pic_ctx* c) {
 cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
     cudaError_t e;
     if (with_sort && (e = run_sort(c)) != cudaSuccess) return e;
-    if ((e = counted(c, "k_tile_step", 1, pic::launch_tile_step)) != cudaSuccess) return e;
+    if ((e = counted(c, "k_tile_step", 2, pic::launch_tile_step)) != cudaSuccess) return e;
     return run_yee(c);
 }
 
@@ -294,22 +296,40 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     c->rsize = D.precision == PIC_FP64 ? 8 : 4;
     cudaGetDevice(&c->device);
     pic::Geom& g = c->g;
+    // Tiles: 4 x 4 x 32 cells when the grid allows (a warp's lanes then walk
+    // one z-row of cells), else the largest powers of two up to 8 per axis.
+    int T[3];
+    const bool given = D.tile[0] > 0 || D.tile[1] > 0 || D.tile[2] > 0;
+    if (!given) {
+        if (D.n[0] % 4 == 0 && D.n[1] % 4 == 0 && D.n[2] % 32 == 0) {
+            T[0] = 4, T[1] = 4, T[2] = 32;
+        } else {
+            for (int a = 0; a < 3; ++a) {
+                T[a] = 8;
+                while (T[a] > 1 && D.n[a] % T[a] != 0) T[a] >>= 1;
+            }
+        }
+    } else {
+        for (int a = 0; a < 3; ++a) T[a] = D.tile[a];
+    }
+    for (int a = 0; a < 3; ++a)
+        if (!is_pow2(T[a]) || D.n[a] % T[a] != 0) {
+            delete c;
+            return fail(PIC_ERR_ARG, "tile extents must be powers of two dividing the grid");
+        }
+    if (T[0] <= 8 && T[1] <= 8 && T[2] <= 8) c->layout = 0;
+    else if (T[0] <= 4 && T[1] <= 4 && T[2] <= 32) c->layout = 1;
+    else {
+        delete c;
+        return fail(PIC_ERR_ARG, "tiles must fit 8x8x8 or 4x4x32 cells");
+    }
     for (int a = 0; a < 3; ++a) {
         g.n[a] = D.n[a];
         g.d[a] = D.d[a];
         g.L[a] = D.n[a] * D.d[a];
-        int T = D.tile[a];
-        if (T == 0) {
-            T = 8;
-            while (T > 1 && D.n[a] % T != 0) T >>= 1;
-        }
-        if (!is_pow2(T) || D.n[a] % T != 0 || T > 64) {
-            delete c;
-            return fail(PIC_ERR_ARG, "tile extents must be powers of two (<= 64) dividing the grid");
-        }
-        g.T[a] = T;
-        g.lT[a] = ilog2(T);
-        g.nt[a] = D.n[a] / T;
+        g.T[a] = T[a];
+        g.lT[a] = ilog2(T[a]);
+        g.nt[a] = D.n[a] / T[a];
     }
     g.cpt = g.T[0] * g.T[1] * g.T[2];
     g.C = C;
@@ -331,8 +351,9 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     c->scan_chunks = int(pic::scan_status_words(C) - 1);
     if ((e = cudaMalloc(&c->scan_status, pic::scan_status_words(C) * sizeof(unsigned long long))) != cudaSuccess)
         return bail(e, "scan state allocation");
-    if ((e = cudaMalloc(&c->err, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
-    if ((e = cudaMemset(c->err, 0, 4 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+    if ((e = cudaMalloc(&c->err, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
+    if ((e = cudaMemset(c->err, 0, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
+    if ((e = pic::configure_tile_kernels(c)) != cudaSuccess) return bail(e, "tile kernel configuration");
     if ((e = cudaMalloc(&c->d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter allocation");
     if ((e = cudaMemset(c->d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMalloc(&c->dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");
@@ -402,19 +423,29 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
     } else {
         for (int i = 0; i < 7; ++i) dsrc[i] = src[i];
     }
-    PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(unsigned), c->stream));
+    PIC_CUDA(cudaMemsetAsync(c->err, 0, 8 * sizeof(unsigned), c->stream));
     clear_stale("k_load");
     cudaError_t e = pic::launch_load_particles(c, dsrc, n);
     if (e == cudaSuccess) c->launches += n > 0 ? 1 : 0;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (staged) cudaFree(staged);
     if (e != cudaSuccess) return cuda_fail(e, n > 0 ? "particle load kernel" : "particle load");
-    unsigned h = 0;
-    PIC_CUDA(cudaMemcpy(&h, c->err, sizeof(unsigned), cudaMemcpyDeviceToHost));
-    if (h) {
-        cudaMemset(c->err, 0, sizeof(unsigned));
+    unsigned hw[8];
+    PIC_CUDA(cudaMemcpy(hw, c->err, sizeof(hw), cudaMemcpyDeviceToHost));
+    PIC_CUDA(cudaMemset(c->err, 0, sizeof(hw)));
+    if (hw[0]) {
         c->np = 0;
         return fail(PIC_ERR_ARG, "non-finite particle value");
+    }
+    {
+        unsigned long long bits = (unsigned long long)hw[6] | ((unsigned long long)hw[7] << 32);
+        double wm;
+        std::memcpy(&wm, &bits, sizeof(wm));
+        c->w_max = n > 0 ? wm : 0.0;
+    }
+    if (c->graph) {  // the deposit scale is a kernel argument baked into the graph
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
     }
     e = run_sort(c);
     if (e != cudaSuccess) return cuda_fail(e, "initial sort");

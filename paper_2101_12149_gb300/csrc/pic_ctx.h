@@ -6,7 +6,7 @@
 #include <cstdint>
 #include <string>
 
-#include "../../include/pic.h"
+#include "pic.h"
 
 namespace pic {
 
@@ -67,11 +67,15 @@ struct pic_ctx {
 
     int64_t np = 0, cap = 0;
     double q = 0.0, m = 1.0;
+    double w_max = 0.0;  // largest |weight| loaded (fixed-point scale of the FP32-mixed deposit)
     pic::PartBuf P[2];
     int cur = 0;
     void* old[6] = {nullptr};  // split API: old position (3 arrays: FP64 x,y,z / FP32-mixed offsets) and move (3)
     int* oldkey = nullptr;     // FP32-mixed: key of the old position
     bool have_old = false;
+
+    int* outl = nullptr;     // outsider list of the tile kernel [cap]
+    int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32
 
     int* count = nullptr;    // per-cell particle counts [C]
     int* offsets = nullptr;  // exclusive scan of count [C+1]; tile t owns [offsets[t*cpt], offsets[(t+1)*cpt])
@@ -80,7 +84,7 @@ struct pic_ctx {
     bool sorted = false;       // particles are in tile order of the current offsets
     int since_sort = 0;
 
-    unsigned* err = nullptr;       // device error word
+    unsigned* err = nullptr;       // device error word [4] + outsider count [1] (8 words allocated)
     long long* d_step = nullptr;   // device copy of the step counter (drive time)
     double* dsum = nullptr;        // diagnostics scratch
     int64_t step = 0;
@@ -102,6 +106,7 @@ namespace pic {
 // launchers (pic_kernels.cu)
 cudaError_t launch_zero_fields(pic_ctx* c, int first, int count);
 cudaError_t launch_tile_step(pic_ctx* c);        // fused gather+push+deposit, tile kernel
+cudaError_t configure_tile_kernels(pic_ctx* c);
 cudaError_t launch_gather_push_global(pic_ctx* c);
 cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);

@@ -14,6 +14,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "pic_ctx.h"
 #include "pic_device.cuh"
@@ -80,8 +81,12 @@ template <typename R> struct StepArgs {
     int* oldkey;
     const int* offsets;
     unsigned* err;
+    int* outn;   // outsider count (device)
+    int* outl;   // outsider particle indices
     const long long* step;
     double drive_amp, drive_k;
+    float vscale;       // FP32-mixed fixed-point scale of the deposit (2^30 / max|coef|)
+    double inv_vscale;
     int64_t np;
 };
 
@@ -105,9 +110,21 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.oldkey = c->oldkey;
     a.offsets = c->offsets;
     a.err = c->err;
+    a.outn = reinterpret_cast<int*>(c->err + 4);
+    a.outl = c->outl;
     a.step = c->d_step;
     a.drive_amp = c->drive_amp;
     a.drive_k = c->drive_k;
+    {
+        double cmax = 0.0;
+        for (int d = 0; d < 3; ++d) {
+            const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
+            cmax = fmax(cmax, fabs(c->q) * c->w_max / (c->dt * c->g.d[t1] * c->g.d[t2]));
+        }
+        if (!(cmax > 0.0)) cmax = 1.0;
+        a.vscale = float(1073741824.0 / cmax);
+        a.inv_vscale = 1.0 / double(a.vscale);
+    }
     a.np = c->np;
     return a;
 }
@@ -351,50 +368,42 @@ __device__ __forceinline__ void renormalise(float f1, int cell, int n, int& ncel
     nf = f;
 }
 
-// Slow paths of the tile kernel for a particle whose cell lies outside the
-// CTA's tile (possible only between sorts): global gather / global atomics.
-// Kept out of line so they do not add to the register pressure of the
-// shared-memory fast path.
-template <int P, typename R>
-__device__ __noinline__ void gather_global_slow(const StepArgs<R>& A, const int cell[3], const R f0[3], R EB[6]) {
-    GatherW<P, R> G;
-    int fn[3], fs[3];
-    gather_weights<P, R>(f0, G, fn, fs);
-    offsets_global<P, R>(G, A.g, cell, fn, fs);
-    gather6<P, R>(G, A.E, A.B, EB);
-}
-
-template <int P, typename R>
-__device__ __noinline__ void deposit_global_slow(const StepArgs<R>& A, const int cell[3], const EsirkAxis<P, R>* ax,
-                                                  const R* coef) {
-    JTarget<P, R> jt;
-    jtarget_global<P, R>(jt, A.g, A.J, cell, ax);
-    esirkepov_deposit<P, R>(ax, coef, jt);
-}
-
 // ---------------------------------------------------------------------------
 // fused tile kernel
 // ---------------------------------------------------------------------------
-// Shared-memory layout of one tile, sized for the largest tile (8 cells per
-// axis); smaller tiles use the low corner of the same boxes, so all strides
-// are compile-time constants and every shared access is base + immediate.
-//   E/B box: cells [-2, T+2) per axis  -> 12 x 12 x 12 per component
-//   J box:   x, y [-2, T+3), z [-4, T+4) -> 13 x 13 x 16 per component
-// (z padded so the flush moves aligned float4s).
-constexpr int kMaxTile = 8;
-constexpr int kSE = kMaxTile + 4;
-constexpr int kSEx = kSE * kSE, kSEy = kSE;
-constexpr int kSEvol = kSE * kSE * kSE;
-constexpr int kSJxy = kMaxTile + 5;
-constexpr int kSJz = kMaxTile + 8;
-constexpr int kSJx = kSJxy * kSJz, kSJy = kSJz;
-constexpr int kSJvol = kSJxy * kSJxy * kSJz;
-
-template <typename R> constexpr size_t tile_smem_bytes() { return sizeof(R) * (6 * size_t(kSEvol) + 3 * size_t(kSJvol)); }
+// Shared-memory boxes of one tile, sized for the largest tile of the layout
+// (MX x MY x MZ cells); smaller tiles use the low corner, so every stride is a
+// compile-time constant and each shared access is base + immediate.
+//   E/B box: cells [-2, T+2) per axis, z rows of pitch EP
+//   J box:   x, y [-2, T+3), z [-4, T+4), z rows of pitch JP (z padded so the
+//            flush moves aligned float4s)
+// Two layouts.  4 x 4 x 32 when nz is a multiple of 32: the lanes of a warp
+// take 32 consecutive cells in tile order (one z-row, or the end of one and
+// the start of the next), and with row and plane pitches that are multiples
+// of 32 words the bank of every access is its z index, so gathers and
+// deposits hit 32 distinct banks whatever the per-lane staggering offsets.
+// Otherwise up to 8 x 8 x 8 cells.
+template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
+    static constexpr int EX = MX + 4, EY = MY + 4, EZ = MZ + 4;
+    static constexpr int eY = EP, eX = EY * EP, eVol = EX * EY * EP;
+    static constexpr int JX = MX + 5, JY = MY + 5, JZ = MZ + 8;
+    static constexpr int jY = JP, jX = JY * JP, jVol = JX * JY * JP;
+    static_assert(EP >= EZ && JP >= JZ && JP % 4 == 0, "row pitches");
+    // FP64: J box of doubles (3 components); FP32-mixed: J box of fixed-point
+    // (lo, hi) int32 pairs (3 components x 2 arrays)
+    template <typename R> static constexpr size_t smem_bytes() {
+        return sizeof(R) == 8 ? 8 * (6 * size_t(eVol) + 3 * size_t(jVol)) : 4 * (6 * size_t(eVol) + 6 * size_t(jVol));
+    }
+};
+// FP64 keeps compact pitches: the bank-conflict-free ones would not fit its
+// shared memory, and the FP64 path is bound by FP64 arithmetic.
+template <typename R>
+using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64>, Layout<4, 4, 32, 36, 40>>;
+using LayoutCube = Layout<8, 8, 8, 12, 20>;
 
 // Gather of one component from the staged box: `base` points at the first
-// stencil node; strides are compile-time.
-template <int P, typename R>
+// stencil node.
+template <int P, typename R, class LY>
 __device__ __forceinline__ R interp_smem(const R* __restrict__ base, const R* wx, const R* wy, const R* wz) {
     R acc = R(0);
 #pragma unroll
@@ -404,7 +413,7 @@ __device__ __forceinline__ R interp_smem(const R* __restrict__ base, const R* wx
         for (int j = 0; j <= P; ++j) {
             R az = R(0);
 #pragma unroll
-            for (int k = 0; k <= P; ++k) az += wz[k] * base[i * kSEx + j * kSEy + k];
+            for (int k = 0; k <= P; ++k) az += wz[k] * base[i * LY::eX + j * LY::eY + k];
             ay += wy[j] * az;
         }
         acc += wx[i] * ay;
@@ -414,8 +423,8 @@ __device__ __forceinline__ R interp_smem(const R* __restrict__ base, const R* wx
 
 // Esirkepov deposit of one particle into the staged J box; `base` is the
 // element offset of window slot (0,0,0).  Same arithmetic as
-// esirkepov_deposit, with compile-time strides.
-template <int P, typename R>
+// esirkepov_deposit (the global-memory form).
+template <int P, typename R, class LY>
 __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict__ J1, R* __restrict__ J2, int base,
                                                const EsirkAxis<P, R> ax[3], const R coef[3]) {
     constexpr int NW = P + 2;
@@ -435,7 +444,7 @@ __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict
                 const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
                 const R Q = ax[1].S0[j] * Az + ax[1].dS[j] * Bz;
 #pragma unroll
-                for (int i = 0; i < NW - 1; ++i) atomicAdd(jx + i * kSJx + j * kSJy + k, cum[i] * Q);
+                for (int i = 0; i < NW - 1; ++i) atomicAdd(jx + i * LY::jX + j * LY::jY + k, cum[i] * Q);
             }
     }
     {
@@ -451,7 +460,7 @@ __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict
                 const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
                 const R Q = ax[0].S0[i] * Az + ax[0].dS[i] * Bz;
 #pragma unroll
-                for (int j = 0; j < NW - 1; ++j) atomicAdd(jy + i * kSJx + j * kSJy + k, cum[j] * Q);
+                for (int j = 0; j < NW - 1; ++j) atomicAdd(jy + i * LY::jX + j * LY::jY + k, cum[j] * Q);
             }
     }
     {
@@ -467,18 +476,165 @@ __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict
                 const R By = R(0.5) * ax[1].S0[j] + R(1.0 / 3.0) * ax[1].dS[j];
                 const R Q = ax[0].S0[i] * Ay + ax[0].dS[i] * By;
 #pragma unroll
-                for (int k = 0; k < NW - 1; ++k) atomicAdd(jz + i * kSJx + j * kSJy + k, cum[k] * Q);
+                for (int k = 0; k < NW - 1; ++k) atomicAdd(jz + i * LY::jX + j * LY::jY + k, cum[k] * Q);
             }
     }
 }
 
-template <int P, typename R>
-__global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(StepArgs<R> A) {
+// FP32-mixed deposit into the staged J box in exact fixed point.
+//
+// Every Esirkepov contribution obeys |v| <= |coef|: the cumulative sum of dS
+// is a difference of two cumulative shape distributions, bounded by the move
+// (< 1 cell), and Q <= 1.  With vscale = 2^30 / max|coef|, x = rn(v vscale)
+// fits in 31 bits; it is split as x = hi 2^15 + lo (hi = x rounded to a
+// multiple of 2^15, |lo| <= 2^14) and the halves go to two int32 arrays by
+// native shared-memory integer reductions.  Integer sums are exact and
+// independent of order; with at most 65535 particles per tile neither sum
+// can overflow (65535 * 2^15 < 2^31).  The flush rebuilds hi 2^15 + lo.
+__device__ __forceinline__ void red_fixed(int* lo, int* hi, float v, float vscale) {
+    const int x = __float2int_rn(v * vscale);
+    const int h = (x + (1 << 14)) >> 15;
+    const int l = x - (h << 15);
+    atomicAdd(lo, l);
+    atomicAdd(hi, h);
+}
+
+template <int P, class LY>
+__device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int base, const EsirkAxis<P, float> ax[3],
+                                                     const float coef[3], float vscale) {
+    constexpr int NW = P + 2;
+    int* jx = sJ + base;                  // lo of J_x; hi at + jVol
+    int* jy = sJ + 2 * LY::jVol + base;   // lo of J_y
+    int* jz = sJ + 4 * LY::jVol + base;   // lo of J_z
+    constexpr int H = LY::jVol;
+    {
+        float cum[NW - 1];
+        float run = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
+#pragma unroll
+        for (int j = 0; j < NW; ++j)
+#pragma unroll
+            for (int kk = 0; kk < NW; ++kk) {
+                const float Az = ax[2].S0[kk] + 0.5f * ax[2].dS[kk];
+                const float Bz = 0.5f * ax[2].S0[kk] + (1.0f / 3.0f) * ax[2].dS[kk];
+                const float Q = ax[1].S0[j] * Az + ax[1].dS[j] * Bz;
+#pragma unroll
+                for (int i = 0; i < NW - 1; ++i) {
+                    const int o = i * LY::jX + j * LY::jY + kk;
+                    red_fixed(jx + o, jx + H + o, cum[i] * Q, vscale);
+                }
+            }
+    }
+    {
+        float cum[NW - 1];
+        float run = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int kk = 0; kk < NW; ++kk) {
+                const float Az = ax[2].S0[kk] + 0.5f * ax[2].dS[kk];
+                const float Bz = 0.5f * ax[2].S0[kk] + (1.0f / 3.0f) * ax[2].dS[kk];
+                const float Q = ax[0].S0[i] * Az + ax[0].dS[i] * Bz;
+#pragma unroll
+                for (int j = 0; j < NW - 1; ++j) {
+                    const int o = i * LY::jX + j * LY::jY + kk;
+                    red_fixed(jy + o, jy + H + o, cum[j] * Q, vscale);
+                }
+            }
+    }
+    {
+        float cum[NW - 1];
+        float run = 0.f;
+#pragma unroll
+        for (int w = 0; w < NW - 1; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
+#pragma unroll
+        for (int i = 0; i < NW; ++i)
+#pragma unroll
+            for (int j = 0; j < NW; ++j) {
+                const float Ay = ax[1].S0[j] + 0.5f * ax[1].dS[j];
+                const float By = 0.5f * ax[1].S0[j] + (1.0f / 3.0f) * ax[1].dS[j];
+                const float Q = ax[0].S0[i] * Ay + ax[0].dS[i] * By;
+#pragma unroll
+                for (int kk = 0; kk < NW - 1; ++kk) {
+                    const int o = i * LY::jX + j * LY::jY + kk;
+                    red_fixed(jz + o, jz + H + o, cum[kk] * Q, vscale);
+                }
+            }
+    }
+}
+
+// Load a particle's cell, in-cell fraction, momentum and weight.
+template <typename R>
+__device__ __forceinline__ void load_particle(const StepArgs<R>& A, int p, int cell[3], R f0[3], double xg0[3],
+                                              R u[3], R& wq) {
+    const Geom& g = A.g;
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xg0[a] = double(A.pa[a][p]);
+            double f;
+            split_pos(xg0[a], g.d[a], g.n[a], cell[a], f);
+            f0[a] = R(f);
+        }
+    } else {
+        cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f0[a] = A.pa[a][p];
+            xg0[a] = 0.0;
+        }
+    }
+    u[0] = A.pa[3][p];
+    u[1] = A.pa[4][p];
+    u[2] = A.pa[5][p];
+    wq = A.pa[6][p];
+}
+
+// Store the moved particle in place: momentum, wrapped position, new cell key.
+template <typename R>
+__device__ __forceinline__ void store_particle(const StepArgs<R>& A, int p, const int cell[3], const Moved<R>& mv) {
+    const Geom& g = A.g;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) A.pa[3 + a][p] = mv.u[a];
+    int nc[3];
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double xw = wrap_pos(mv.xg1[a], g.L[a]);
+            A.pa[a][p] = R(xw);
+            double f;
+            split_pos(xw, g.d[a], g.n[a], nc[a], f);
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            float nf;
+            renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
+            A.pa[a][p] = R(nf);
+        }
+    }
+    A.key[p] = key_of(g, nc[0], nc[1], nc[2]);
+}
+
+// Gather + push + advance + Esirkepov for one tile of cells per CTA.
+// Particles whose cell is not in the tile (possible only between sorts) are
+// appended to the outsider list and left for k_outsiders.
+// Block size of the tile kernel: FP32-mixed 512 threads (one CTA per SM, its
+// shared memory holding the fixed-point J box), FP64 256.
+template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
+
+template <int P, typename R, class LY>
+__global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* sm = reinterpret_cast<R*>(smem_raw);
     const Geom& g = A.g;
-    R* sEB = sm;               // 6 * kSEvol
-    R* sJ = sm + 6 * kSEvol;   // 3 * kSJvol
+    constexpr bool kFixed = sizeof(R) == 4;
+    R* sEB = sm;                  // 6 * eVol
+    R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
+    int* sJi = reinterpret_cast<int*>(sJ);
 
     const int t = blockIdx.x;
     const int lcpt = g.lT[0] + g.lT[1] + g.lT[2];
@@ -489,7 +645,7 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
     int oi, oj, ok;
     tile_origin(g, t, oi, oj, ok);
 
-    // stage E, B of the tile and a halo of 2 (wrapped) into the fixed-stride box
+    // stage E, B of the tile and a halo of 2 (wrapped)
     {
         const int ex = g.T[0] + 4, ey = g.T[1] + 4, ez = g.T[2] + 4;
         const int vol = ex * ey * ez;
@@ -504,119 +660,81 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 2 + kk, g.n[2]);
             const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
-            PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < kSE && b < kSE && kk < kSE, A.err, 2, gidx, continue);
-            sEB[c * kSEvol + a * kSEx + b * kSEy + kk] = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+            PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx, continue);
+            sEB[c * LY::eVol + a * LY::eX + b * LY::eY + kk] = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
         }
-        for (int e = threadIdx.x; e < 3 * kSJvol; e += blockDim.x) sJ[e] = R(0);
+        if (kFixed)
+            for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
+        else
+            for (int e = threadIdx.x; e < 3 * LY::jVol; e += blockDim.x) sJ[e] = R(0);
     }
     __syncthreads();
 
-    // contiguous chunk of the tile's (cell-sorted) particles per thread
+    // The tile's particles are cell-sorted; consecutive lanes take consecutive
+    // runs of about one cell's worth of particles, so the lanes of a warp work
+    // in neighbouring cells (distinct shared-memory banks).
     const int cnt = end - beg;
-    const int per = (cnt + blockDim.x - 1) / blockDim.x;
-    const int s0 = beg + threadIdx.x * per;
-    const int s1 = min(s0 + per, end);
-    for (int p = s0; p < s1; ++p) {
-        int cell[3];
-        R f0[3];
-        double xg0[3] = {0.0, 0.0, 0.0};
-        if (sizeof(R) == 8) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                xg0[a] = double(A.pa[a][p]);
-                double f;
-                split_pos(xg0[a], g.d[a], g.n[a], cell[a], f);
-                f0[a] = R(f);
+    const int run = max(1, (cnt + (g.cpt >> 1)) / g.cpt);
+    const int nrun = (cnt + run - 1) / run;
+    for (int rr = threadIdx.x; rr < nrun; rr += blockDim.x) {
+        const int p0 = beg + rr * run;
+        const int p1 = min(p0 + run, end);
+        for (int p = p0; p < p1; ++p) {
+            int cell[3];
+            R f0[3], u[3], wq;
+            double xg0[3];
+            load_particle<R>(A, p, cell, f0, xg0, u, wq);
+            const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
+            // the fixed-point sums are exact for up to 65535 particles per tile
+            const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
+                                unsigned(lk) < unsigned(g.T[2]) && (!kFixed || p - beg < 65535);
+            if (!inside) {
+                const int slot = atomicAdd(A.outn, 1);
+                A.outl[slot] = p;
+                continue;
             }
-        } else {
-            cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) f0[a] = A.pa[a][p];
-        }
-        R u[3] = {A.pa[3][p], A.pa[4][p], A.pa[5][p]};
-        const R wq = A.pa[6][p];
-        bool inside = (key_of(g, cell[0], cell[1], cell[2]) >> lcpt) == t;
-#ifdef PIC_CHECK
-        if (inside && !(cell[0] - oi >= 0 && cell[0] - oi < g.T[0] && cell[1] - oj >= 0 && cell[1] - oj < g.T[1] &&
-                        cell[2] - ok >= 0 && cell[2] - ok < g.T[2])) {
-            check_failed(A.err, 3, ((long long)(cell[0] - oi) << 40) | ((long long)(cell[1] - oj) << 20) | (cell[2] - ok));
-            inside = false;
-        }
-#endif
-
-        R EB[6];
-        if (inside) {
-            GatherW<P, R> G;
-            int fn[3], fs[3];
-            gather_weights<P, R>(f0, G, fn, fs);
-            const int li = cell[0] - oi + 2, lj = cell[1] - oj + 2, lk = cell[2] - ok + 2;
-            // per component: first stencil node (node-centred n / staggered s per axis)
-            const int bnx = (li + fn[0]) * kSEx, bsx = (li + fs[0]) * kSEx;
-            const int bny = (lj + fn[1]) * kSEy, bsy = (lj + fs[1]) * kSEy;
-            const int bnz = lk + fn[2], bsz = lk + fs[2];
-            EB[0] = interp_smem<P, R>(sEB + 0 * kSEvol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
-            EB[1] = interp_smem<P, R>(sEB + 1 * kSEvol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
-            EB[2] = interp_smem<P, R>(sEB + 2 * kSEvol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
-            EB[3] = interp_smem<P, R>(sEB + 3 * kSEvol + bnx + bsy + bsz, G.wn[0], G.ws[1], G.ws[2]);
-            EB[4] = interp_smem<P, R>(sEB + 4 * kSEvol + bsx + bny + bsz, G.ws[0], G.wn[1], G.ws[2]);
-            EB[5] = interp_smem<P, R>(sEB + 5 * kSEvol + bsx + bsy + bnz, G.ws[0], G.ws[1], G.wn[2]);
-        } else {
-            gather_global_slow<P, R>(A, cell, f0, EB);
-        }
-        Moved<R> mv;
-        push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
-        if (!mv.ok) {
-            raise_error(A.err, ERRBIT_PARTICLE);
-            continue;
-        }
-        EsirkAxis<P, R> ax[3];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
-        const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
-        if (inside) {
-            const int base = (cell[0] - oi + 2 + ax[0].b) * kSJx + (cell[1] - oj + 2 + ax[1].b) * kSJy +
-                             (cell[2] - ok + 4 + ax[2].b);
-#ifdef PIC_CHECK
+            R EB[6];
             {
-                const int x0 = cell[0] - oi + 2 + ax[0].b, y0 = cell[1] - oj + 2 + ax[1].b, z0 = cell[2] - ok + 4 + ax[2].b;
-                if (!(x0 >= 0 && x0 + P + 1 < kSJxy && y0 >= 0 && y0 + P + 1 < kSJxy && z0 >= 0 && z0 + P + 1 < kSJz)) {
-                    check_failed(A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8));
-                    continue;
-                }
+                GatherW<P, R> G;
+                int fn[3], fs[3];
+                gather_weights<P, R>(f0, G, fn, fs);
+                const int bnx = (li + 2 + fn[0]) * LY::eX, bsx = (li + 2 + fs[0]) * LY::eX;
+                const int bny = (lj + 2 + fn[1]) * LY::eY, bsy = (lj + 2 + fs[1]) * LY::eY;
+                const int bnz = lk + 2 + fn[2], bsz = lk + 2 + fs[2];
+                EB[0] = interp_smem<P, R, LY>(sEB + 0 * LY::eVol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
+                EB[1] = interp_smem<P, R, LY>(sEB + 1 * LY::eVol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
+                EB[2] = interp_smem<P, R, LY>(sEB + 2 * LY::eVol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
+                EB[3] = interp_smem<P, R, LY>(sEB + 3 * LY::eVol + bnx + bsy + bsz, G.wn[0], G.ws[1], G.ws[2]);
+                EB[4] = interp_smem<P, R, LY>(sEB + 4 * LY::eVol + bsx + bny + bsz, G.ws[0], G.wn[1], G.ws[2]);
+                EB[5] = interp_smem<P, R, LY>(sEB + 5 * LY::eVol + bsx + bsy + bnz, G.ws[0], G.ws[1], G.wn[2]);
             }
-#endif
-            esirkepov_smem<P, R>(sJ, sJ + kSJvol, sJ + 2 * kSJvol, base, ax, coef);
-        } else {
-            deposit_global_slow<P, R>(A, cell, ax, coef);
+            Moved<R> mv;
+            push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+            if (!mv.ok) {
+                raise_error(A.err, ERRBIT_PARTICLE);
+                continue;
+            }
+            EsirkAxis<P, R> ax[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
+            const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+            const int bx = li + 2 + ax[0].b, by = lj + 2 + ax[1].b, bz = lk + 4 + ax[2].b;
+            PIC_CHECK_OR(bx >= 0 && bx + P + 1 < LY::JX && by >= 0 && by + P + 1 < LY::JY && bz >= 0 &&
+                             bz + P + 1 < LY::JZ,
+                         A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8), continue);
+            if constexpr (kFixed)
+                esirkepov_smem_fixed<P, LY>(sJi, bx * LY::jX + by * LY::jY + bz, ax, coef, A.vscale);
+            else
+                esirkepov_smem<P, R, LY>(sJ, sJ + LY::jVol, sJ + 2 * LY::jVol, bx * LY::jX + by * LY::jY + bz, ax,
+                                         coef);
+            store_particle<R>(A, p, cell, mv);
         }
-
-        // store the new state in place
-#pragma unroll
-        for (int a = 0; a < 3; ++a) A.pa[3 + a][p] = mv.u[a];
-        int nc[3];
-        if (sizeof(R) == 8) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const double xw = wrap_pos(mv.xg1[a], g.L[a]);
-                A.pa[a][p] = R(xw);
-                double f;
-                split_pos(xw, g.d[a], g.n[a], nc[a], f);
-            }
-        } else {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float nf;
-                renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
-                A.pa[a][p] = R(nf);
-            }
-        }
-        A.key[p] = key_of(g, nc[0], nc[1], nc[2]);
     }
     __syncthreads();
 
     // flush the tile's current into the global arrays (periodic fold)
     const int jx = g.T[0] + 5, jy = g.T[1] + 5, jz = g.T[2] + 8;
-    if (sizeof(R) == 4 && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
+    if (kFixed && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
         const int q4 = jz / 4;
         const int rows = jx * jy;
         for (int e = threadIdx.x; e < 3 * rows * q4; e += blockDim.x) {
@@ -626,9 +744,14 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
             const int q = r - row * q4;
             const int a = row / jy;
             const int b = row - a * jy;
-            const float4 v =
-                *reinterpret_cast<const float4*>(sJ + c * kSJvol + a * kSJx + b * kSJy + 4 * q);
-            if (v.x == 0.f && v.y == 0.f && v.z == 0.f && v.w == 0.f) continue;
+            const int o = 2 * c * LY::jVol + a * LY::jX + b * LY::jY + 4 * q;
+            const int4 lo = *reinterpret_cast<const int4*>(sJi + o);
+            const int4 hi = *reinterpret_cast<const int4*>(sJi + o + LY::jVol);
+            if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
+            const float4 v = make_float4(float(double((long long)hi.x * 32768 + lo.x) * A.inv_vscale),
+                                         float(double((long long)hi.y * 32768 + lo.y) * A.inv_vscale),
+                                         float(double((long long)hi.z * 32768 + lo.z) * A.inv_vscale),
+                                         float(double((long long)hi.w * 32768 + lo.w) * A.inv_vscale));
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 4 + 4 * q, g.n[2]);
@@ -645,13 +768,54 @@ __global__ void __launch_bounds__(kBlock, sizeof(R) == 4 ? 2 : 1) k_tile_step(St
             r -= a * jy * jz;
             const int b = r / jz;
             const int kk = r - b * jz;
-            const R v = sJ[c * kSJvol + a * kSJx + b * kSJy + kk];
+            const int o = a * LY::jX + b * LY::jY + kk;
+            R v;
+            if (kFixed)
+                v = R(double((long long)sJi[2 * c * LY::jVol + LY::jVol + o] * 32768 + sJi[2 * c * LY::jVol + o]) *
+                      A.inv_vscale);
+            else
+                v = sJ[c * LY::jVol + o];
             if (v == R(0)) continue;
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 4 + kk, g.n[2]);
             atomicAdd(A.J[c] + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk, v);
         }
+    }
+}
+
+// Particles the tile kernel listed as outside their tile: gather from global
+// memory, push, deposit with global atomics (the same arithmetic).
+template <int P, typename R>
+__global__ void __launch_bounds__(kBlock) k_outsiders(StepArgs<R> A) {
+    const int n = *A.outn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = A.outl[i];
+        int cell[3];
+        R f0[3], u[3], wq;
+        double xg0[3];
+        load_particle<R>(A, p, cell, f0, xg0, u, wq);
+        R EB[6];
+        {
+            GatherW<P, R> G;
+            int fn[3], fs[3];
+            gather_weights<P, R>(f0, G, fn, fs);
+            offsets_global<P, R>(G, A.g, cell, fn, fs);
+            gather6<P, R>(G, A.E, A.B, EB);
+        }
+        Moved<R> mv;
+        push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+        if (!mv.ok) {
+            raise_error(A.err, ERRBIT_PARTICLE);
+            continue;
+        }
+        EsirkAxis<P, R> ax[3];
+        for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
+        const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+        JTarget<P, R> jt;
+        jtarget_global<P, R>(jt, A.g, A.J, cell, ax);
+        esirkepov_deposit<P, R>(ax, coef, jt);
+        store_particle<R>(A, p, cell, mv);
     }
 }
 
@@ -833,7 +997,7 @@ template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const double* z, const double* ux,
-                       const double* uy, const double* uz, const double* w, int* id) {
+                       const double* uy, const double* uz, const double* w, int* id, unsigned long long* wmax) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= A.np) return;
     const Geom& g = A.g;
@@ -863,6 +1027,8 @@ __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const do
     A.pa[6][p] = R(w[p]);
     A.key[p] = key_of(g, cell[0], cell[1], cell[2]);
     id[p] = int(p);
+    // largest |w|: non-negative doubles order like their bit patterns
+    if (isfinite(w[p])) atomicMax(wmax, (unsigned long long)__double_as_longlong(fabs(double(R(w[p])))));
     if (!ok) raise_error(A.err, ERRBIT_PARTICLE);
 }
 
@@ -963,33 +1129,60 @@ __global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int n
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n) { return unsigned((n + kBlock - 1) / kBlock); }
 
-template <typename R, int P> cudaError_t tile_step_impl(pic_ctx* c) {
+template <typename R, int P, class LY> cudaError_t tile_step_impl(pic_ctx* c) {
     StepArgs<R> A = make_args<R>(c);
-    const size_t smem = tile_smem_bytes<R>();
-    static thread_local size_t configured = 0;
+    const size_t smem = LY::template smem_bytes<R>();
+    static size_t configured = 0;  // per instantiation; set outside stream capture by pic_init_grid
     if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_step<P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tile_step<P, R, LY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              int(smem));
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    k_tile_step<P, R><<<unsigned(c->g.ntiles), kBlock, smem, c->stream>>>(A);
+    k_tile_step<P, R, LY><<<unsigned(c->g.ntiles), tile_block<R>(), smem, c->stream>>>(A);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_outsiders<P, R><<<152 * 4, kBlock, 0, c->stream>>>(A);
     return cudaGetLastError();
 }
 
-template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
+template <typename R, class LY> cudaError_t tile_step_order(pic_ctx* c) {
     switch (c->order) {
-    case 1: return tile_step_impl<R, 1>(c);
-    case 2: return tile_step_impl<R, 2>(c);
-    default: return tile_step_impl<R, 3>(c);
+    case 1: return tile_step_impl<R, 1, LY>(c);
+    case 2: return tile_step_impl<R, 2, LY>(c);
+    default: return tile_step_impl<R, 3, LY>(c);
     }
 }
 
+template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
+    return c->layout == 1 ? tile_step_order<R, LayoutRow<R>>(c) : tile_step_order<R, LayoutCube>(c);
+}
+
 cudaError_t launch_tile_step(pic_ctx* c) {
+    // J is one allocation of three components (see pic_api.cu); the outsider
+    // counter sits after the four error words
     cudaError_t e = cudaMemsetAsync(c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err + 4, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
-    // J is one allocation of three components (see pic_api.cu)
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
+}
+
+// The tile kernels need more than 48 KB of dynamic shared memory: raise the
+// limit once, before any stream capture.
+cudaError_t configure_tile_kernels(pic_ctx* c) {
+    auto set = [](auto kernel, size_t bytes) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    };
+    cudaError_t e = cudaSuccess;
+#define PIC_CFG(R, P, LY)                                                              \
+    if (e == cudaSuccess) e = set(k_tile_step<P, R, LY>, LY::template smem_bytes<R>());
+    PIC_CFG(float, 1, LayoutRow<float>) PIC_CFG(float, 2, LayoutRow<float>) PIC_CFG(float, 3, LayoutRow<float>)
+    PIC_CFG(float, 1, LayoutCube) PIC_CFG(float, 2, LayoutCube) PIC_CFG(float, 3, LayoutCube)
+    PIC_CFG(double, 1, LayoutRow<double>) PIC_CFG(double, 2, LayoutRow<double>) PIC_CFG(double, 3, LayoutRow<double>)
+    PIC_CFG(double, 1, LayoutCube) PIC_CFG(double, 2, LayoutCube) PIC_CFG(double, 3, LayoutCube)
+#undef PIC_CFG
+    (void)c;
+    return e;
 }
 
 template <typename R, int P> cudaError_t gp_impl(pic_ctx* c) {
@@ -1072,11 +1265,13 @@ cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_
     if (c->prec == PIC_FP64) {
         auto A = make_args<double>(c);
         k_load<double><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                               src[6], c->P[c->cur].id);
+                                                               src[6], c->P[c->cur].id,
+                                                               reinterpret_cast<unsigned long long*>(c->err + 6));
     } else {
         auto A = make_args<float>(c);
         k_load<float><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                              src[6], c->P[c->cur].id);
+                                                              src[6], c->P[c->cur].id,
+                                                              reinterpret_cast<unsigned long long*>(c->err + 6));
     }
     return cudaGetLastError();
 }
