@@ -49,6 +49,15 @@ def _declare(lib):
         "orc_field_energy": (D, [G, P]),
         "orc_kinetic_energy": (D, [D, L, P, P, P, P]),
         "orc_wrap": (D, [D, D]),
+        "orc_dshape": (D, [I, D]),
+        "orc_gather_adj": (None, [G, I, P, P, P, P, P]),
+        "orc_boris_adj": (None, [D, D, D, P, P, P, P, P, P, P]),
+        "orc_deposit_adj": (None, [G, I, D, D, P, P, P, P, P]),
+        "orc_yee_step_adj": (None, [G, D, P, P, P]),
+        "orc_pic_adjoint": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, I, D, D, P, P, P]),
+        "orc_curlE": (None, [G, P, P]),
+        "orc_curlE_T": (None, [G, P, P]),
+        "orc_curlB_T": (None, [G, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -186,3 +195,75 @@ class Oracle:
 
     def wrap(self, x, L):
         return self.lib.orc_wrap(float(x), float(L))
+
+    # -- adjoint -----------------------------------------------------
+    def dshape(self, p, xi):
+        xi = np.atleast_1d(np.asarray(xi, dtype=np.float64))
+        f = self.lib.orc_dshape
+        return np.array([f(int(p), float(v)) for v in xi.ravel()]).reshape(xi.shape)
+
+    @staticmethod
+    def _v3(a):
+        return np.ascontiguousarray(a, dtype=np.float64)
+
+    def gather_adj(self, g, p, fields, x, lamEB):
+        """One particle: returns (lamF (6, n...), lam_x (3))."""
+        F = [self._f64(fields[c]) for c in range(6)]
+        lamF = np.zeros((6,) + tuple(g.n))
+        lx = np.zeros(3)
+        self.lib.orc_gather_adj(ct.byref(g), int(p), self._ptr_array(F), self._ptr_array([lamF[c] for c in range(6)]),
+                                self._ptr(self._v3(x)), self._ptr(self._v3(lamEB)), self._ptr(lx))
+        return lamF, lx
+
+    def boris_adj(self, q, m, dt, E, B, u_old, lam_unew):
+        """Returns (lam_uold, lam_E, lam_B)."""
+        lu, lE, lB = np.zeros(3), np.zeros(3), np.zeros(3)
+        self.lib.orc_boris_adj(float(q), float(m), float(dt), self._ptr(self._v3(E)), self._ptr(self._v3(B)),
+                               self._ptr(self._v3(u_old)), self._ptr(self._v3(lam_unew)), self._ptr(lu),
+                               self._ptr(lE), self._ptr(lB))
+        return lu, lE, lB
+
+    def deposit_adj(self, g, p, dt, qw, x0, x1, lamJ):
+        """One particle: returns (lam_x0, lam_x1)."""
+        l0, l1 = np.zeros(3), np.zeros(3)
+        LJ = [self._f64(lamJ[c]) for c in range(3)]
+        self.lib.orc_deposit_adj(ct.byref(g), int(p), float(dt), float(qw), self._ptr(self._v3(x0)),
+                                 self._ptr(self._v3(x1)), self._ptr_array(LJ), self._ptr(l0), self._ptr(l1))
+        return l0, l1
+
+    def yee_step_adj(self, g, dt, lamE, lamB):
+        """Returns (lamE^n, lamB^n, lamJ) from the adjoints after the step."""
+        lE = np.array(lamE, dtype=np.float64, copy=True)
+        lB = np.array(lamB, dtype=np.float64, copy=True)
+        lJ = np.zeros_like(lE)
+        self.lib.orc_yee_step_adj(ct.byref(g), float(dt), self._ptr_array([lE[c] for c in range(3)]),
+                                  self._ptr_array([lB[c] for c in range(3)]), self._ptr_array([lJ[c] for c in range(3)]))
+        return lE, lB, lJ
+
+    def _map3(self, fname, g, A):
+        A = [self._f64(A[c]) for c in range(3)]
+        out = np.zeros((3,) + tuple(g.n))
+        getattr(self.lib, fname)(ct.byref(g), self._ptr_array(A), self._ptr_array([out[c] for c in range(3)]))
+        return out
+
+    def curlE(self, g, E):
+        return self._map3("orc_curlE", g, E)
+
+    def curlE_T(self, g, B):
+        return self._map3("orc_curlE_T", g, B)
+
+    def curlB_T(self, g, E):
+        return self._map3("orc_curlB_T", g, E)
+
+    def pic_adjoint(self, g, p, dt, q, m, parts, fields, nsteps, A, kd):
+        """Forward nsteps then reverse; returns (loss, dL/dA, dL/du (3, np)).
+        parts and fields are left at the final forward state."""
+        keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+        np_ = parts["x"].size
+        dA = ct.c_double()
+        loss = ct.c_double()
+        du = np.zeros((3, np_))
+        self.lib.orc_pic_adjoint(ct.byref(g), int(p), float(dt), float(q), float(m), np_,
+                                 *[self._ptr(parts[k]) for k in keys], self._ptr_array([fields[c] for c in range(9)]),
+                                 int(nsteps), float(A), float(kd), ct.byref(dA), self._ptr(du), ct.byref(loss))
+        return loss.value, dA.value, du

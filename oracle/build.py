@@ -12,6 +12,7 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 BUILD_DIR = os.path.join(HERE, "_build")
 SRC = os.path.join(HERE, "pic_oracle.c")
+SRCS = [SRC, os.path.join(HERE, "pic_oracle_adj.c")]
 
 
 def lib_path(mutant: int = 0) -> str:
@@ -23,12 +24,12 @@ def build(mutant: int = 0, force: bool = False) -> str:
     out = lib_path(mutant)
     hdr = os.path.join(HERE, "pic_oracle.h")
     if (not force and os.path.exists(out)
-            and os.path.getmtime(out) >= max(os.path.getmtime(SRC), os.path.getmtime(hdr))):
+            and os.path.getmtime(out) >= max([os.path.getmtime(s) for s in SRCS] + [os.path.getmtime(hdr)])):
         return out
     os.makedirs(BUILD_DIR, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-           f"-DORC_MUTANT={int(mutant)}", SRC, "-o", tmp, "-lm"]
+           f"-DORC_MUTANT={int(mutant)}", *SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out

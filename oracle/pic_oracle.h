@@ -31,4 +31,20 @@ void orc_div_face(const orc_grid* g, const double* const F[3], double* out);
 double orc_field_energy(const orc_grid* g, const double* const F[6]);
 double orc_kinetic_energy(double m, int64_t np, const double* ux, const double* uy, const double* uz,
                           const double* w);
+/* adjoint (pic_oracle_adj.c) */
+double orc_dshape(int p, double xi);
+void orc_gather_adj(const orc_grid* g, int p, const double* const F[6], double* const lamF[6], const double x[3],
+                    const double lamEB[6], double lam_x[3]);
+void orc_boris_adj(double q, double m, double dt, const double E[3], const double B[3], const double u_old[3],
+                   const double lam_unew[3], double lam_uold[3], double lam_E[3], double lam_B[3]);
+void orc_deposit_adj(const orc_grid* g, int p, double dt, double qw, const double x0[3], const double x1[3],
+                     const double* const lamJ[3], double lam_x0[3], double lam_x1[3]);
+void orc_yee_step_adj(const orc_grid* g, double dt, double* const lamE[3], double* const lamB[3],
+                      double* const lamJ[3]);
+void orc_pic_adjoint(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                     double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                     int nsteps, double A, double kd, double* dL_dA, double* dL_du, double* loss);
+void orc_curlE(const orc_grid* g, const double* const E[3], double* const out[3]);
+void orc_curlE_T(const orc_grid* g, const double* const lamB[3], double* const out[3]);
+void orc_curlB_T(const orc_grid* g, const double* const lamE[3], double* const out[3]);
 #endif
