@@ -117,6 +117,31 @@ pic_status pic_yee_step(pic_ctx* ctx);
  * per tile), Yee update.  Checks the device error word at the end. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 
+/* Discrete adjoint of nsteps PIC steps (the paper has no adjoint; this is
+ * the reverse-mode derivative of exactly the step pic_step runs: gather,
+ * Boris push, advance, Esirkepov deposit, Yee update).
+ *
+ * Loss: L = 1/2 sum over cells (|E|^2 + |B|^2) dV after the nsteps steps.
+ * Runs the steps forward from the current state, storing the full state
+ * (particles and fields) every ckpt_every steps; then, segment by segment from
+ * the last, recomputes the segment's per-step states from its checkpoint and
+ * runs the reverse kernels: transposed Yee update, then per particle the
+ * adjoints of the deposit, advance, Boris rotation, drive and gather.  Cell
+ * indices are held fixed (floor has zero derivative).
+ *
+ * loss: host double, written (may be NULL).
+ * dL_dA: host double, written: dL/d(drive amplitude) (may be NULL).
+ * dL_du0: 3*n doubles, written (may be NULL): dL/du at the current state,
+ *   component-major (all ux, then uy, then uz), each component in particle
+ *   load order (by id).  Host memory unless on_device = 1.
+ * ckpt_every >= 1.  The call allocates its work space (about
+ *   (ceil(nsteps/ckpt_every) + ckpt_every + 1) states plus the adjoint
+ *   arrays) and frees it before returning; PIC_ERR_OOM if that fails.
+ * On return the context holds the state after the nsteps steps, as after
+ * pic_step(ctx, nsteps).  Waits.  PIC_ERR_STATE if no particles are loaded. */
+pic_status pic_step_adjoint(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss,
+                            double* dL_dA, double* dL_du0, int on_device);
+
 /* Copy one field component (PIC_EX..PIC_JZ) out as FP64 / in from FP64. */
 pic_status pic_get_field(pic_ctx* ctx, int32_t which, double* dst, int on_device);
 pic_status pic_set_field(pic_ctx* ctx, int32_t which, const double* src, int on_device);

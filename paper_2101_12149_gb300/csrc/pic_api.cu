@@ -178,6 +178,130 @@ cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
     return run_yee(c);
 }
 
+// One step of pic_step's direct path: sort at the cadence, tile kernel, Yee.
+cudaError_t run_one_step(pic_ctx* c) {
+    const bool sort_now = c->since_sort >= c->sort_every;
+    cudaError_t e = enqueue_step(c, sort_now);
+    if (e != cudaSuccess) return e;
+    if (sort_now) c->since_sort = 0;
+    c->since_sort += 1;
+    c->step += 1;
+    return cudaSuccess;
+}
+
+// ---- adjoint work space ------------------------------------------------------
+// A device allocation freed on scope exit.
+struct DeviceBlock {
+    char* p = nullptr;
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes < 256 ? 256 : bytes); }
+    ~DeviceBlock() {
+        if (p) cudaFree(p);
+    }
+};
+
+// Host-side part of a stored state.
+struct StateMeta {
+    int cur = 0, since_sort = 0;
+    bool sorted = false;
+    int64_t step = 0;
+};
+
+// Byte layout of one stored state: the current particle buffer (as laid out
+// by alloc_particles), the nine field arrays, the cell offsets of the last
+// sort and the device step counter.
+struct StateLayout {
+    size_t per, ints, part, fields, offs, total;
+    int64_t C;
+    size_t rs;
+    explicit StateLayout(const pic_ctx* c) {
+        auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+        rs = c->rsize;
+        C = c->g.C;
+        const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
+        per = align(cap * rs);
+        ints = align(cap * sizeof(int));
+        part = 7 * per + 2 * ints;
+        fields = align(9 * size_t(C) * rs);
+        offs = align((size_t(C) + 1) * sizeof(int));
+        total = part + fields + offs + 256;
+    }
+    pic::Snapshot view(char* base) const {
+        pic::Snapshot s;
+        for (int i = 0; i < 7; ++i) s.a[i] = base + i * per;
+        s.key = reinterpret_cast<int*>(base + 7 * per);
+        s.id = reinterpret_cast<int*>(base + 7 * per + ints);
+        for (int i = 0; i < 9; ++i) s.F[i] = base + part + i * size_t(C) * rs;
+        return s;
+    }
+};
+
+cudaError_t save_state(pic_ctx* c, const StateLayout& L, char* dst, StateMeta& m) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(dst, c->P[c->cur].a[0], L.part, cudaMemcpyDeviceToDevice, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(dst + L.part, c->F[0], 9 * size_t(L.C) * L.rs, cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(dst + L.part + L.fields, c->offsets, (size_t(L.C) + 1) * sizeof(int),
+                             cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(dst + L.part + L.fields + L.offs, c->d_step, sizeof(long long),
+                             cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    m.cur = c->cur;
+    m.since_sort = c->since_sort;
+    m.sorted = c->sorted;
+    m.step = c->step;
+    return cudaSuccess;
+}
+
+cudaError_t restore_state(pic_ctx* c, const StateLayout& L, const char* src, const StateMeta& m) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->P[m.cur].a[0], src, L.part, cudaMemcpyDeviceToDevice, c->stream))) return e;
+    if ((e = cudaMemcpyAsync(c->F[0], src + L.part, 9 * size_t(L.C) * L.rs, cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(c->offsets, src + L.part + L.fields, (size_t(L.C) + 1) * sizeof(int),
+                             cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    if ((e = cudaMemcpyAsync(c->d_step, src + L.part + L.fields + L.offs, sizeof(long long),
+                             cudaMemcpyDeviceToDevice, c->stream)))
+        return e;
+    c->cur = m.cur;
+    c->since_sort = m.since_sort;
+    c->sorted = m.sorted;
+    c->step = m.step;
+    return cudaSuccess;
+}
+
+// Adjoint arrays: lamx, lamu (3 x cap each), lamE, lamB, lamJ (3 x C each),
+// lamA (one double), one block.
+size_t adj_work_bytes(const pic_ctx* c) {
+    const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
+    return 6 * cap * c->rsize + 9 * size_t(c->g.C) * c->rsize + 256;
+}
+
+pic::AdjBuffers adj_buffers(const pic_ctx* c, char* base) {
+    pic::AdjBuffers b;
+    const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
+    const size_t pn = cap * c->rsize, fc = size_t(c->g.C) * c->rsize;
+    b.lamA = reinterpret_cast<double*>(base);
+    char* p = base + 256;
+    for (int a = 0; a < 3; ++a) b.lamx[a] = p + a * pn;
+    p += 3 * pn;
+    for (int a = 0; a < 3; ++a) b.lamu[a] = p + a * pn;
+    p += 3 * pn;
+    for (int a = 0; a < 3; ++a) b.lamE[a] = p + a * fc;
+    for (int a = 0; a < 3; ++a) b.lamB[a] = p + (3 + a) * fc;
+    for (int a = 0; a < 3; ++a) b.lamJ[a] = p + (6 + a) * fc;
+    return b;
+}
+
+template <typename Fn> cudaError_t adj_counted(pic_ctx* c, int kernels, Fn fn) {
+    clear_stale("adjoint kernels");
+    cudaError_t e = fn();
+    if (e == cudaSuccess && debug_sync()) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->launches += kernels;
+    return e;
+}
+
 pic_status read_error_word(pic_ctx* c) {
     unsigned hw[4] = {0, 0, 0, 0};
     PIC_CUDA(cudaMemcpyAsync(hw, c->err, sizeof(hw), cudaMemcpyDeviceToHost, c->stream));
@@ -521,14 +645,83 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
             left -= 2;
         }
     }
-    for (; left > 0; --left) {
-        const bool sort_now = c->since_sort >= c->sort_every;
-        PIC_CUDA(enqueue_step(c, sort_now));
-        if (sort_now) c->since_sort = 0;
-        c->since_sort += 1;
-        c->step += 1;
+    for (; left > 0; --left) PIC_CUDA(run_one_step(c));
+    c->have_old = false;
+    return read_error_word(c);
+}
+
+pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, double* loss, double* dL_dA,
+                            double* dL_du0, int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+    if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    if (pic_status s = read_error_word(c)) return s;
+    const int k = ckpt_every;
+    const int nseg = (nsteps + k - 1) / k;
+    const int seg_slots = nsteps > 0 ? (nsteps < k ? nsteps : k) - 1 : 0;
+    const int nstates = nseg + seg_slots + 1;  // checkpoints, segment states, final state
+    StateLayout L(c);
+    DeviceBlock states, work;
+    if (states.alloc(size_t(nstates) * L.total) != cudaSuccess || work.alloc(adj_work_bytes(c)) != cudaSuccess) {
+        clear_stale("adjoint work space");
+        return fail(PIC_ERR_OOM, "adjoint work space");
+    }
+    auto state_at = [&](int i) { return states.p + size_t(i) * L.total; };
+    std::vector<StateMeta> meta(nstates);
+    // forward sweep with checkpoints
+    for (int s = 0; s < nsteps; ++s) {
+        if (s % k == 0) PIC_CUDA(save_state(c, L, state_at(s / k), meta[s / k]));
+        PIC_CUDA(run_one_step(c));
     }
     c->have_old = false;
+    if (pic_status s = read_error_word(c)) return s;
+    const int fin = nstates - 1;
+    PIC_CUDA(save_state(c, L, state_at(fin), meta[fin]));
+    double diag[4];
+    if (pic_status s = pic_diagnostics(c, diag)) return s;
+    if (loss) *loss = diag[0];
+    // reverse sweep
+    pic::AdjBuffers b = adj_buffers(c, work.p);
+    PIC_CUDA(cudaMemsetAsync(work.p, 0, adj_work_bytes(c), c->stream));
+    PIC_CUDA(adj_counted(c, 6, [&] { return pic::launch_adj_init(c, b); }));
+    std::vector<int> view(k);
+    for (int seg = nseg - 1; seg >= 0; --seg) {
+        const int s0 = seg * k, len = (nsteps - s0 < k ? nsteps - s0 : k);
+        PIC_CUDA(restore_state(c, L, state_at(seg), meta[seg]));
+        view[0] = seg;
+        for (int j = 1; j < len; ++j) {
+            PIC_CUDA(run_one_step(c));
+            view[j] = nseg + j - 1;
+            PIC_CUDA(save_state(c, L, state_at(view[j]), meta[view[j]]));
+        }
+        for (int j = len - 1; j >= 0; --j) {
+            const pic::Snapshot snap = L.view(state_at(view[j]));
+            const double t = double(meta[view[j]].step) * c->dt;
+            PIC_CUDA(adj_counted(c, 3, [&] { return pic::launch_adj_yee(c, b); }));
+            PIC_CUDA(adj_counted(c, 1, [&] { return pic::launch_adj_particles(c, b, snap, t); }));
+        }
+    }
+    if (pic_status s = read_error_word(c)) return s;
+    if (dL_dA) PIC_CUDA(cudaMemcpyAsync(dL_dA, b.lamA, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (dL_du0) {
+        double* dst = dL_du0;
+        DeviceBlock staged;
+        if (!on_device) {
+            if (staged.alloc(3 * size_t(c->np) * sizeof(double)) != cudaSuccess) {
+                clear_stale("adjoint output");
+                return fail(PIC_ERR_OOM, "adjoint output staging");
+            }
+            dst = reinterpret_cast<double*>(staged.p);
+        }
+        PIC_CUDA(adj_counted(c, 3, [&] { return pic::launch_adj_output(c, b, dst); }));
+        if (!on_device)
+            PIC_CUDA(cudaMemcpyAsync(dL_du0, dst, 3 * size_t(c->np) * sizeof(double), cudaMemcpyDeviceToHost,
+                                     c->stream));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+    }
+    PIC_CUDA(restore_state(c, L, state_at(fin), meta[fin]));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
     return read_error_word(c);
 }
 

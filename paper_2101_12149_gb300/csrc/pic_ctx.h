@@ -118,6 +118,31 @@ cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst);
 cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src);
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
 
+// adjoint (pic_adjoint.cu)
+// Work buffers of the reverse sweep: adjoints of positions (cell units) and
+// momenta indexed by particle id, of E, B and J per cell, and of the drive
+// amplitude (FP64 accumulator).
+struct AdjBuffers {
+    void* lamx[3] = {nullptr, nullptr, nullptr};
+    void* lamu[3] = {nullptr, nullptr, nullptr};
+    void* lamE[3] = {nullptr, nullptr, nullptr};
+    void* lamB[3] = {nullptr, nullptr, nullptr};
+    void* lamJ[3] = {nullptr, nullptr, nullptr};
+    double* lamA = nullptr;
+};
+// A stored state: one particle buffer (same layout as PartBuf) and the nine
+// field arrays, as they were at the start of a step.
+struct Snapshot {
+    void* a[7] = {nullptr};
+    int* key = nullptr;
+    int* id = nullptr;
+    const void* F[9] = {nullptr};
+};
+cudaError_t launch_adj_init(pic_ctx* c, const AdjBuffers& b);
+cudaError_t launch_adj_yee(pic_ctx* c, const AdjBuffers& b);
+cudaError_t launch_adj_particles(pic_ctx* c, const AdjBuffers& b, const Snapshot& s, double t);
+cudaError_t launch_adj_output(pic_ctx* c, const AdjBuffers& b, double* d_out);
+
 // sort (pic_sort.cu)
 cudaError_t launch_hist(pic_ctx* c);
 cudaError_t launch_scan(pic_ctx* c);

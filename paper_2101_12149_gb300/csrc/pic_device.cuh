@@ -100,6 +100,42 @@ template <typename R> struct Shape<3, R> {
     }
 };
 
+// Derivatives of the weights with respect to the position (same nodes):
+// d/dx s_P(i0 + f - node), piece by piece.
+template <int P, typename R> struct ShapeD;
+
+template <typename R> struct ShapeD<1, R> {
+    __device__ __forceinline__ static void dweights(R, R d[2]) {
+        d[0] = R(-1);
+        d[1] = R(1);
+    }
+};
+
+template <typename R> struct ShapeD<2, R> {
+    __device__ __forceinline__ static void dweights(R f, R d[3]) {
+        const R g = f >= R(0.5) ? f - R(1) : f;
+        d[0] = -(R(0.5) - g);
+        d[1] = R(-2) * g;
+        d[2] = R(0.5) + g;
+    }
+};
+
+template <typename R> struct ShapeD<3, R> {
+    __device__ __forceinline__ static void dweights(R f, R d[4]) {
+        const R g = R(1) - f;
+        d[0] = R(-0.5) * g * g;
+        d[1] = (R(-2) + R(1.5) * f) * f;
+        d[2] = R(0.5) + f - R(1.5) * f * f;
+        d[3] = R(0.5) * f * f;
+    }
+};
+
+template <int P, typename R>
+__device__ __forceinline__ void staggered_dweights(R f, R d[P + 1]) {
+    const bool hi = f >= R(0.5);
+    ShapeD<P, R>::dweights(hi ? f - R(0.5) : f + R(0.5), d);
+}
+
 // Weights for a component staggered by half a cell along this axis: the
 // position relative to the staggered lattice is (i0 + f) - 1/2.
 template <int P, typename R>
@@ -165,6 +201,8 @@ __device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
 // stay in registers.  S0 / dS hold s_P at the old position and the change
 // s_P(new) - s_P(old) on the window.
 // ---------------------------------------------------------------------------
+template <int P, typename R> struct EsirkAxisD;
+
 template <int P, typename R> struct EsirkAxis {
     static constexpr int NW = P + 2;
     int b;
@@ -189,6 +227,33 @@ template <int P, typename R> struct EsirkAxis {
             const R s1 = off1 == 0 ? (a <= P ? w1[a] : R(0)) : (a >= 1 ? w1[a - 1] : R(0));
             S0[a] = s0;
             dS[a] = s1 - s0;
+        }
+    }
+};
+
+// The position derivatives of the old and new shapes on the same window
+// (D0[w] = s_P'(x0 - node_w), D1[w] = s_P'(x1 - node_w)), for the adjoint.
+template <int P, typename R> struct EsirkAxisD {
+    static constexpr int NW = P + 2;
+    R D0[NW];
+    R D1[NW];
+
+    __device__ __forceinline__ void init(R f0, R f1) {
+        int first0, first1;
+        R w0[P + 1], w1[P + 1], d0[P + 1], d1[P + 1];
+        Shape<P, R>::weights(f0, first0, w0);
+        ShapeD<P, R>::dweights(f0, d0);
+        const R fl1 = rfloor<R>(f1);
+        Shape<P, R>::weights(f1 - fl1, first1, w1);
+        ShapeD<P, R>::dweights(f1 - fl1, d1);
+        first1 += int(fl1);
+        const int b = first0 < first1 ? first0 : first1;
+        const int off0 = min(first0 - b, 1);
+        const int off1 = min(first1 - b, 1);
+#pragma unroll
+        for (int a = 0; a < NW; ++a) {
+            D0[a] = off0 == 0 ? (a <= P ? d0[a] : R(0)) : (a >= 1 ? d0[a - 1] : R(0));
+            D1[a] = off1 == 0 ? (a <= P ? d1[a] : R(0)) : (a >= 1 ? d1[a - 1] : R(0));
         }
     }
 };

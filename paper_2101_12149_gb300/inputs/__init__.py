@@ -116,6 +116,13 @@ def workload_particles(name: str, cells=None, out=None):
                           pert_amp=w["pert_amp"], pert_k=w["pert_k"], cells=cells, out=out)
 
 
+def drive_amplitude(seed: int) -> float:
+    """Amplitude of the external plane-wave drive of the differentiation
+    workload: A = 0.05 (1 + U), U uniform in [0, 1) from the seed (draw 15,
+    which the particle loader does not use)."""
+    return 0.05 * (1.0 + float(uniform(seed, 0, 1, 15)[0]))
+
+
 def random_fields(seed: int, n, scale: float = 1.0) -> np.ndarray:
     """Nine seeded uniform(-scale, scale) field arrays (Ex..Bz, Jx..Jz)."""
     C = int(n[0]) * int(n[1]) * int(n[2])

@@ -58,6 +58,7 @@ def load_library(path: str = LIB_PATH):
             "pic_deposit": [P],
             "pic_yee_step": [P],
             "pic_step": [P, I32],
+            "pic_step_adjoint": [P, I32, I32, P, P, P, ct.c_int],
             "pic_get_field": [P, I32, P, ct.c_int],
             "pic_set_field": [P, I32, P, ct.c_int],
             "pic_num_particles": [P, ct.POINTER(I64)],
@@ -191,6 +192,21 @@ class Context:
 
     def step(self, nsteps=1):
         _check(self.lib.pic_step(self.h, int(nsteps)))
+
+    def step_adjoint(self, nsteps, ckpt_every=20, du=None):
+        """Run nsteps steps and the discrete adjoint of L = 1/2 sum(|E|^2+|B|^2) dV
+        at the end.  Returns (L, dL/dA, dL/du0) with dL/du0 of shape (3, n) in
+        load order (numpy, or `du` when given: a (3, n) float64 array or CUDA
+        tensor that is written).  The context ends in the state after the
+        steps."""
+        n = self.num_particles()
+        if du is None:
+            du = np.empty((3, n))
+        p, dev = _ptr(du)
+        loss, dA = ct.c_double(), ct.c_double()
+        _check(self.lib.pic_step_adjoint(self.h, int(nsteps), int(ckpt_every), ct.byref(loss), ct.byref(dA),
+                                         ct.c_void_p(p), dev))
+        return loss.value, dA.value, du
 
     # -- fields ------------------------------------------------------
     def get_field(self, which, out=None):
