@@ -214,6 +214,89 @@ pic_status pic_launch_count(pic_ctx* ctx, int64_t* n);
 pic_status pic_sort_keys_noalloc(const int32_t* keys, int64_t n, int32_t nbins, int32_t* offsets,
                                  int32_t* perm, void* cuda_stream);
 
+/* ---- batch of independent boxes -----------------------------------------
+ *
+ * Many independent periodic plasma boxes of uneven sizes (each its own
+ * extents, cell size, shape order, particles and fields; one dt for all)
+ * stepped together: each step runs one persistent tile kernel per shape
+ * order over the (box, tile) work items of all boxes, and pic_batch_step
+ * replays its whole step loop as one CUDA graph.  Each box computes exactly
+ * what a single-box context with the same extents computes (Sec. 3.1 gather
+ * and push, Sec. 3.4.1 Esirkepov deposit, Sec. 2.4 Yee update, Sec. 3.4.2
+ * sort); the paper runs one box per GPU and has no batching. */
+typedef struct pic_batch pic_batch;
+
+/* Performance knobs (results are unchanged up to the order of floating-point
+ * additions): largest tile extent per axis (powers of two <= 8; each box
+ * uses the largest power of two not above it that divides its extent),
+ * particles per lane run in the tile kernel (0 = about one cell's worth),
+ * sort cadence in steps (>= 1; between sorts particles that left their tile
+ * take a slower global-memory path).  Default {8,8,8}, 0, 1. */
+typedef struct {
+    int32_t tile[3];
+    int32_t run;
+    int32_t sort_every;
+} pic_batch_tuning;
+
+/* nboxes boxes: n = 3*nboxes extents (each >= order + 2 and >= 3), d =
+ * 3*nboxes cell sizes or NULL for unit cells, order = nboxes shape orders
+ * (1..3).  dt > 0 is used as given (PIC_ERR_CFL if above any box's Courant
+ * limit); dt = 0 takes cfl times the smallest limit.  precision PIC_FP64 or
+ * PIC_FP32_MIXED.  Fields start at zero.  Host pointers; all are copied.
+ * cuda_stream NULL: the batch creates and owns a non-blocking stream (the
+ * legacy default stream cannot be captured into a graph); device inputs
+ * must then be complete before the call that reads them. */
+pic_status pic_batch_init(int32_t nboxes, const int32_t* n, const double* d, const int32_t* order,
+                          double dt, double cfl, int32_t precision, void* cuda_stream,
+                          pic_batch** out);
+
+/* Particles of all boxes, one species (q, m): counts[i] particles for box i,
+ * the arrays holding box 0's particles first, then box 1's, ...; positions
+ * in each box's own coordinates.  Replaces any earlier particles, resets the
+ * step count, sorts.  on_device as for pic_load_particles.  Waits. */
+pic_status pic_batch_load_particles(pic_batch* b, double q, double m, const int64_t* counts,
+                                    const double* x, const double* y, const double* z,
+                                    const double* ux, const double* uy, const double* uz,
+                                    const double* w, int on_device);
+
+/* nsteps steps of every box (captured once as a CUDA graph per step count
+ * and state, then replayed).  Waits and checks the device error word. */
+pic_status pic_batch_step(pic_batch* b, int32_t nsteps);
+
+/* Per-box access, as pic_get_field / pic_set_field / pic_get_particles /
+ * pic_diagnostics (particle ids are load indices within the box; fields may
+ * be set after pic_batch_load_particles). */
+pic_status pic_batch_get_field(pic_batch* b, int32_t box, int32_t which, double* dst, int on_device);
+pic_status pic_batch_set_field(pic_batch* b, int32_t box, int32_t which, const double* src, int on_device);
+pic_status pic_batch_get_particles(pic_batch* b, int32_t box, double* x, double* y, double* z,
+                                   double* ux, double* uy, double* uz, double* w, int32_t* id,
+                                   int on_device);
+pic_status pic_batch_diagnostics(pic_batch* b, int32_t box, double out[4]);
+
+/* Particle and cell counts of one box (box = -1: all boxes), steps taken and
+ * dt.  Any output may be NULL. */
+pic_status pic_batch_info(pic_batch* b, int32_t box, int64_t* num_particles, int64_t* num_cells,
+                          int64_t* steps, double* dt);
+
+/* Switch the knobs (re-keys and re-sorts the particles).  Waits. */
+pic_status pic_batch_set_tuning(pic_batch* b, const pic_batch_tuning* t);
+pic_status pic_batch_get_tuning(pic_batch* b, pic_batch_tuning* t);
+
+/* Autotuner: from the current state, times trial_steps steps (after one
+ * untimed step) of every candidate (tile extents {8,8,8}, {4,8,8}, {4,4,8},
+ * {4,4,4} x run {0,1,4} x sort cadence {1,2,4}), restores the state after
+ * each, and keeps the fastest; returns it and its milliseconds per step.
+ * The simulation state afterwards is the state before the call (re-sorted).
+ * Allocates one stored state for the duration of the call.  Waits. */
+pic_status pic_batch_autotune(pic_batch* b, int32_t trial_steps, pic_batch_tuning* best,
+                              double* best_ms);
+
+/* Number of kernels the batch has launched (graph replays counted per node). */
+pic_status pic_batch_launch_count(pic_batch* b, int64_t* n);
+
+/* Release the batch (NULL is allowed). */
+pic_status pic_batch_destroy(pic_batch* b);
+
 /* Release every buffer of the context (NULL is allowed). */
 pic_status pic_destroy(pic_ctx* ctx);
 

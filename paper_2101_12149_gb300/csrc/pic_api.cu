@@ -38,6 +38,10 @@ int ilog2(int v) {
     return l;
 }
 
+}  // namespace
+
+namespace pic {
+
 void free_particles(pic_ctx* c) {
     for (int b = 0; b < 2; ++b) {
         cudaFree(c->P[b].a[0]);
@@ -75,6 +79,13 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
     c->cap = int64_t(cap);
     return cudaSuccess;
 }
+
+}  // namespace pic
+
+namespace {
+
+using pic::alloc_particles;
+using pic::free_particles;
 
 // ---- kernel launch bookkeeping (counts, optional timing) -------------------
 // In timing mode every launch is bracketed by a pair of events from a pool on
@@ -189,51 +200,9 @@ cudaError_t run_one_step(pic_ctx* c) {
     return cudaSuccess;
 }
 
-// ---- adjoint work space ------------------------------------------------------
-// A device allocation freed on scope exit.
-struct DeviceBlock {
-    char* p = nullptr;
-    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes < 256 ? 256 : bytes); }
-    ~DeviceBlock() {
-        if (p) cudaFree(p);
-    }
-};
+}  // namespace
 
-// Host-side part of a stored state.
-struct StateMeta {
-    int cur = 0, since_sort = 0;
-    bool sorted = false;
-    int64_t step = 0;
-};
-
-// Byte layout of one stored state: the current particle buffer (as laid out
-// by alloc_particles), the nine field arrays, the cell offsets of the last
-// sort and the device step counter.
-struct StateLayout {
-    size_t per, ints, part, fields, offs, total;
-    int64_t C;
-    size_t rs;
-    explicit StateLayout(const pic_ctx* c) {
-        auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
-        rs = c->rsize;
-        C = c->g.C;
-        const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
-        per = align(cap * rs);
-        ints = align(cap * sizeof(int));
-        part = 7 * per + 2 * ints;
-        fields = align(9 * size_t(C) * rs);
-        offs = align((size_t(C) + 1) * sizeof(int));
-        total = part + fields + offs + 256;
-    }
-    pic::Snapshot view(char* base) const {
-        pic::Snapshot s;
-        for (int i = 0; i < 7; ++i) s.a[i] = base + i * per;
-        s.key = reinterpret_cast<int*>(base + 7 * per);
-        s.id = reinterpret_cast<int*>(base + 7 * per + ints);
-        for (int i = 0; i < 9; ++i) s.F[i] = base + part + i * size_t(C) * rs;
-        return s;
-    }
-};
+namespace pic {
 
 cudaError_t save_state(pic_ctx* c, const StateLayout& L, char* dst, StateMeta& m) {
     cudaError_t e;
@@ -270,6 +239,16 @@ cudaError_t restore_state(pic_ctx* c, const StateLayout& L, const char* src, con
     c->step = m.step;
     return cudaSuccess;
 }
+
+}  // namespace pic
+
+namespace {
+
+using pic::DeviceBlock;
+using pic::StateLayout;
+using pic::StateMeta;
+using pic::restore_state;
+using pic::save_state;
 
 // Adjoint arrays: lamx, lamu (3 x cap each), lamE, lamB, lamJ (3 x C each),
 // lamA (one double), one block.
@@ -458,6 +437,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     g.cpt = g.T[0] * g.T[1] * g.T[2];
     g.C = C;
     g.ntiles = int64_t(g.nt[0]) * g.nt[1] * g.nt[2];
+    g.kbase = 0;
 
     auto bail = [&](cudaError_t e, const char* what) {
         pic_destroy(c);

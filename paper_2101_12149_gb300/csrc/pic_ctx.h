@@ -43,6 +43,7 @@ struct Geom {
     int64_t ntiles;
     double d[3];
     double L[3];
+    int kbase;     // added to every cell key (a box's first key in a batch of boxes; 0 otherwise)
 };
 
 struct Timer {
@@ -138,10 +139,87 @@ struct Snapshot {
     int* id = nullptr;
     const void* F[9] = {nullptr};
 };
+// ---- stored states (adjoint checkpoints, autotuner trials) -------------------
+// A device allocation freed on scope exit.
+struct DeviceBlock {
+    char* p = nullptr;
+    cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes < 256 ? 256 : bytes); }
+    ~DeviceBlock() {
+        if (p) cudaFree(p);
+    }
+};
+
+// Host-side part of a stored state.
+struct StateMeta {
+    int cur = 0, since_sort = 0;
+    bool sorted = false;
+    int64_t step = 0;
+};
+
+// Byte layout of one stored state: the current particle buffer (as laid out
+// by alloc_particles), the nine field arrays, the cell offsets of the last
+// sort and the device step counter.
+struct StateLayout {
+    size_t per, ints, part, fields, offs, total;
+    int64_t C;
+    size_t rs;
+    explicit StateLayout(const pic_ctx* c) {
+        auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+        rs = c->rsize;
+        C = c->g.C;
+        const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
+        per = align(cap * rs);
+        ints = align(cap * sizeof(int));
+        part = 7 * per + 2 * ints;
+        fields = align(9 * size_t(C) * rs);
+        offs = align((size_t(C) + 1) * sizeof(int));
+        total = part + fields + offs + 256;
+    }
+    pic::Snapshot view(char* base) const {
+        pic::Snapshot s;
+        for (int i = 0; i < 7; ++i) s.a[i] = base + i * per;
+        s.key = reinterpret_cast<int*>(base + 7 * per);
+        s.id = reinterpret_cast<int*>(base + 7 * per + ints);
+        for (int i = 0; i < 9; ++i) s.F[i] = base + part + i * size_t(C) * rs;
+        return s;
+    }
+};
+
+cudaError_t save_state(pic_ctx* c, const StateLayout& L, char* dst, StateMeta& m);
+cudaError_t restore_state(pic_ctx* c, const StateLayout& L, const char* src, const StateMeta& m);
+
+// particle buffers (pic_api.cu): one allocation per buffer, 7 real arrays, key, id
+cudaError_t alloc_particles(pic_ctx* c, int64_t n);
+void free_particles(pic_ctx* c);
+
 cudaError_t launch_adj_init(pic_ctx* c, const AdjBuffers& b);
 cudaError_t launch_adj_yee(pic_ctx* c, const AdjBuffers& b);
 cudaError_t launch_adj_particles(pic_ctx* c, const AdjBuffers& b, const Snapshot& s, double t);
 cudaError_t launch_adj_output(pic_ctx* c, const AdjBuffers& b, double* d_out);
+
+// batch of boxes (pic_batch.cu host side, kernels in pic_kernels.cu)
+// One launch of the persistent batch tile kernel over the boxes of one shape
+// order, followed by its outsider kernel.
+struct BatchTileLaunch {
+    int order = 1;
+    const void* boxes = nullptr;     // StepArgs<R>[nboxes] (R = double for FP64, float for FP32-mixed)
+    const int2* items = nullptr;     // (box, tile) work items, heaviest first
+    int nitems = 0;
+    int* queue = nullptr;            // work counter, zeroed before the launch
+    const int64_t* pbase = nullptr;  // first particle of each box, nboxes + 1 entries
+    int nboxes = 0;
+    const int* outn = nullptr;       // outsider count and list of this order's boxes
+    const int* outl = nullptr;
+    int grid = 0;                    // persistent CTAs
+};
+cudaError_t launch_tile_step_batch(int prec, const BatchTileLaunch& L, cudaStream_t s);
+// Yee update of all boxes: yb / ye are YeeArgs<R>[nboxes] with h = dt/2 and
+// h = dt; blocks maps each 256-thread block to (box, first cell, cells).
+cudaError_t launch_yee_batch(int prec, const void* yb, const void* ye, const int4* blocks, int nblocks,
+                             long long* step, cudaStream_t s);
+// New cell keys of n particles after a change of tile shape (from -> to).
+cudaError_t launch_rekey(int* key, int64_t n, const Geom& from, const Geom& to, cudaStream_t s);
+cudaError_t configure_batch_kernels();
 
 // sort (pic_sort.cu)
 cudaError_t launch_hist(pic_ctx* c);

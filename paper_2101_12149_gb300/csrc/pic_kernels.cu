@@ -224,9 +224,10 @@ __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int b
 // shared memory holding the fixed-point J box), FP64 256.
 template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
 
+// One tile t of the box described by A, by the whole CTA; `smem_raw` is the
+// CTA's dynamic shared memory.  Returns with the block converged.
 template <int P, typename R, class LY>
-__global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw) {
     R* sm = reinterpret_cast<R*>(smem_raw);
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
@@ -234,8 +235,6 @@ __global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A)
     R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
     int* sJi = reinterpret_cast<int*>(sJ);
 
-    const int t = blockIdx.x;
-    const int lcpt = g.lT[0] + g.lT[1] + g.lT[2];
     const int beg = A.offsets[(int64_t)t * g.cpt];
     const int end = A.offsets[(int64_t)(t + 1) * g.cpt];
     if (end <= beg) return;
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A)
     // runs of about one cell's worth of particles, so the lanes of a warp work
     // in neighbouring cells (distinct shared-memory banks).
     const int cnt = end - beg;
-    const int run = max(1, (cnt + (g.cpt >> 1)) / g.cpt);
+    const int run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
     const int nrun = (cnt + run - 1) / run;
     for (int rr = threadIdx.x; rr < nrun; rr += blockDim.x) {
         const int p0 = beg + rr * run;
@@ -382,38 +381,92 @@ __global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A)
     }
 }
 
-// Particles the tile kernel listed as outside their tile: gather from global
+template <int P, typename R, class LY>
+__global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    tile_body<P, R, LY>(A, int(blockIdx.x), smem_raw);
+}
+
+// Batch of boxes: a persistent grid pulls (box, tile) items from a queue
+// counter (zeroed before the launch); each item's box arguments are copied
+// into shared memory first.  Items are ordered heaviest first.
+template <int P, typename R, class LY>
+__global__ void __launch_bounds__(tile_block<R>(), 1)
+    k_tile_step_batch(const StepArgs<R>* __restrict__ boxes, const int2* __restrict__ items, int nitems, int* queue) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) StepArgs<R> sA;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 bt = items[it];
+        {
+            const int* src = reinterpret_cast<const int*>(boxes + bt.x);
+            int* dst = reinterpret_cast<int*>(&sA);
+            for (int w = threadIdx.x; w < int(sizeof(StepArgs<R>) / 4); w += blockDim.x) dst[w] = src[w];
+        }
+        __syncthreads();
+        tile_body<P, R, LY>(sA, bt.y, smem_raw);
+        __syncthreads();
+    }
+}
+
+// One particle the tile kernel listed as outside its tile: gather from global
 // memory, push, deposit with global atomics (the same arithmetic).
+template <int P, typename R>
+__device__ __forceinline__ void outsider_body(const StepArgs<R>& A, const int p) {
+    int cell[3];
+    R f0[3], u[3], wq;
+    double xg0[3];
+    load_particle<R>(A, p, cell, f0, xg0, u, wq);
+    R EB[6];
+    {
+        GatherW<P, R> G;
+        int fn[3], fs[3];
+        gather_weights<P, R>(f0, G, fn, fs);
+        offsets_global<P, R>(G, A.g, cell, fn, fs);
+        gather6<P, R>(G, A.E, A.B, EB);
+    }
+    Moved<R> mv;
+    push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+    if (!mv.ok) {
+        raise_error(A.err, ERRBIT_PARTICLE);
+        return;
+    }
+    EsirkAxis<P, R> ax[3];
+    for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
+    const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+    JTarget<P, R> jt;
+    jtarget_global<P, R>(jt, A.g, A.J, cell, ax);
+    esirkepov_deposit<P, R>(ax, coef, jt);
+    store_particle<R>(A, p, cell, mv);
+}
+
 template <int P, typename R>
 __global__ void __launch_bounds__(kBlock) k_outsiders(StepArgs<R> A) {
     const int n = *A.outn;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        outsider_body<P, R>(A, A.outl[i]);
+}
+
+// Batch: the box of an outsider is found from the boxes' first particle
+// indices (pbase, nboxes + 1 entries, ascending).
+template <int P, typename R>
+__global__ void __launch_bounds__(kBlock)
+    k_outsiders_batch(const StepArgs<R>* __restrict__ boxes, const int64_t* __restrict__ pbase, int nboxes,
+                      const int* outn, const int* outl) {
+    const int n = *outn;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const int p = A.outl[i];
-        int cell[3];
-        R f0[3], u[3], wq;
-        double xg0[3];
-        load_particle<R>(A, p, cell, f0, xg0, u, wq);
-        R EB[6];
-        {
-            GatherW<P, R> G;
-            int fn[3], fs[3];
-            gather_weights<P, R>(f0, G, fn, fs);
-            offsets_global<P, R>(G, A.g, cell, fn, fs);
-            gather6<P, R>(G, A.E, A.B, EB);
+        const int p = outl[i];
+        int lo = 0, hi = nboxes - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pbase[mid] <= p) lo = mid;
+            else hi = mid - 1;
         }
-        Moved<R> mv;
-        push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
-        if (!mv.ok) {
-            raise_error(A.err, ERRBIT_PARTICLE);
-            continue;
-        }
-        EsirkAxis<P, R> ax[3];
-        for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
-        const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
-        JTarget<P, R> jt;
-        jtarget_global<P, R>(jt, A.g, A.J, cell, ax);
-        esirkepov_deposit<P, R>(ax, coef, jt);
-        store_particle<R>(A, p, cell, mv);
+        outsider_body<P, R>(boxes[lo], p);
     }
 }
 
@@ -517,22 +570,9 @@ __global__ void __launch_bounds__(kBlock) k_deposit(StepArgs<R> A) {
 // ---------------------------------------------------------------------------
 // Yee FDTD
 // ---------------------------------------------------------------------------
-template <typename R> struct YeeArgs {
-    R* E[3];
-    R* B[3];
-    const R* J[3];
-    int n[3];
-    R inv[3];
-    R h;
-    long long* step;  // advanced by one thread when non-null
-};
 
-// B <- B - h curl E (forward differences: B sits half a cell above E).
-template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (Y.step && c == 0) *Y.step += 1;
-    if (c >= C) return;
+// B <- B - h curl E (forward differences: B sits half a cell above E), at cell c.
+template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>& Y, const int64_t c) {
     const int k = int(c % Y.n[2]);
     const int j = int((c / Y.n[2]) % Y.n[1]);
     const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
@@ -552,11 +592,8 @@ template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<
     Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
 }
 
-// E <- E + dt (curl B - J) (backward differences).
-template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+// E <- E + dt (curl B - J) (backward differences), at cell c.
+template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>& Y, const int64_t c) {
     const int k = int(c % Y.n[2]);
     const int j = int((c / Y.n[2]) % Y.n[1]);
     const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
@@ -574,6 +611,36 @@ template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<
     Y.E[0][c] += Y.h * ((dBz_dy - dBy_dz) - Y.J[0][c]);
     Y.E[1][c] += Y.h * ((dBx_dz - dBz_dx) - Y.J[1][c]);
     Y.E[2][c] += Y.h * ((dBy_dx - dBx_dy) - Y.J[2][c]);
+}
+
+template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<R> Y) {
+    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (Y.step && c == 0) *Y.step += 1;
+    if (c < C) yee_b_at(Y, c);
+}
+
+template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
+    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c < C) yee_e_at(Y, c);
+}
+
+// Batch of boxes: block b updates cells [blocks[b].y, blocks[b].y + blocks[b].z)
+// of box blocks[b].x (a block never spans two boxes).  `step`, when non-null,
+// is advanced once.
+template <typename R>
+__global__ void __launch_bounds__(kBlock)
+    k_yee_b_batch(const YeeArgs<R>* __restrict__ boxes, const int4* __restrict__ blocks, long long* step) {
+    const int4 bk = blocks[blockIdx.x];
+    if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
+    if (int(threadIdx.x) < bk.z) yee_b_at(boxes[bk.x], int64_t(bk.y) + threadIdx.x);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_yee_e_batch(const YeeArgs<R>* __restrict__ boxes, const int4* __restrict__ blocks) {
+    const int4 bk = blocks[blockIdx.x];
+    if (int(threadIdx.x) < bk.z) yee_e_at(boxes[bk.x], int64_t(bk.y) + threadIdx.x);
 }
 
 template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
@@ -780,6 +847,81 @@ cudaError_t configure_tile_kernels(pic_ctx* c) {
     PIC_CFG(double, 1, LayoutCube) PIC_CFG(double, 2, LayoutCube) PIC_CFG(double, 3, LayoutCube)
 #undef PIC_CFG
     (void)c;
+    return e;
+}
+
+// ---- batch of boxes ----------------------------------------------------------
+template <typename R, int P> cudaError_t tile_batch_impl(const BatchTileLaunch& L, cudaStream_t s) {
+    using LY = LayoutCube;
+    if (L.nitems <= 0) return cudaSuccess;
+    const size_t smem = LY::template smem_bytes<R>();
+    const int grid = L.grid < L.nitems ? L.grid : L.nitems;
+    k_tile_step_batch<P, R, LY><<<unsigned(grid), tile_block<R>(), smem, s>>>(
+        static_cast<const StepArgs<R>*>(L.boxes), L.items, L.nitems, L.queue);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_outsiders_batch<P, R><<<152 * 2, kBlock, 0, s>>>(static_cast<const StepArgs<R>*>(L.boxes), L.pbase, L.nboxes,
+                                                        L.outn, L.outl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_step_batch(int prec, const BatchTileLaunch& L, cudaStream_t s) {
+    if (prec == PIC_FP64) {
+        switch (L.order) {
+        case 1: return tile_batch_impl<double, 1>(L, s);
+        case 2: return tile_batch_impl<double, 2>(L, s);
+        default: return tile_batch_impl<double, 3>(L, s);
+        }
+    }
+    switch (L.order) {
+    case 1: return tile_batch_impl<float, 1>(L, s);
+    case 2: return tile_batch_impl<float, 2>(L, s);
+    default: return tile_batch_impl<float, 3>(L, s);
+    }
+}
+
+template <typename R>
+cudaError_t yee_batch_impl(const void* yb, const void* ye, const int4* blocks, int nblocks, long long* step,
+                           cudaStream_t s) {
+    if (nblocks <= 0) return cudaSuccess;
+    const auto* B = static_cast<const YeeArgs<R>*>(yb);
+    const auto* E = static_cast<const YeeArgs<R>*>(ye);
+    k_yee_b_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(B, blocks, nullptr);
+    k_yee_e_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(E, blocks);
+    k_yee_b_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(B, blocks, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_batch(int prec, const void* yb, const void* ye, const int4* blocks, int nblocks,
+                             long long* step, cudaStream_t s) {
+    return prec == PIC_FP64 ? yee_batch_impl<double>(yb, ye, blocks, nblocks, step, s)
+                            : yee_batch_impl<float>(yb, ye, blocks, nblocks, step, s);
+}
+
+__global__ void k_rekey(int* key, int64_t n, Geom from, Geom to) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int i, j, k;
+    cell_of(from, key[p], i, j, k);
+    key[p] = key_of(to, i, j, k);
+}
+
+cudaError_t launch_rekey(int* key, int64_t n, const Geom& from, const Geom& to, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_rekey<<<blocks_for(n), kBlock, 0, s>>>(key, n, from, to);
+    return cudaGetLastError();
+}
+
+cudaError_t configure_batch_kernels() {
+    auto set = [](auto kernel, size_t bytes) {
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    };
+    using LY = LayoutCube;
+    cudaError_t e = cudaSuccess;
+#define PIC_CFG(R, P) \
+    if (e == cudaSuccess) e = set(k_tile_step_batch<P, R, LY>, LY::template smem_bytes<R>());
+    PIC_CFG(float, 1) PIC_CFG(float, 2) PIC_CFG(float, 3) PIC_CFG(double, 1) PIC_CFG(double, 2) PIC_CFG(double, 3)
+#undef PIC_CFG
     return e;
 }
 

@@ -24,7 +24,7 @@ __device__ __forceinline__ int key_of(const Geom& g, int i, int j, int k) {
     const int li = i & (g.T[0] - 1), lj = j & (g.T[1] - 1), lk = k & (g.T[2] - 1);
     const int t = (ti * g.nt[1] + tj) * g.nt[2] + tk;
     const int l = (li << (g.lT[1] + g.lT[2])) | (lj << g.lT[2]) | lk;
-    return t * g.cpt + l;
+    return g.kbase + t * g.cpt + l;
 }
 
 __device__ __forceinline__ void tile_origin(const Geom& g, int t, int& oi, int& oj, int& ok) {
@@ -38,6 +38,7 @@ __device__ __forceinline__ void tile_origin(const Geom& g, int t, int& oi, int& 
 }
 
 __device__ __forceinline__ void cell_of(const Geom& g, int key, int& i, int& j, int& k) {
+    key -= g.kbase;
     const int lcpt = g.lT[0] + g.lT[1] + g.lT[2];
     const int t = key >> lcpt, l = key & (g.cpt - 1);
     int oi, oj, ok;
@@ -78,6 +79,7 @@ template <typename R> struct StepArgs {
     int* outl;   // outsider particle indices
     const long long* step;
     double drive_amp, drive_k;
+    int run;            // tile kernel: particles per lane run (0 = about one cell's worth)
     float vscale;       // FP32-mixed fixed-point scale of the deposit (2^30 / max|coef|)
     double inv_vscale;
     int64_t np;
@@ -108,6 +110,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.step = c->d_step;
     a.drive_amp = c->drive_amp;
     a.drive_k = c->drive_k;
+    a.run = 0;
     {
         double cmax = 0.0;
         for (int d = 0; d < 3; ++d) {
@@ -121,6 +124,18 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.np = c->np;
     return a;
 }
+
+// Arguments of the Yee kernels: E, B, J of one box, its extents, inverse
+// cell sizes and the time step h of the update (dt/2 for a B half step).
+template <typename R> struct YeeArgs {
+    R* E[3];
+    R* B[3];
+    const R* J[3];
+    int n[3];
+    R inv[3];
+    R h;
+    long long* step;  // advanced by one thread when non-null
+};
 
 // ---------------------------------------------------------------------------
 // field sources / current targets: offset tables per axis, plain or wrapped

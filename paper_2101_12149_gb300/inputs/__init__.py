@@ -116,6 +116,38 @@ def workload_particles(name: str, cells=None, out=None):
                           pert_amp=w["pert_amp"], pert_k=w["pert_k"], cells=cells, out=out)
 
 
+ENSEMBLE = dict(nboxes=96, edges=(16, 24, 32, 48, 64), ppc=(1, 8), density=(0.1, 10.0), orders=(1, 3),
+                sigma_u=0.05, cfl=0.99, steps=200, seed=3)
+
+
+def ensemble_boxes(seed: int = ENSEMBLE["seed"], nboxes: int = ENSEMBLE["nboxes"], edges=ENSEMBLE["edges"],
+                   ppc=ENSEMBLE["ppc"], density=ENSEMBLE["density"], orders=ENSEMBLE["orders"]):
+    """Boxes of the batched ensemble: per box b (the counter of each draw)
+    each axis extent drawn uniformly from `edges` (draws 0, 1, 2), particles
+    per cell uniform in {ppc[0] .. ppc[1]} (draw 3), density log-uniform in
+    [density[0], density[1]] (draw 4), shape order orders[0] or orders[1]
+    with probability 1/2 (draw 5), and the box's own loader seed."""
+    u = [uniform(seed, 0, nboxes, k) for k in range(6)]
+    out = []
+    for b in range(nboxes):
+        n = tuple(int(edges[min(int(u[a][b] * len(edges)), len(edges) - 1)]) for a in range(3))
+        p = int(ppc[0] + min(int(u[3][b] * (ppc[1] - ppc[0] + 1)), ppc[1] - ppc[0]))
+        dens = float(np.exp(np.log(density[0]) + u[4][b] * (np.log(density[1]) - np.log(density[0]))))
+        order = int(orders[0] if u[5][b] < 0.5 else orders[1])
+        out.append(dict(n=n, ppc=p, density=dens, order=order, seed=1000 * int(seed) + b + 1))
+    return out
+
+
+def ensemble_particles(boxes, sigma_u: float = ENSEMBLE["sigma_u"]):
+    """Particles of all boxes concatenated in box order (box-local
+    coordinates, unit cells) and the per-box counts."""
+    parts = [uniform_plasma(b["seed"], b["n"], b["ppc"], sigma_u=sigma_u, density=b["density"]) for b in boxes]
+    keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+    counts = np.array([p["x"].size for p in parts], dtype=np.int64)
+    cat = {k: np.concatenate([p[k] for p in parts]) if parts else np.empty(0) for k in keys}
+    return cat, counts, parts
+
+
 def drive_amplitude(seed: int) -> float:
     """Amplitude of the external plane-wave drive of the differentiation
     workload: A = 0.05 (1 + U), U uniform in [0, 1) from the seed (draw 15,

@@ -41,6 +41,10 @@ class GridDesc(ct.Structure):
                 ("tile", ct.c_int32 * 3)]
 
 
+class BatchTuning(ct.Structure):
+    _fields_ = [("tile", ct.c_int32 * 3), ("run", ct.c_int32), ("sort_every", ct.c_int32)]
+
+
 def load_library(path: str = LIB_PATH):
     """Load libpic; raises if it is missing (build it with build.build())."""
     global _lib
@@ -72,6 +76,19 @@ def load_library(path: str = LIB_PATH):
             "pic_launch_count": [P, ct.POINTER(I64)],
             "pic_destroy": [P],
             "pic_sort_keys_noalloc": [P, I64, I32, P, P, P],
+            "pic_batch_init": [I32, P, P, P, D, D, I32, P, ct.POINTER(P)],
+            "pic_batch_load_particles": [P, D, D, P, P, P, P, P, P, P, P, ct.c_int],
+            "pic_batch_step": [P, I32],
+            "pic_batch_get_field": [P, I32, I32, P, ct.c_int],
+            "pic_batch_set_field": [P, I32, I32, P, ct.c_int],
+            "pic_batch_get_particles": [P, I32, P, P, P, P, P, P, P, P, ct.c_int],
+            "pic_batch_diagnostics": [P, I32, P],
+            "pic_batch_info": [P, I32, ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(I64), ct.POINTER(D)],
+            "pic_batch_set_tuning": [P, ct.POINTER(BatchTuning)],
+            "pic_batch_get_tuning": [P, ct.POINTER(BatchTuning)],
+            "pic_batch_autotune": [P, I32, ct.POINTER(BatchTuning), ct.POINTER(D)],
+            "pic_batch_launch_count": [P, ct.POINTER(I64)],
+            "pic_batch_destroy": [P],
         }
         for name, args in sigs.items():
             f = getattr(lib, name)
@@ -263,6 +280,118 @@ class Context:
     def launch_count(self):
         v = ct.c_int64()
         _check(self.lib.pic_launch_count(self.h, ct.byref(v)))
+        return v.value
+
+
+class Batch:
+    """Many independent periodic boxes stepped together (pic_batch_*): per box
+    extents, shape order and cell size; one dt."""
+
+    def __init__(self, ns, orders, d=None, dt=0.0, cfl=0.99, precision=FP32_MIXED, stream=None):
+        self.lib = load_library()
+        self.nboxes = len(ns)
+        n_arr = np.ascontiguousarray(np.asarray(ns, dtype=np.int32).reshape(self.nboxes, 3))
+        o_arr = np.ascontiguousarray(np.asarray(orders, dtype=np.int32).reshape(self.nboxes))
+        d_arr = None if d is None else np.ascontiguousarray(np.asarray(d, dtype=np.float64).reshape(self.nboxes, 3))
+        self.ns = [tuple(int(v) for v in r) for r in n_arr]
+        s = None
+        if stream is not None:
+            s = ct.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        h = ct.c_void_p()
+        self.h = None
+        _check(self.lib.pic_batch_init(self.nboxes, n_arr.ctypes.data, None if d_arr is None else d_arr.ctypes.data,
+                                       o_arr.ctypes.data, float(dt), float(cfl), int(precision), s, ct.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h is not None:
+            self.lib.pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load_particles(self, q, m, parts, counts):
+        """parts: dict of concatenated arrays (box order), counts: per-box sizes."""
+        counts = np.ascontiguousarray(np.asarray(counts, dtype=np.int64))
+        assert counts.size == self.nboxes
+        ptrs = [_ptr(parts[k]) for k in PARTICLE_KEYS]
+        on_dev = {p[1] for p in ptrs}
+        assert len(on_dev) == 1, "all particle arrays must be on the same side"
+        _check(self.lib.pic_batch_load_particles(self.h, float(q), float(m), counts.ctypes.data,
+                                                 *[p[0] for p in ptrs], on_dev.pop()))
+
+    def step(self, nsteps=1):
+        _check(self.lib.pic_batch_step(self.h, int(nsteps)))
+
+    def info(self, box=-1):
+        n, c, st, dt = ct.c_int64(), ct.c_int64(), ct.c_int64(), ct.c_double()
+        _check(self.lib.pic_batch_info(self.h, int(box), ct.byref(n), ct.byref(c), ct.byref(st), ct.byref(dt)))
+        return {"particles": n.value, "cells": c.value, "steps": st.value, "dt": dt.value}
+
+    def get_field(self, box, which, out=None):
+        w = FIELDS.index(which) if isinstance(which, str) else int(which)
+        if out is None:
+            out = np.empty(self.ns[box])
+        p, dev = _ptr(out)
+        _check(self.lib.pic_batch_get_field(self.h, int(box), w, ct.c_void_p(p), dev))
+        return out
+
+    def get_fields(self, box):
+        return np.stack([self.get_field(box, i) for i in range(9)])
+
+    def set_field(self, box, which, arr):
+        w = FIELDS.index(which) if isinstance(which, str) else int(which)
+        a = np.ascontiguousarray(arr, dtype=np.float64) if isinstance(arr, np.ndarray) else arr
+        p, dev = _ptr(a)
+        _check(self.lib.pic_batch_set_field(self.h, int(box), w, ct.c_void_p(p), dev))
+
+    def set_fields(self, box, F):
+        for i in range(F.shape[0]):
+            self.set_field(box, i, F[i])
+
+    def get_particles(self, box):
+        n = self.info(box)["particles"]
+        out = {k: np.empty(n) for k in PARTICLE_KEYS}
+        out["id"] = np.empty(n, dtype=np.int32)
+        ptrs = [out[k].ctypes.data for k in PARTICLE_KEYS + ("id",)]
+        _check(self.lib.pic_batch_get_particles(self.h, int(box), *ptrs, 0))
+        return out
+
+    def diagnostics(self, box):
+        out = (ct.c_double * 4)()
+        _check(self.lib.pic_batch_diagnostics(self.h, int(box), out))
+        return {"field_energy": out[0], "kinetic_energy": out[1], "charge": out[2], "max_div_b": out[3]}
+
+    def set_tuning(self, tile=(8, 8, 8), run=0, sort_every=1):
+        t = BatchTuning()
+        for a in range(3):
+            t.tile[a] = int(tile[a])
+        t.run, t.sort_every = int(run), int(sort_every)
+        _check(self.lib.pic_batch_set_tuning(self.h, ct.byref(t)))
+
+    def get_tuning(self):
+        t = BatchTuning()
+        _check(self.lib.pic_batch_get_tuning(self.h, ct.byref(t)))
+        return {"tile": tuple(t.tile), "run": t.run, "sort_every": t.sort_every}
+
+    def autotune(self, trial_steps=3):
+        t, ms = BatchTuning(), ct.c_double()
+        _check(self.lib.pic_batch_autotune(self.h, int(trial_steps), ct.byref(t), ct.byref(ms)))
+        return {"tile": tuple(t.tile), "run": t.run, "sort_every": t.sort_every}, ms.value
+
+    def launch_count(self):
+        v = ct.c_int64()
+        _check(self.lib.pic_batch_launch_count(self.h, ct.byref(v)))
         return v.value
 
 

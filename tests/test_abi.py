@@ -87,3 +87,35 @@ def test_null_arguments(lib):
     assert lib.pic_step(None, 1) == pic.PIC_ERR_ARG
     assert lib.pic_sync(None) == pic.PIC_ERR_ARG
     assert lib.pic_destroy(None) == pic.PIC_OK
+
+
+def test_batch_tuning_layout_matches_binding(tmp_path):
+    src = tmp_path / "tlayout.c"
+    src.write_text(
+        '#include <stddef.h>\n#include <stdio.h>\n#include "pic.h"\n'
+        "int main(void){printf(\"%zu %zu %zu\\n\", sizeof(pic_batch_tuning),"
+        " offsetof(pic_batch_tuning, run), offsetof(pic_batch_tuning, sort_every));return 0;}\n")
+    exe = tmp_path / "tlayout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    T = pic.BatchTuning
+    assert vals == [ct.sizeof(T), T.run.offset, T.sort_every.offset]
+
+
+@pytest.mark.parametrize("ns,orders,dt,cfl,status", [
+    ([], [], 0.0, 0.99, pic.PIC_ERR_ARG),                                  # no boxes
+    ([(8, 8, 8), (16, 8, 8)], [1, 4], 0.0, 0.99, pic.PIC_ERR_ARG),         # order 4
+    ([(8, 8, 8), (4, 8, 8)], [1, 3], 0.0, 0.99, pic.PIC_ERR_ARG),          # n < order + 2
+    ([(8, 8, 8)], [1], 0.6, 0.99, pic.PIC_ERR_CFL),                        # above 1/sqrt(3)
+    ([(8, 8, 8)], [1], 0.0, 1.5, pic.PIC_ERR_ARG),                         # bad cfl
+])
+def test_invalid_batches_rejected_without_gpu(lib, ns, orders, dt, cfl, status):
+    import numpy as np
+    nb = len(ns)
+    n_arr = np.ascontiguousarray(np.asarray(ns, dtype=np.int32).reshape(max(nb, 1) if nb else 0, 3)) if nb else \
+        np.zeros((1, 3), dtype=np.int32)
+    o_arr = np.ascontiguousarray(np.asarray(orders if nb else [1], dtype=np.int32))
+    h = ct.c_void_p()
+    st = lib.pic_batch_init(nb, n_arr.ctypes.data, None, o_arr.ctypes.data, dt, cfl, 1, None, ct.byref(h))
+    assert st == status
+    assert h.value is None

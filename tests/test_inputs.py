@@ -51,3 +51,33 @@ def test_plasma_layout_and_ranges():
 def test_normal_moments():
     z = inputs.normal(5, 0, 200000, 3)
     assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+
+
+def test_ensemble_boxes_follow_the_recipe():
+    boxes = inputs.ensemble_boxes()
+    assert len(boxes) == 96
+    edges = set(inputs.ENSEMBLE["edges"])
+    for b in boxes:
+        assert set(b["n"]) <= edges
+        assert 1 <= b["ppc"] <= 8
+        assert 0.1 <= b["density"] <= 10.0
+        assert b["order"] in (1, 3)
+    # every edge, particle count and both orders occur; seeds are distinct
+    assert {e for b in boxes for e in b["n"]} == edges
+    assert {b["ppc"] for b in boxes} == set(range(1, 9))
+    assert len({b["seed"] for b in boxes}) == 96
+    # log-uniform densities: about half below the geometric mean 1
+    below = sum(b["density"] < 1.0 for b in boxes)
+    assert 30 <= below <= 66
+    # the same seed gives the same boxes
+    assert inputs.ensemble_boxes() == boxes
+
+
+def test_ensemble_particles_concatenate_in_box_order():
+    boxes = inputs.ensemble_boxes(nboxes=4, edges=(8, 16))
+    cat, counts, parts = inputs.ensemble_particles(boxes)
+    assert counts.tolist() == [int(np.prod(b["n"])) * b["ppc"] for b in boxes]
+    off = np.concatenate([[0], np.cumsum(counts)])
+    for i, p in enumerate(parts):
+        assert np.array_equal(cat["x"][off[i]:off[i + 1]], p["x"])
+        assert np.allclose(p["w"], boxes[i]["density"] / boxes[i]["ppc"])
