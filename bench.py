@@ -239,6 +239,68 @@ def field_error_statement(torch, steps=100):
     return res
 
 
+def ensemble_statement(torch, stream, steps=20):
+    """The batched ensemble (96 uneven periodic boxes, FP32-mixed): autotuned,
+    then `steps` steps timed as one graph replay with CUDA events on the
+    batch's stream; FP64 timed beside it."""
+    from paper_2101_12149_gb300 import inputs, pic
+    boxes = inputs.ensemble_boxes()
+    cat, counts, _ = inputs.ensemble_particles(boxes)
+    N = int(counts.sum())
+    C = sum(int(np.prod(b["n"])) for b in boxes)
+    dt = inputs.dt_from_cfl((1.0, 1.0, 1.0), inputs.ENSEMBLE["cfl"])
+    res = {"boxes": len(boxes), "particles": N, "cells": C,
+           "orders": {str(o): sum(b["order"] == o for b in boxes) for o in (1, 3)}}
+    for prec, name in ((pic.FP32_MIXED, "fp32_mixed"), (pic.FP64, "fp64")):
+        with pic.Batch([b["n"] for b in boxes], [b["order"] for b in boxes], dt=dt, precision=prec,
+                       stream=stream) as B:
+            B.load_particles(-1.0, 1.0, cat, counts)
+            if prec == pic.FP32_MIXED:
+                best, best_ms = B.autotune(trial_steps=3)
+                res["tuning"] = best
+            k = steps if prec == pic.FP32_MIXED else max(3, steps // 5)
+            B.step(k)  # captures the k-step graph, warms up
+            l0 = B.launch_count()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            B.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            res[name] = {"particle_steps_per_s": N * k / t, "cell_steps_per_s": C * k / t,
+                         "ms_per_step": 1e3 * t / k, "steps": k, "gpu_launches": B.launch_count() - l0}
+    res["fp32_mixed_speedup"] = res["fp32_mixed"]["particle_steps_per_s"] / res["fp64"]["particle_steps_per_s"]
+    return res
+
+
+def adjoint_statement(torch):
+    """The differentiation workload: 64^3, 4 ppc, order 2, drive A from seed 4,
+    200 steps with checkpoints every 20; forward + checkpointed reverse timed
+    on the host around pic_step_adjoint (it waits), FP32-mixed and FP64."""
+    from paper_2101_12149_gb300 import inputs, pic
+    w = inputs.WORKLOADS["adjoint_64"]
+    parts = inputs.workload_particles("adjoint_64")
+    A = inputs.drive_amplitude(w["seed"])
+    kd = 2 * np.pi / w["n"][0]
+    N = parts["x"].size
+    res = {"grid": "64^3", "particles": N, "steps": w["steps"], "ckpt_every": 20, "A": A}
+    s = torch.cuda.Stream()
+    for prec, name in ((pic.FP32_MIXED, "fp32_mixed"), (pic.FP64, "fp64")):
+        with pic.Context(w["n"], cfl=w["cfl"], order=w["order"], precision=prec, stream=s) as ctx:
+            ctx.load_particles(-1.0, 1.0, parts)
+            ctx.set_external_drive(A, kd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            loss, dA, du = ctx.step_adjoint(w["steps"], 20)
+            t = time.perf_counter() - t0
+            res[name] = {"seconds": t, "loss": loss, "dL_dA": dA, "dL_du_norm": float(np.linalg.norm(du)),
+                         "forward_equiv_particle_steps_per_s": N * w["steps"] / t}
+    res["fp32_vs_fp64_dL_dA_rel"] = abs(res["fp32_mixed"]["dL_dA"] - res["fp64"]["dL_dA"]) / abs(res["fp64"]["dL_dA"])
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -388,6 +450,9 @@ def main():
                        "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                        "what": "context creation + pic_load_particles from pinned host FP64 arrays + "
                                f"{e2e_steps} x (pic_step + pic_diagnostics read-back) + E_x field read-back"}
+        if rank == 0:
+            line["ensemble"] = ensemble_statement(torch, stream)
+            line["adjoint"] = adjoint_statement(torch)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline()
 
