@@ -25,7 +25,7 @@ _dp = ct.POINTER(ct.c_double)
 
 
 class _Grid(ct.Structure):
-    _fields_ = [("n", ct.c_int64 * 3), ("d", ct.c_double * 3)]
+    _fields_ = [("n", ct.c_int64 * 3), ("d", ct.c_double * 3), ("zopen", ct.c_int64)]
 
 
 def _declare(lib):
@@ -83,11 +83,12 @@ class Oracle:
 
     # -- helpers -----------------------------------------------------
     @staticmethod
-    def grid(n, d=(1.0, 1.0, 1.0)):
+    def grid(n, d=(1.0, 1.0, 1.0), zopen=False):
         g = _Grid()
         for a in range(3):
             g.n[a] = int(n[a])
             g.d[a] = float(d[a])
+        g.zopen = 1 if zopen else 0
         return g
 
     @staticmethod
@@ -171,6 +172,68 @@ class Oracle:
                               *[self._ptr(parts[k]) for k in keys],
                               self._ptr_array([fields[c] for c in range(9)]),
                               float(drive_amp), float(drive_k), float(t))
+
+    # -- moving window (z open) -----------------------------------------
+    # Readings of the wakefield run: z is open (fields beyond the ends are
+    # zero, particles leaving [0, Lz) are removed after their deposit); after
+    # the field update of step n the window moves one cell along z whenever
+    # speed * t_{n+1} reaches (shifts + 1) dz: fields move down one cell (the
+    # new front slab is zero), particles move by -dz and those below z = 0 are
+    # removed, and the new front slab of cells is filled with plasma.
+    @staticmethod
+    def density_profile(z_lab, n0, ramp_start, ramp_length):
+        """Plasma density at lab-frame z: 0 below ramp_start, rising linearly
+        over ramp_length to the plateau n0."""
+        z = np.asarray(z_lab, dtype=np.float64)
+        if ramp_length > 0:
+            return n0 * np.clip((z - ramp_start) / ramp_length, 0.0, 1.0)
+        return np.where(z >= ramp_start, n0, 0.0)
+
+    @staticmethod
+    def lattice_slab(g, k, ppc, shifts, n0, ramp_start, ramp_length, first_id):
+        """Plasma particles of the cell slab k (window frame): in each cell
+        (i, j, k) particles m = 0..ppc-1 at in-cell offset (m + 1/2)/ppc on every
+        axis, at rest, weight = density(lab z) dV / ppc; ids first_id +
+        (i ny + j) ppc + m; particles where the density is zero are not made."""
+        nx, ny = int(g.n[0]), int(g.n[1])
+        d = [float(g.d[a]) for a in range(3)]
+        i, j, m = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(ppc), indexing="ij")
+        off = (m.ravel() + 0.5) / ppc
+        x = (i.ravel() + off) * d[0]
+        y = (j.ravel() + off) * d[1]
+        z = (k + off) * d[2]
+        dens = Oracle.density_profile(z + shifts * d[2], n0, ramp_start, ramp_length)
+        ids = first_id + (i.ravel() * ny + j.ravel()) * ppc + m.ravel()
+        keep = dens > 0
+        zero = np.zeros(int(keep.sum()))
+        return {"x": x[keep], "y": y[keep], "z": z[keep], "ux": zero.copy(), "uy": zero.copy(), "uz": zero.copy(),
+                "w": dens[keep] * d[0] * d[1] * d[2] / ppc, "id": ids[keep].astype(np.int64)}
+
+    def window_step(self, g, p, dt, q, m, parts, fields, win):
+        """One step of a moving-window run.  parts: dict of the 7 particle
+        arrays plus 'id'; fields (9, nx, ny, nz) in place; win: dict with
+        step, shifts, speed, next_id and the injected plasma (ppc, n0,
+        ramp_start, ramp_length).  Returns the new particle dict."""
+        assert g.zopen
+        Lz = g.n[2] * g.d[2]
+        self.pic_step(g, p, dt, q, m, parts, fields, 0.0, 0.0, win["step"] * dt)
+        keep = (parts["z"] >= 0.0) & (parts["z"] < Lz)
+        parts = {k: np.ascontiguousarray(v[keep]) for k, v in parts.items()}
+        win["step"] += 1
+        while win["speed"] > 0 and win["speed"] * (win["step"] * dt) >= (win["shifts"] + 1) * g.d[2]:
+            fields[:, :, :, :-1] = fields[:, :, :, 1:].copy()
+            fields[:, :, :, -1] = 0.0
+            parts["z"] = parts["z"] - g.d[2]
+            keep = parts["z"] >= 0.0
+            parts = {k: v[keep] for k, v in parts.items()}
+            win["shifts"] += 1
+            if win["ppc"] > 0:
+                new = self.lattice_slab(g, int(g.n[2]) - 1, win["ppc"], win["shifts"], win["n0"], win["ramp_start"],
+                                        win["ramp_length"], win["next_id"])
+                win["next_id"] += int(g.n[0]) * int(g.n[1]) * win["ppc"]
+                parts = {k: np.concatenate([parts[k], new[k]]) for k in parts}
+            parts = {k: np.ascontiguousarray(v) for k, v in parts.items()}
+        return parts
 
     # -- diagnostics -------------------------------------------------
     def div_edge(self, g, F3):

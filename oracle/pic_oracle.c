@@ -59,6 +59,17 @@ static int64_t idx3(const orc_grid* g, int64_t i, int64_t j, int64_t k) {
     return (wrapi(i, g->n[0]) * g->n[1] + wrapi(j, g->n[1])) * g->n[2] + wrapi(k, g->n[2]);
 }
 
+/* With z open, a node outside [0, nz) along z holds no field and takes no current. */
+static int outside(const orc_grid* g, int64_t k) { return g->zopen && (k < 0 || k >= g->n[2]); }
+
+static double fetch(const orc_grid* g, const double* F, int64_t i, int64_t j, int64_t k) {
+    return outside(g, k) ? 0.0 : F[idx3(g, i, j, k)];
+}
+
+static void add_to(const orc_grid* g, double* F, int64_t i, int64_t j, int64_t k, double v) {
+    if (!outside(g, k)) F[idx3(g, i, j, k)] += v;
+}
+
 /* Staggering (in units of the cell size) of each field component along
  * each axis: rows Ex Ey Ez Bx By Bz. */
 static const double STAG[6][3] = {
@@ -129,7 +140,7 @@ void orc_gather(const orc_grid* g, int p, const double* const F[6],
                 for (int r2 = 0; r2 < NR; ++r2) {
                     const double wgt = wt[0][r0] * wt[1][r1] * wt[2][r2];
                     if (wgt == 0.0) continue;
-                    acc += wgt * F[c][idx3(g, first[0] + r0, first[1] + r1, first[2] + r2)];
+                    acc += wgt * fetch(g, F[c], first[0] + r0, first[1] + r1, first[2] + r2);
                 }
         EB[c] = acc;
     }
@@ -240,7 +251,7 @@ void orc_deposit_esirkepov(const orc_grid* g, int p, double dt, double qw,
                     node[comp] = b[comp] + w0;
                     node[t1] = b[t1] + w1;
                     node[t2] = b[t2] + w2;
-                    J[comp][idx3(g, node[0], node[1], node[2])] += coef * run;
+                    add_to(g, J[comp], node[0], node[1], node[2], coef * run);
                 }
             }
         }
@@ -264,7 +275,7 @@ void orc_deposit_rho(const orc_grid* g, int p, double qw, const double x[3], dou
             for (int r2 = 0; r2 < NR; ++r2) {
                 const double wgt = wt[0][r0] * wt[1][r1] * wt[2][r2];
                 if (wgt == 0.0) continue;
-                rho[idx3(g, first[0] + r0, first[1] + r1, first[2] + r2)] += qw * wgt / dV;
+                add_to(g, rho, first[0] + r0, first[1] + r1, first[2] + r2, qw * wgt / dV);
             }
 }
 
@@ -282,8 +293,8 @@ void orc_yee_b(const orc_grid* g, double h, const double* const E[3], double* co
             for (int64_t k = 0; k < nz; ++k) {
                 const int64_t c = idx3(g, i, j, k);
                 const double dEz_dy = (E[2][idx3(g, i, j + 1, k)] - E[2][c]) * iy;
-                const double dEy_dz = (E[1][idx3(g, i, j, k + 1)] - E[1][c]) * iz;
-                const double dEx_dz = (E[0][idx3(g, i, j, k + 1)] - E[0][c]) * iz;
+                const double dEy_dz = (fetch(g, E[1], i, j, k + 1) - E[1][c]) * iz;
+                const double dEx_dz = (fetch(g, E[0], i, j, k + 1) - E[0][c]) * iz;
                 const double dEz_dx = (E[2][idx3(g, i + 1, j, k)] - E[2][c]) * ix;
                 const double dEy_dx = (E[1][idx3(g, i + 1, j, k)] - E[1][c]) * ix;
                 const double dEx_dy = (E[0][idx3(g, i, j + 1, k)] - E[0][c]) * iy;
@@ -308,8 +319,8 @@ void orc_yee_e(const orc_grid* g, double dt, double* const E[3], const double* c
             for (int64_t k = 0; k < nz; ++k) {
                 const int64_t c = idx3(g, i, j, k);
                 const double dBz_dy = (B[2][c] - B[2][idx3(g, i, j - 1, k)]) * iy;
-                const double dBy_dz = (B[1][c] - B[1][idx3(g, i, j, k - 1)]) * iz;
-                const double dBx_dz = (B[0][c] - B[0][idx3(g, i, j, k - 1)]) * iz;
+                const double dBy_dz = (B[1][c] - fetch(g, B[1], i, j, k - 1)) * iz;
+                const double dBx_dz = (B[0][c] - fetch(g, B[0], i, j, k - 1)) * iz;
                 const double dBz_dx = (B[2][c] - B[2][idx3(g, i - 1, j, k)]) * ix;
                 const double dBy_dx = (B[1][c] - B[1][idx3(g, i - 1, j, k)]) * ix;
                 const double dBx_dy = (B[0][c] - B[0][idx3(g, i, j - 1, k)]) * iy;
@@ -339,7 +350,9 @@ void orc_yee_step(const orc_grid* g, double dt, double* const E[3], double* cons
  * external drive E_ext = drive_amp * y_hat * cos(drive_k x - drive_k t)),
  * Boris u^{n-1/2} -> u^{n+1/2}, advance x^n -> x^{n+1}, Esirkepov J^{n+1/2}
  * (J is zeroed first), periodic wrap of x^{n+1}, then the Yee update.
- * fields = {Ex,Ey,Ez,Bx,By,Bz,Jx,Jy,Jz}. */
+ * With z open, z^{n+1} is not wrapped: a particle that left [0, Lz) keeps
+ * its outside position (its current inside the grid was deposited) and the
+ * caller removes it.  fields = {Ex,Ey,Ez,Bx,By,Bz,Jx,Jy,Jz}. */
 void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64_t np,
                   double* x, double* y, double* z, double* ux, double* uy, double* uz,
                   const double* w, double* const fields[9],
@@ -363,7 +376,7 @@ void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64
         orc_deposit_esirkepov(g, p, dt, q * w[n], x0, x1, J);
         x[n] = orc_wrap(x1[0], L[0]);
         y[n] = orc_wrap(x1[1], L[1]);
-        z[n] = orc_wrap(x1[2], L[2]);
+        z[n] = g->zopen ? x1[2] : orc_wrap(x1[2], L[2]); /* z open: left unwrapped, the caller removes it */
         ux[n] = u[0];
         uy[n] = u[1];
         uz[n] = u[2];
@@ -384,7 +397,7 @@ void orc_div_edge(const orc_grid* g, const double* const F[3], double* out) {
                 const int64_t c = idx3(g, i, j, k);
                 out[c] = (F[0][c] - F[0][idx3(g, i - 1, j, k)]) / g->d[0] +
                          (F[1][c] - F[1][idx3(g, i, j - 1, k)]) / g->d[1] +
-                         (F[2][c] - F[2][idx3(g, i, j, k - 1)]) / g->d[2];
+                         (F[2][c] - fetch(g, F[2], i, j, k - 1)) / g->d[2];
             }
 }
 
@@ -397,7 +410,7 @@ void orc_div_face(const orc_grid* g, const double* const F[3], double* out) {
                 const int64_t c = idx3(g, i, j, k);
                 out[c] = (F[0][idx3(g, i + 1, j, k)] - F[0][c]) / g->d[0] +
                          (F[1][idx3(g, i, j + 1, k)] - F[1][c]) / g->d[1] +
-                         (F[2][idx3(g, i, j, k + 1)] - F[2][c]) / g->d[2];
+                         (fetch(g, F[2], i, j, k + 1) - F[2][c]) / g->d[2];
             }
 }
 

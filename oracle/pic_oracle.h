@@ -10,6 +10,7 @@
 typedef struct {
     int64_t n[3]; /* cells per axis */
     double d[3];  /* cell size per axis */
+    int64_t zopen; /* 0: periodic in z; 1: z open, fields beyond the ends are zero (moving-window runs) */
 } orc_grid;
 
 double orc_shape(int p, double xi);

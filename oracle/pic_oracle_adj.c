@@ -21,6 +21,7 @@
  *   Boris:    lamu^{n-1/2}, lamE_p, lamB_p by the reverse sweep of the rotation;
  *   gather:   lamF += weights * lamEB_p, lamx0 += (d weights/dx)^T (F lamEB_p),
  *             drive: lamA += lamE_y,p cos(k x - k t), lamx += -A k sin(..) lamE_y,p.
+ * Periodic grids only (orc_grid.zopen = 0).
  */
 #include <math.h>
 #include <stdint.h>

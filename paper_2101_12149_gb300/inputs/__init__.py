@@ -15,6 +15,8 @@ Sec. 4.2; normalised units, electrons q = -1, m = 1, cell size 1):
   wakefield     128 x 128 x 1024, 2 ppc, order 2, moving window, laser a0 = 2
   ensemble      96 boxes with edges in {16,24,32,48,64}, 1-8 ppc, n in [0.1, 10], order 1 or 3
   adjoint_64    64^3, 4 ppc, order 2, external plane-wave drive, 200 steps
+  WAKEFIELD     128 x 128 x 1024, moving window along z, laser + ramped plasma
+  ENSEMBLE      96 independent boxes of uneven sizes
 """
 import ctypes as ct
 import os
@@ -146,6 +148,74 @@ def ensemble_particles(boxes, sigma_u: float = ENSEMBLE["sigma_u"]):
     counts = np.array([p["x"].size for p in parts], dtype=np.int64)
     cat = {k: np.concatenate([p[k] for p in parts]) if parts else np.empty(0) for k in keys}
     return cat, counts, parts
+
+
+# Laser-wakefield-shaped run (moving window along z): 24 cells per laser
+# wavelength (omega0 = 2 pi / 24, critical density n_c = omega0^2 in these
+# units), a0 = 2 (E0 = a0 omega0), waist 24 cells, 1/e field half-length 30
+# cells, focus at z0 = 100 cells; plasma from a linear ramp over 64 cells
+# starting at z = 200 to the plateau n = 1e-3 n_c, 2 particles per cell, cold.
+WAKEFIELD = dict(n=(128, 128, 1024), ppc=2, order=2, lambda0=24.0, a0=2.0, w0=24.0, tau=30.0, z0=100.0,
+                 ramp_start=200.0, ramp_length=64.0, n_over_nc=1e-3, cfl=0.99, speed=1.0, steps=2000)
+# The same recipe shrunk to 16 x 16 x 64 cells (parity tests).
+WAKEFIELD_SMALL = dict(n=(16, 16, 64), ppc=2, order=2, lambda0=8.0, a0=2.0, w0=4.0, tau=6.0, z0=16.0,
+                       ramp_start=24.0, ramp_length=8.0, n_over_nc=1e-2, cfl=0.99, speed=1.0, steps=60)
+
+
+def wakefield_plasma_density(cfg) -> float:
+    omega0 = 2.0 * np.pi / cfg["lambda0"]
+    return cfg["n_over_nc"] * omega0 * omega0
+
+
+def laser_fields(cfg, d=(1.0, 1.0, 1.0)) -> np.ndarray:
+    """Initial fields (9, nx, ny, nz): a linearly polarised Gaussian pulse
+    moving along +z, E_x = E0 exp(-r^2/w0^2) exp(-(z-z0)^2/tau^2)
+    cos(omega0 (z-z0)) with r measured from the box axis, and B_y equal to the
+    same expression at B_y's staggered location; everything else zero."""
+    nx, ny, nz = cfg["n"]
+    omega0 = 2.0 * np.pi / cfg["lambda0"]
+    E0 = cfg["a0"] * omega0
+    cx, cy = 0.5 * nx * d[0], 0.5 * ny * d[1]
+
+    def pulse(x, y, z):
+        r2 = (x - cx) ** 2 + (y - cy) ** 2
+        return (E0 * np.exp(-r2 / cfg["w0"] ** 2) * np.exp(-((z - cfg["z0"]) / cfg["tau"]) ** 2)
+                * np.cos(omega0 * (z - cfg["z0"])))
+
+    i = (np.arange(nx) + 0.5)[:, None, None] * d[0]      # E_x and B_y sit at i + 1/2
+    j = np.arange(ny)[None, :, None] * d[1]
+    F = np.zeros((9, nx, ny, nz))
+    F[0] = pulse(i, j, np.arange(nz)[None, None, :] * d[2])
+    F[4] = pulse(i, j, (np.arange(nz) + 0.5)[None, None, :] * d[2])
+    return F
+
+
+def lattice_plasma(n, ppc, n0, ramp_start, ramp_length, d=(1.0, 1.0, 1.0), shifts=0):
+    """Cold plasma on a lattice: in each cell (i, j, k) particles m = 0..ppc-1
+    at in-cell offset (m + 1/2)/ppc on every axis, weight = density(lab z) dV /
+    ppc with the density rising linearly from 0 at ramp_start over
+    ramp_length to n0 (lab z = window z + shifts dz); particles where the
+    density is zero are left out.  Order: i, j, k, m."""
+    nx, ny, nz = (int(a) for a in n)
+    i, j, k, m = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), np.arange(ppc), indexing="ij")
+    off = (m.ravel() + 0.5) / ppc
+    x = (i.ravel() + off) * d[0]
+    y = (j.ravel() + off) * d[1]
+    z = (k.ravel() + off) * d[2]
+    zl = z + shifts * d[2]
+    if ramp_length > 0:
+        dens = n0 * np.clip((zl - ramp_start) / ramp_length, 0.0, 1.0)
+    else:
+        dens = np.where(zl >= ramp_start, n0, 0.0)
+    keep = dens > 0
+    zero = np.zeros(int(keep.sum()))
+    return {"x": x[keep], "y": y[keep], "z": z[keep], "ux": zero, "uy": zero.copy(), "uz": zero.copy(),
+            "w": dens[keep] * d[0] * d[1] * d[2] / ppc}
+
+
+def wakefield_particles(cfg):
+    return lattice_plasma(cfg["n"], cfg["ppc"], wakefield_plasma_density(cfg), cfg["ramp_start"],
+                          cfg["ramp_length"])
 
 
 def drive_amplitude(seed: int) -> float:
