@@ -75,8 +75,10 @@ typedef struct {
     int32_t precision;   /* PIC_FP64 or PIC_FP32_MIXED */
     int32_t order;       /* shape order 1..3 */
     int32_t sort_every;  /* counting sort every this many steps (>= 1) */
-    int32_t window_axis; /* -1 (no moving window); reserved */
-    double window_speed; /* reserved */
+    int32_t window_axis; /* -1: periodic box; 2: moving window along z (Sec. 4.2): z open (no field
+                            beyond the z ends, current there dropped, particles leaving z removed),
+                            x, y periodic; needs sort_every = 1 */
+    double window_speed; /* window speed in units of c, in [0, 1] (window_axis = 2) */
     uint64_t seed;       /* reserved for generators that run inside the library */
     int32_t tile[3];     /* cells per tile per axis (powers of two dividing n); 0 = automatic */
 } pic_grid_desc;
@@ -101,7 +103,8 @@ pic_status pic_load_particles(pic_ctx* ctx, double q, double m, int64_t n,
 
 /* Gather E,B at the particles, Boris push and position advance (one
  * particle per thread, fields read from global memory).  Saves the old
- * positions for pic_deposit.  Does not sort. */
+ * positions for pic_deposit.  Does not sort.  Periodic grids only
+ * (PIC_ERR_STATE with a moving window), as is pic_deposit. */
 pic_status pic_gather_push(pic_ctx* ctx);
 
 /* Zero J and deposit the Esirkepov current of the move made by the last
@@ -114,8 +117,32 @@ pic_status pic_yee_step(pic_ctx* ctx);
 
 /* nsteps full PIC steps: counting sort (at the sort cadence), fused tile
  * kernel (gather + push + advance + Esirkepov into shared memory, one flush
- * per tile), Yee update.  Checks the device error word at the end. */
+ * per tile), Yee update.  Checks the device error word at the end.
+ * With a moving window (Sec. 4.2: the domain moves with the beam at c, new
+ * plasma enters at the front, particles leaving at the back are removed),
+ * each step is: tile kernel, Yee update, then as often as
+ * window_speed * t_{n+1} has reached the next cell the window shift (all
+ * fields move down one cell along z with a zero front slab, particles move
+ * by -dz and those below z = 0 are removed) and the injection of the front
+ * slab's plasma (pic_set_window_plasma), then a sort that also drops removed
+ * particles; the step waits for the live particle count. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
+
+/* Plasma injected into each new front slab of a moving-window context:
+ * in every cell of the slab, ppc particles m = 0..ppc-1 at in-cell offset
+ * (m + 1/2)/ppc on every axis, at rest, of weight n(z) dV / ppc where the
+ * density at lab-frame z (window z + shifts * dz) is 0 below ramp_start,
+ * rises linearly over ramp_length (0 = a step) and is n0 beyond; none where
+ * it is zero.  Injected particles take ids counting on from the loaded ones,
+ * (i ny + j) ppc + m within a slab.  Call before pic_load_particles (it sizes
+ * the particle buffers for a full box of this plasma plus two slabs;
+ * exceeding that gives PIC_ERR_STATE).  PIC_ERR_STATE without a window. */
+pic_status pic_set_window_plasma(pic_ctx* ctx, int32_t ppc, double n0, double ramp_start,
+                                 double ramp_length);
+
+/* Number of window shifts so far and the lab-frame z of the window's
+ * lower end (shifts * dz).  Either pointer may be NULL. */
+pic_status pic_get_window(pic_ctx* ctx, int64_t* shifts, double* z_lab);
 
 /* Discrete adjoint of nsteps PIC steps (the paper has no adjoint; this is
  * the reverse-mode derivative of exactly the step pic_step runs: gather,
@@ -138,7 +165,8 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
  *   (ceil(nsteps/ckpt_every) + ckpt_every + 1) states plus the adjoint
  *   arrays) and frees it before returning; PIC_ERR_OOM if that fails.
  * On return the context holds the state after the nsteps steps, as after
- * pic_step(ctx, nsteps).  Waits.  PIC_ERR_STATE if no particles are loaded. */
+ * pic_step(ctx, nsteps).  Waits.  PIC_ERR_STATE if no particles are loaded
+ * or the context has a moving window (periodic grids only). */
 pic_status pic_step_adjoint(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss,
                             double* dL_dA, double* dL_du0, int on_device);
 

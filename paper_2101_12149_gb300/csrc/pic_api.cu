@@ -3,6 +3,7 @@
 // per-kernel timing.  Declarations and the contract: include/pic.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -189,6 +190,46 @@ cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
     return run_yee(c);
 }
 
+// Particle count after a sort with open z: the removed ones went to the last bin.
+cudaError_t read_live_count(pic_ctx* c) {
+    int live = 0;
+    cudaError_t e = cudaMemcpyAsync(&live, c->offsets + c->g.C, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) c->np = live;
+    return e;
+}
+
+cudaError_t window_shift(pic_ctx* c) { return pic::launch_window_shift(c); }
+cudaError_t inject(pic_ctx* c) { return pic::launch_inject(c); }
+
+// One step with the moving window: tile kernel (particles leaving z get the
+// removed key), Yee, then the window shifts (fields and particles down one
+// cell, front slab filled with plasma) as often as speed * t has passed the
+// next cell, then a sort that also drops the removed particles.  The state
+// after the step is sorted and holds only live particles.
+pic_status run_window_step(pic_ctx* c) {
+    PIC_CUDA(counted(c, "k_tile_step", 2, pic::launch_tile_step));
+    PIC_CUDA(run_yee(c));
+    c->step += 1;
+    const double t = double(c->step) * c->dt;
+    while (c->window_speed > 0.0 && c->window_speed * t >= double(c->shifts + 1) * c->g.d[2]) {
+        PIC_CUDA(counted(c, "k_window_shift", c->np > 0 ? 2 : 1, window_shift));
+        c->shifts += 1;
+        if (c->inj_ppc > 0) {
+            const int64_t total = int64_t(c->g.n[0]) * c->g.n[1] * c->inj_ppc;
+            if (c->np + total > c->cap) return fail(PIC_ERR_STATE, "particle capacity exceeded by injection");
+            PIC_CUDA(counted(c, "k_inject", 1, inject));
+            c->np += total;
+            c->next_id += total;
+        }
+    }
+    PIC_CUDA(run_sort(c));
+    PIC_CUDA(read_live_count(c));
+    c->since_sort = 1;
+    c->sorted = true;
+    return PIC_OK;
+}
+
 // One step of pic_step's direct path: sort at the cadence, tile kernel, Yee.
 cudaError_t run_one_step(pic_ctx* c) {
     const bool sort_now = c->since_sort >= c->sort_every;
@@ -373,14 +414,19 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     if (D.order < 1 || D.order > 3) return fail(PIC_ERR_ARG, "order must be 1, 2 or 3");
     if (D.precision != PIC_FP64 && D.precision != PIC_FP32_MIXED) return fail(PIC_ERR_ARG, "unknown precision");
     if (D.sort_every < 1) return fail(PIC_ERR_ARG, "sort_every must be >= 1");
-    if (D.window_axis != -1) return fail(PIC_ERR_ARG, "moving window not supported by this entry point");
+    if (D.window_axis != -1 && D.window_axis != 2) return fail(PIC_ERR_ARG, "window_axis must be -1 or 2 (z)");
+    if (D.window_axis == 2) {
+        if (!(D.window_speed >= 0.0 && D.window_speed <= 1.0))
+            return fail(PIC_ERR_ARG, "window_speed must be in [0, 1] (units of c)");
+        if (D.sort_every != 1) return fail(PIC_ERR_ARG, "a moving window needs sort_every == 1");
+    }
     int64_t C = 1;
     for (int a = 0; a < 3; ++a) {
         if (D.n[a] < D.order + 2 || D.n[a] < 3) return fail(PIC_ERR_ARG, "each extent must be >= order + 2 and >= 3");
         if (!(D.d[a] > 0.0) || !std::isfinite(D.d[a])) return fail(PIC_ERR_ARG, "cell sizes must be finite and > 0");
         C *= D.n[a];
     }
-    if (C >= (int64_t(1) << 31)) return fail(PIC_ERR_ARG, "too many cells (limit 2^31 - 1)");
+    if (C >= (int64_t(1) << 31) - 1) return fail(PIC_ERR_ARG, "too many cells (limit 2^31 - 2)");
     const double cfl_dt = 1.0 / std::sqrt(1.0 / (D.d[0] * D.d[0]) + 1.0 / (D.d[1] * D.d[1]) + 1.0 / (D.d[2] * D.d[2]));
     double dt = D.dt;
     if (dt == 0.0) {
@@ -438,6 +484,9 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     g.C = C;
     g.ntiles = int64_t(g.nt[0]) * g.nt[1] * g.nt[2];
     g.kbase = 0;
+    g.zopen = D.window_axis == 2 ? 1 : 0;
+    c->window = D.window_axis == 2;
+    c->window_speed = c->window ? D.window_speed : 0.0;
 
     auto bail = [&](cudaError_t e, const char* what) {
         pic_destroy(c);
@@ -448,12 +497,13 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     if ((e = cudaMalloc(&fb, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field allocation");
     for (int i = 0; i < 9; ++i) c->F[i] = fb + i * C * c->rsize;
     if ((e = cudaMemset(fb, 0, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field zeroing");
-    if ((e = cudaMalloc(&c->count, C * sizeof(int))) != cudaSuccess) return bail(e, "count allocation");
-    if ((e = cudaMemset(c->count, 0, C * sizeof(int))) != cudaSuccess) return bail(e, "count zeroing");
-    if ((e = cudaMalloc(&c->offsets, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "offsets allocation");
-    if ((e = cudaMemset(c->offsets, 0, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "offsets zeroing");
-    c->scan_chunks = int(pic::scan_status_words(C) - 1);
-    if ((e = cudaMalloc(&c->scan_status, pic::scan_status_words(C) * sizeof(unsigned long long))) != cudaSuccess)
+    // one bin more than cells (removed particles, open z) and its offset
+    if ((e = cudaMalloc(&c->count, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "count allocation");
+    if ((e = cudaMemset(c->count, 0, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "count zeroing");
+    if ((e = cudaMalloc(&c->offsets, (C + 2) * sizeof(int))) != cudaSuccess) return bail(e, "offsets allocation");
+    if ((e = cudaMemset(c->offsets, 0, (C + 2) * sizeof(int))) != cudaSuccess) return bail(e, "offsets zeroing");
+    c->scan_chunks = int(pic::scan_status_words(C + g.zopen) - 1);
+    if ((e = cudaMalloc(&c->scan_status, pic::scan_status_words(C + 1) * sizeof(unsigned long long))) != cudaSuccess)
         return bail(e, "scan state allocation");
     if ((e = cudaMalloc(&c->err, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
     if ((e = cudaMemset(c->err, 0, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
@@ -498,9 +548,16 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
-    if (n > c->cap || c->cap == 0) {
+    // moving window: room for the plasma the window brings in (a full box of
+    // it plus two slabs: the removed particles of a step go at the next sort)
+    int64_t need = n;
+    if (c->window && c->inj_ppc > 0) {
+        const int64_t slab = int64_t(c->g.n[0]) * c->g.n[1] * c->inj_ppc;
+        need = std::max<int64_t>(n, c->g.C * c->inj_ppc) + 2 * slab;
+    }
+    if (need > c->cap || c->cap == 0) {
         free_particles(c);
-        cudaError_t e = alloc_particles(c, n);
+        cudaError_t e = alloc_particles(c, need);
         if (e != cudaSuccess) {
             free_particles(c);
             return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "particle allocation") : cuda_fail(e, "alloc");
@@ -546,20 +603,48 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
         double wm;
         std::memcpy(&wm, &bits, sizeof(wm));
         c->w_max = n > 0 ? wm : 0.0;
+        if (c->window && c->inj_ppc > 0)  // the injected plasma's weight bounds the deposit's fixed-point scale too
+            c->w_max = std::max(c->w_max, c->inj_n0 * c->g.d[0] * c->g.d[1] * c->g.d[2] / c->inj_ppc);
     }
+    c->next_id = n;
+    c->shifts = 0;
+    c->step = 0;
     if (c->graph) {  // the deposit scale is a kernel argument baked into the graph
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
     e = run_sort(c);
     if (e != cudaSuccess) return cuda_fail(e, "initial sort");
+    if (c->window && (e = read_live_count(c)) != cudaSuccess) return cuda_fail(e, "initial sort");
     c->since_sort = 0;
     c->sorted = true;
     return read_error_word(c);
 }
 
+pic_status pic_set_window_plasma(pic_ctx* c, int32_t ppc, double n0, double ramp_start, double ramp_length) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!c->window) return fail(PIC_ERR_STATE, "the context has no moving window (window_axis = 2)");
+    if (c->cap > 0) return fail(PIC_ERR_STATE, "set the injected plasma before pic_load_particles");
+    if (ppc < 0 || ppc > 64 || !(n0 >= 0.0) || !std::isfinite(n0) || !std::isfinite(ramp_start) ||
+        !(ramp_length >= 0.0) || !std::isfinite(ramp_length))
+        return fail(PIC_ERR_ARG, "ppc in [0, 64], finite n0 >= 0, finite ramp_start, finite ramp_length >= 0");
+    c->inj_ppc = ppc;
+    c->inj_n0 = n0;
+    c->inj_ramp_start = ramp_start;
+    c->inj_ramp_length = ramp_length;
+    return PIC_OK;
+}
+
+pic_status pic_get_window(pic_ctx* c, int64_t* shifts, double* z_lab) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (shifts) *shifts = c->shifts;
+    if (z_lab) *z_lab = double(c->shifts) * c->g.d[2];
+    return PIC_OK;
+}
+
 pic_status pic_gather_push(pic_ctx* c) {
     if (pic_status s = check_ctx(c)) return s;
+    if (c->window) return fail(PIC_ERR_STATE, "the split API runs periodic grids only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     PIC_CUDA(counted(c, "k_gather_push", 1, pic::launch_gather_push_global));
     c->have_old = true;
@@ -568,6 +653,7 @@ pic_status pic_gather_push(pic_ctx* c) {
 
 pic_status pic_deposit(pic_ctx* c) {
     if (pic_status s = check_ctx(c)) return s;
+    if (c->window) return fail(PIC_ERR_STATE, "the split API runs periodic grids only");
     if (!c->have_old) return fail(PIC_ERR_STATE, "pic_deposit needs a preceding pic_gather_push");
     PIC_CUDA(counted(c, "k_deposit", 1, pic::launch_deposit_global));
     return PIC_OK;
@@ -586,6 +672,12 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (nsteps < 0) return fail(PIC_ERR_ARG, "nsteps < 0");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     int32_t left = nsteps;
+    if (c->window) {
+        for (; left > 0; --left)
+            if (pic_status s = run_window_step(c)) return s;
+        c->have_old = false;
+        return read_error_word(c);
+    }
     // With a sort every step, two consecutive steps return the particle
     // double buffer to its starting role, so a captured pair of steps can be
     // replayed as one graph launch.
@@ -634,6 +726,7 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
                             double* dL_du0, int on_device) {
     if (pic_status s = check_ctx(c)) return s;
     if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+    if (c->window) return fail(PIC_ERR_STATE, "the adjoint runs periodic grids only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (pic_status s = read_error_word(c)) return s;

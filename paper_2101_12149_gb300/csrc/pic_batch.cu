@@ -121,6 +121,7 @@ pic::Geom box_geom(const BoxInfo& B, const int tile[3]) {
     g.C = C;
     g.ntiles = int64_t(g.nt[0]) * g.nt[1] * g.nt[2];
     g.kbase = int(B.cbase);
+    g.zopen = 0;
     return g;
 }
 
@@ -191,6 +192,7 @@ template <typename R> void fill_args(const pic_batch* b, std::vector<char>& host
             Y.inv[d] = R(1.0 / B.d[d]);
         }
         Y.step = nullptr;
+        Y.zopen = 0;
         Y.h = R(0.5 * P.dt);
         yb[i] = Y;
         Y.h = R(P.dt);

@@ -44,7 +44,11 @@ struct Geom {
     double d[3];
     double L[3];
     int kbase;     // added to every cell key (a box's first key in a batch of boxes; 0 otherwise)
+    int zopen;     // 1: z is open (moving window): no field beyond the z ends, particles leaving z die
 };
+
+// Key of a removed particle: one past the last cell; the sort puts these last.
+__host__ __device__ inline int dead_key(const Geom& g) { return g.kbase + int(g.C); }
 
 struct Timer {
     const char* name;
@@ -96,6 +100,15 @@ struct pic_ctx {
     int ntimers = 0;
     void* tstate = nullptr;  // pending event pairs and the event pool
 
+    // moving window along z (window_axis = 2): speed in units of c, shifts so
+    // far, the plasma injected into each new front slab, next particle id
+    bool window = false;
+    double window_speed = 0.0;
+    int64_t shifts = 0;
+    int inj_ppc = 0;
+    double inj_n0 = 0.0, inj_ramp_start = 0.0, inj_ramp_length = 0.0;
+    int64_t next_id = 0;
+
     cudaGraphExec_t graph = nullptr;
     int graph_cur = 0;
     int graph_kernels = 0;
@@ -118,6 +131,10 @@ cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id);
 cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst);
 cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src);
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
+// moving window: move fields and particles down one cell along z (particles
+// below z = 0 die), then fill the front slab with plasma at slots [np, np + nx*ny*ppc)
+cudaError_t launch_window_shift(pic_ctx* c);
+cudaError_t launch_inject(pic_ctx* c);
 
 // adjoint (pic_adjoint.cu)
 // Work buffers of the reverse sweep: adjoints of positions (cell units) and

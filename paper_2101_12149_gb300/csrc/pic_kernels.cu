@@ -255,10 +255,16 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             const int kk = r - b * ez;
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
-            const int gk = wrap_any(ok - 2 + kk, g.n[2]);
-            const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
-            PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx, continue);
-            sEB[c * LY::eVol + a * LY::eX + b * LY::eY + kk] = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+            const int kz = ok - 2 + kk;
+            R v = R(0);
+            if (!g.zopen || unsigned(kz) < unsigned(g.n[2])) {  // z open: nothing beyond the ends
+                const int gk = wrap_any(kz, g.n[2]);
+                const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+                PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx,
+                             continue);
+                v = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+            }
+            sEB[c * LY::eVol + a * LY::eX + b * LY::eY + kk] = v;
         }
         if (kFixed)
             for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
@@ -351,6 +357,8 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                                          float(double((long long)hi.w * 32768 + lo.w) * A.inv_vscale));
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
+            // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
+            if (g.zopen && unsigned(ok - 4 + 4 * q) >= unsigned(g.n[2])) continue;
             const int gk = wrap_any(ok - 4 + 4 * q, g.n[2]);
             PIC_CHECK_OR(gk + 3 < g.n[2] && ((gk & 3) == 0), A.err, 6, gk, continue);
             float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
@@ -373,6 +381,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             else
                 v = sJ[c * LY::jVol + o];
             if (v == R(0)) continue;
+            if (g.zopen && unsigned(ok - 4 + kk) >= unsigned(g.n[2])) continue;
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             const int gk = wrap_any(ok - 4 + kk, g.n[2]);
@@ -581,9 +590,10 @@ template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>&
     const int64_t jp = c + (j + 1 == Y.n[1] ? -(int64_t)(Y.n[1] - 1) * sy : sy);
     const int64_t kp = c + (k + 1 == Y.n[2] ? -(int64_t)(Y.n[2] - 1) : 1);
     const R ex = Y.E[0][c], ey = Y.E[1][c], ez = Y.E[2][c];
+    const bool top = Y.zopen && k + 1 == Y.n[2];  // z open: E beyond the end is zero
     const R dEz_dy = (Y.E[2][jp] - ez) * Y.inv[1];
-    const R dEy_dz = (Y.E[1][kp] - ey) * Y.inv[2];
-    const R dEx_dz = (Y.E[0][kp] - ex) * Y.inv[2];
+    const R dEy_dz = ((top ? R(0) : Y.E[1][kp]) - ey) * Y.inv[2];
+    const R dEx_dz = ((top ? R(0) : Y.E[0][kp]) - ex) * Y.inv[2];
     const R dEz_dx = (Y.E[2][ip] - ez) * Y.inv[0];
     const R dEy_dx = (Y.E[1][ip] - ey) * Y.inv[0];
     const R dEx_dy = (Y.E[0][jp] - ex) * Y.inv[1];
@@ -602,9 +612,10 @@ template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>&
     const int64_t jm = c - (j == 0 ? -(int64_t)(Y.n[1] - 1) * sy : sy);
     const int64_t km = c - (k == 0 ? -(int64_t)(Y.n[2] - 1) : 1);
     const R bx = Y.B[0][c], by = Y.B[1][c], bz = Y.B[2][c];
+    const bool bottom = Y.zopen && k == 0;  // z open: B below the start is zero
     const R dBz_dy = (bz - Y.B[2][jm]) * Y.inv[1];
-    const R dBy_dz = (by - Y.B[1][km]) * Y.inv[2];
-    const R dBx_dz = (bx - Y.B[0][km]) * Y.inv[2];
+    const R dBy_dz = (by - (bottom ? R(0) : Y.B[1][km])) * Y.inv[2];
+    const R dBx_dz = (bx - (bottom ? R(0) : Y.B[0][km])) * Y.inv[2];
     const R dBz_dx = (bz - Y.B[2][im]) * Y.inv[0];
     const R dBy_dx = (by - Y.B[1][im]) * Y.inv[0];
     const R dBx_dy = (bx - Y.B[0][jm]) * Y.inv[1];
@@ -654,6 +665,7 @@ template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
     }
     Y.h = R(h);
     Y.step = nullptr;
+    Y.zopen = c->g.zopen;
     return Y;
 }
 
@@ -670,9 +682,11 @@ __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const do
     const double us[3] = {ux[p], uy[p], uz[p]};
     bool ok = isfinite(w[p]);
     int cell[3];
+    bool gone = false;  // z open: a particle loaded outside [0, Lz) is dropped by the first sort
     for (int a = 0; a < 3; ++a) {
         ok = ok && isfinite(xs[a]) && isfinite(us[a]);
         double xv = isfinite(xs[a]) ? xs[a] : 0.0;
+        if (a == 2 && g.zopen && !(xv >= 0.0 && xv < g.L[2])) gone = true, xv = 0.0;
         xv = fmod(xv, g.L[a]);
         xv = wrap_pos(xv, g.L[a]);
         double f;
@@ -690,7 +704,7 @@ __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const do
         A.pa[3 + a][p] = R(us[a]);
     }
     A.pa[6][p] = R(w[p]);
-    A.key[p] = key_of(g, cell[0], cell[1], cell[2]);
+    A.key[p] = gone ? dead_key(g) : key_of(g, cell[0], cell[1], cell[2]);
     id[p] = int(p);
     // largest |w|: non-negative doubles order like their bit patterns
     if (isfinite(w[p])) atomicMax(wmax, (unsigned long long)__double_as_longlong(fabs(double(R(w[p])))));
@@ -773,7 +787,7 @@ __global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out)
 
 template <typename R>
 __global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int ny, int nz, double dx, double dy,
-                            double dz, unsigned long long* out) {
+                            double dz, int zopen, unsigned long long* out) {
     const int64_t C = (int64_t)nx * ny * nz;
     double mx = 0.0;
     for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
@@ -781,12 +795,110 @@ __global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int n
         const int64_t ip = ((int64_t)wrap_once(i + 1, nx) * ny + j) * nz + k;
         const int64_t jp = ((int64_t)i * ny + wrap_once(j + 1, ny)) * nz + k;
         const int64_t kp = ((int64_t)i * ny + j) * nz + wrap_once(k + 1, nz);
+        const double bz_up = zopen && k + 1 == nz ? 0.0 : double(Bz[kp]);  // z open: zero beyond the end
         const double v = (double(Bx[ip]) - double(Bx[c])) / dx + (double(By[jp]) - double(By[c])) / dy +
-                         (double(Bz[kp]) - double(Bz[c])) / dz;
+                         (bz_up - double(Bz[c])) / dz;
         mx = fmax(mx, fabs(v));
     }
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
+}
+
+// ---------------------------------------------------------------------------
+// moving window (z open)
+// ---------------------------------------------------------------------------
+// F(i,j,k) <- F(i,j,k+1), F(i,j,nz-1) <- 0 in place: one warp per z column
+// walks it in chunks of 32 (each element is read before it is overwritten:
+// in the same chunk by the warp's load, or by the previous chunk's).
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_shift_fields(R* F0, int64_t C, int nz, int64_t columns) {
+    const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (col >= columns) return;
+    R* f = F0 + (int64_t)blockIdx.y * C + col * nz;
+    for (int k0 = 0; k0 < nz; k0 += 32) {
+        const int k = k0 + lane;
+        const R v = k + 1 < nz ? f[k + 1] : R(0);
+        __syncwarp();
+        if (k < nz) f[k] = v;
+        __syncwarp();
+    }
+}
+
+// Particles move down one cell along z; those below z = 0 get the removed key.
+template <typename R> __global__ void __launch_bounds__(kBlock) k_shift_particles(StepArgs<R> A) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    const int dead = dead_key(g);
+    const int key = A.key[p];
+    if (key == dead) return;
+    int i, j, k;
+    if (sizeof(R) == 8) {
+        const double z = double(A.pa[2][p]) - g.d[2];
+        A.pa[2][p] = R(z);
+        if (!(z >= 0.0)) {
+            A.key[p] = dead;
+            return;
+        }
+        double f;
+        split_pos(double(A.pa[0][p]), g.d[0], g.n[0], i, f);
+        split_pos(double(A.pa[1][p]), g.d[1], g.n[1], j, f);
+        split_pos(z, g.d[2], g.n[2], k, f);
+    } else {
+        cell_of(g, key, i, j, k);
+        k -= 1;  // the in-cell offset is unchanged
+        if (k < 0) {
+            A.key[p] = dead;
+            return;
+        }
+    }
+    A.key[p] = key_of(g, i, j, k);
+}
+
+struct InjectArgs {
+    int64_t first;     // first slot (particle index) written
+    int64_t first_id;  // id of slot `first`
+    int ppc;
+    double n0, ramp_start, ramp_length;
+    double zlab0;      // lab-frame z of the front slab's lower face
+};
+
+// The front slab k = nz-1: in each cell particles m = 0..ppc-1 at in-cell
+// offset (m + 1/2)/ppc on every axis, at rest, weight density(lab z) dV / ppc
+// with the density rising linearly from 0 at ramp_start over ramp_length to
+// n0; where the density is zero the slot gets the removed key.  Slot and id
+// follow (i ny + j) ppc + m.
+template <typename R> __global__ void __launch_bounds__(kBlock) k_inject(StepArgs<R> A, InjectArgs I, int* id) {
+    const Geom& g = A.g;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)g.n[0] * g.n[1] * I.ppc;
+    if (t >= total) return;
+    const int m = int(t % I.ppc);
+    const int64_t ij = t / I.ppc;
+    const int j = int(ij % g.n[1]), i = int(ij / g.n[1]);
+    const int k = g.n[2] - 1;
+    const double off = (m + 0.5) / I.ppc;
+    const double zl = I.zlab0 + off * g.d[2];
+    double dens;
+    if (I.ramp_length > 0.0) dens = I.n0 * fmin(fmax((zl - I.ramp_start) / I.ramp_length, 0.0), 1.0);
+    else dens = zl >= I.ramp_start ? I.n0 : 0.0;
+    const int64_t p = I.first + t;
+    if (sizeof(R) == 8) {
+        A.pa[0][p] = R((i + off) * g.d[0]);
+        A.pa[1][p] = R((j + off) * g.d[1]);
+        A.pa[2][p] = R((k + off) * g.d[2]);
+    } else {
+        A.pa[0][p] = R(off);
+        A.pa[1][p] = R(off);
+        A.pa[2][p] = R(off);
+    }
+    A.pa[3][p] = R(0);
+    A.pa[4][p] = R(0);
+    A.pa[5][p] = R(0);
+    A.pa[6][p] = R(dens * g.d[0] * g.d[1] * g.d[2] / I.ppc);
+    A.key[p] = dens > 0.0 ? key_of(g, i, j, k) : dead_key(g);
+    id[p] = int(I.first_id + t);
 }
 
 // ---------------------------------------------------------------------------
@@ -1061,13 +1173,46 @@ template <typename R> cudaError_t diag_impl(pic_ctx* c, double* d_out) {
     }
     k_diag_divb<R><<<nb, kBlock, 0, c->stream>>>(static_cast<const R*>(c->F[3]), static_cast<const R*>(c->F[4]),
                                                  static_cast<const R*>(c->F[5]), c->g.n[0], c->g.n[1], c->g.n[2],
-                                                 c->g.d[0], c->g.d[1], c->g.d[2],
+                                                 c->g.d[0], c->g.d[1], c->g.d[2], c->g.zopen,
                                                  reinterpret_cast<unsigned long long*>(d_out + 3));
     return cudaGetLastError();
 }
 
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out) {
     return c->prec == PIC_FP64 ? diag_impl<double>(c, d_out) : diag_impl<float>(c, d_out);
+}
+
+template <typename R> cudaError_t window_shift_impl(pic_ctx* c) {
+    const int64_t columns = int64_t(c->g.n[0]) * c->g.n[1];
+    const dim3 grid(unsigned((columns * 32 + kBlock - 1) / kBlock), 9);
+    k_shift_fields<R><<<grid, kBlock, 0, c->stream>>>(static_cast<R*>(c->F[0]), c->g.C, c->g.n[2], columns);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || c->np == 0) return e;
+    k_shift_particles<R><<<blocks_for(c->np), kBlock, 0, c->stream>>>(make_args<R>(c));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_window_shift(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? window_shift_impl<double>(c) : window_shift_impl<float>(c);
+}
+
+template <typename R> cudaError_t inject_impl(pic_ctx* c) {
+    InjectArgs I;
+    I.first = c->np;
+    I.first_id = c->next_id;
+    I.ppc = c->inj_ppc;
+    I.n0 = c->inj_n0;
+    I.ramp_start = c->inj_ramp_start;
+    I.ramp_length = c->inj_ramp_length;
+    I.zlab0 = double(c->shifts + c->g.n[2] - 1) * c->g.d[2];
+    const int64_t total = int64_t(c->g.n[0]) * c->g.n[1] * c->inj_ppc;
+    if (total == 0) return cudaSuccess;
+    k_inject<R><<<blocks_for(total), kBlock, 0, c->stream>>>(make_args<R>(c), I, c->P[c->cur].id);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inject(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? inject_impl<double>(c) : inject_impl<float>(c);
 }
 
 }  // namespace pic

@@ -188,10 +188,13 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
 
 size_t scan_status_words(int64_t C) { return size_t((C + kScanChunk - 1) / kScanChunk) + 1; }
 
+// Bins of the sort: one per cell, plus one for removed particles when z is open.
+static int64_t nbins(const pic_ctx* c) { return c->g.C + (c->g.zopen ? 1 : 0); }
+
 cudaError_t launch_hist(pic_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
-    k_hist<<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur].key, c->np, c->count, c->g.C, c->err);
+    k_hist<<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur].key, c->np, c->count, nbins(c), c->err);
     return cudaGetLastError();
 }
 
@@ -199,7 +202,7 @@ cudaError_t launch_scan(pic_ctx* c) {
     cudaError_t e =
         cudaMemsetAsync(c->scan_status, 0, (size_t(c->scan_chunks) + 1) * sizeof(unsigned long long), c->stream);
     if (e != cudaSuccess) return e;
-    k_scan<<<unsigned(c->scan_chunks), kSortBlock, 0, c->stream>>>(c->count, c->offsets, c->g.C, c->scan_status,
+    k_scan<<<unsigned(c->scan_chunks), kSortBlock, 0, c->stream>>>(c->count, c->offsets, nbins(c), c->scan_status,
                                                                   c->scan_chunks, c->err);
     return cudaGetLastError();
 }
@@ -209,10 +212,10 @@ cudaError_t launch_scatter(pic_ctx* c) {
     const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
     if (c->prec == PIC_FP64)
         k_scatter<double><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                            c->count, c->g.C, c->err);
+                                                            c->count, nbins(c), c->err);
     else
         k_scatter<float><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                           c->count, c->g.C, c->err);
+                                                           c->count, nbins(c), c->err);
     return cudaGetLastError();
 }
 

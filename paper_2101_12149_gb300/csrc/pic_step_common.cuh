@@ -135,6 +135,7 @@ template <typename R> struct YeeArgs {
     R inv[3];
     R h;
     long long* step;  // advanced by one thread when non-null
+    int zopen;        // no field beyond the z ends
 };
 
 // ---------------------------------------------------------------------------
@@ -203,6 +204,7 @@ __device__ __forceinline__ void offsets_local(GatherW<P, R>& G, const int base[3
         }
 }
 
+// With z open, a node beyond the z ends gets weight 0 (and offset 0).
 template <int P, typename R>
 __device__ __forceinline__ void offsets_global(GatherW<P, R>& G, const Geom& g, const int cell[3],
                                                const int first_n[3], const int first_s[3]) {
@@ -214,6 +216,13 @@ __device__ __forceinline__ void offsets_global(GatherW<P, R>& G, const Geom& g, 
             G.on[a][r] = wrap_once(cell[a] + first_n[a] + r, g.n[a]) * st[a];
             G.os[a][r] = wrap_once(cell[a] + first_s[a] + r, g.n[a]) * st[a];
         }
+    if (g.zopen) {
+#pragma unroll
+        for (int r = 0; r <= P; ++r) {
+            if (unsigned(cell[2] + first_n[2] + r) >= unsigned(g.n[2])) G.on[2][r] = 0, G.wn[2][r] = R(0);
+            if (unsigned(cell[2] + first_s[2] + r) >= unsigned(g.n[2])) G.os[2][r] = 0, G.ws[2][r] = R(0);
+        }
+    }
 }
 
 // Current target in the global arrays: node (cell + b + slot) per axis,
@@ -222,7 +231,9 @@ template <int P, typename R> struct JTarget {
     R* J[3];
     int cx, cy, cz;  // first window node per axis (unwrapped)
     int nx, ny, nz;
+    int zopen;       // drop current beyond the z ends
     __device__ __forceinline__ void add(int c, int i, int j, int k, R v) const {
+        if (zopen && unsigned(cz + k) >= unsigned(nz)) return;
         const int gi = wrap_once(cx + i, nx), gj = wrap_once(cy + j, ny), gk = wrap_once(cz + k, nz);
         atomicAdd(J[c] + ((int64_t)gi * ny + gj) * nz + gk, v);
     }
@@ -301,6 +312,7 @@ __device__ __forceinline__ void jtarget_global(JTarget<P, R>& t, const Geom& g, 
     t.nx = g.n[0];
     t.ny = g.n[1];
     t.nz = g.n[2];
+    t.zopen = g.zopen;
 }
 
 // ---------------------------------------------------------------------------
@@ -404,16 +416,20 @@ __device__ __forceinline__ void load_particle(const StepArgs<R>& A, int p, int c
 }
 
 // Store the moved particle in place: momentum, wrapped position, new cell key.
+// With z open, a particle whose new z is outside [0, Lz) gets the removed key.
 template <typename R>
 __device__ __forceinline__ void store_particle(const StepArgs<R>& A, int p, const int cell[3], const Moved<R>& mv) {
     const Geom& g = A.g;
 #pragma unroll
     for (int a = 0; a < 3; ++a) A.pa[3 + a][p] = mv.u[a];
     int nc[3];
+    bool gone = false;
     if (sizeof(R) == 8) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const double xw = wrap_pos(mv.xg1[a], g.L[a]);
+            double xw = mv.xg1[a];
+            if (a == 2 && g.zopen) gone = !(xw >= 0.0 && xw < g.L[2]);
+            else xw = wrap_pos(xw, g.L[a]);
             A.pa[a][p] = R(xw);
             double f;
             split_pos(xw, g.d[a], g.n[a], nc[a], f);
@@ -422,11 +438,20 @@ __device__ __forceinline__ void store_particle(const StepArgs<R>& A, int p, cons
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             float nf;
-            renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
+            if (a == 2 && g.zopen) {
+                const float fl = floorf(float(mv.f1[2]));
+                nf = float(mv.f1[2]) - fl;
+                int cz = cell[2] + int(fl);
+                if (nf >= 1.0f) nf -= 1.0f, cz += 1;
+                gone = unsigned(cz) >= unsigned(g.n[2]);
+                nc[2] = gone ? 0 : cz;
+            } else {
+                renormalise(float(mv.f1[a]), cell[a], g.n[a], nc[a], nf);
+            }
             A.pa[a][p] = R(nf);
         }
     }
-    A.key[p] = key_of(g, nc[0], nc[1], nc[2]);
+    A.key[p] = gone ? dead_key(g) : key_of(g, nc[0], nc[1], nc[2]);
 }
 
 // Gather + push + advance + Esirkepov for one tile of cells per CTA.

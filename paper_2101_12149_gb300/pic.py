@@ -63,6 +63,8 @@ def load_library(path: str = LIB_PATH):
             "pic_yee_step": [P],
             "pic_step": [P, I32],
             "pic_step_adjoint": [P, I32, I32, P, P, P, ct.c_int],
+            "pic_set_window_plasma": [P, I32, D, D, D],
+            "pic_get_window": [P, ct.POINTER(I64), ct.POINTER(D)],
             "pic_get_field": [P, I32, P, ct.c_int],
             "pic_set_field": [P, I32, P, ct.c_int],
             "pic_num_particles": [P, ct.POINTER(I64)],
@@ -130,7 +132,7 @@ class Context:
     """One PIC simulation: grid, fields and one particle species on one GPU."""
 
     def __init__(self, n, d=(1.0, 1.0, 1.0), dt=0.0, cfl=0.99, precision=FP64, order=1, sort_every=1,
-                 tile=(0, 0, 0), stream=None):
+                 tile=(0, 0, 0), stream=None, window_speed=None):
         self.lib = load_library()
         desc = GridDesc()
         for a in range(3):
@@ -142,8 +144,8 @@ class Context:
         desc.precision = int(precision)
         desc.order = int(order)
         desc.sort_every = int(sort_every)
-        desc.window_axis = -1
-        desc.window_speed = 0.0
+        desc.window_axis = -1 if window_speed is None else 2
+        desc.window_speed = 0.0 if window_speed is None else float(window_speed)
         desc.seed = 0
         self.n = tuple(int(v) for v in n)
         self.C = self.n[0] * self.n[1] * self.n[2]
@@ -209,6 +211,14 @@ class Context:
 
     def step(self, nsteps=1):
         _check(self.lib.pic_step(self.h, int(nsteps)))
+
+    def set_window_plasma(self, ppc, n0, ramp_start, ramp_length):
+        _check(self.lib.pic_set_window_plasma(self.h, int(ppc), float(n0), float(ramp_start), float(ramp_length)))
+
+    def window(self):
+        s, z = ct.c_int64(), ct.c_double()
+        _check(self.lib.pic_get_window(self.h, ct.byref(s), ct.byref(z)))
+        return {"shifts": s.value, "z_lab": z.value}
 
     def step_adjoint(self, nsteps, ckpt_every=20, du=None):
         """Run nsteps steps and the discrete adjoint of L = 1/2 sum(|E|^2+|B|^2) dV

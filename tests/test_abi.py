@@ -55,6 +55,7 @@ def _init(lib, **kw):
     d.order = kw.get("order", 1)
     d.sort_every = kw.get("sort_every", 1)
     d.window_axis = kw.get("window_axis", -1)
+    d.window_speed = kw.get("window_speed", 0.0)
     h = ct.c_void_p()
     st = lib.pic_init_grid(ct.byref(d), None, ct.byref(h))
     return st, h
@@ -72,7 +73,9 @@ def _init(lib, **kw):
     (dict(sort_every=0), pic.PIC_ERR_ARG),
     (dict(tile=(3, 8, 8)), pic.PIC_ERR_ARG),             # not a power of two
     (dict(tile=(16, 8, 8)), pic.PIC_ERR_ARG),            # larger than the grid
-    (dict(window_axis=2), pic.PIC_ERR_ARG),
+    (dict(window_axis=1), pic.PIC_ERR_ARG),              # only z
+    (dict(window_axis=2, sort_every=2), pic.PIC_ERR_ARG),
+    (dict(window_axis=2, window_speed=1.5), pic.PIC_ERR_ARG),
 ])
 def test_invalid_descriptions_rejected_without_gpu(lib, kw, status):
     st, h = _init(lib, **kw)
