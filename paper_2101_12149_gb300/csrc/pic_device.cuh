@@ -206,6 +206,7 @@ template <int P, typename R> struct EsirkAxisD;
 template <int P, typename R> struct EsirkAxis {
     static constexpr int NW = P + 2;
     int b;
+    bool narrow;  // both shapes start at node b: slot P+1 is zero, and so is the last cumulative sum
     R S0[NW];
     R dS[NW];
 
@@ -221,6 +222,7 @@ template <int P, typename R> struct EsirkAxis {
         // cannot index outside the window
         const int off0 = min(first0 - b, 1);
         const int off1 = min(first1 - b, 1);
+        narrow = off0 == 0 && off1 == 0;
 #pragma unroll
         for (int a = 0; a < NW; ++a) {
             const R s0 = off0 == 0 ? (a <= P ? w0[a] : R(0)) : (a >= 1 ? w0[a - 1] : R(0));

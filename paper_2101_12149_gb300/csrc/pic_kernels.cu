@@ -78,59 +78,58 @@ __device__ __forceinline__ R interp_smem(const R* __restrict__ base, const R* wx
 // Esirkepov deposit of one particle into the staged J box; `base` is the
 // element offset of window slot (0,0,0).  Same arithmetic as
 // esirkepov_deposit (the global-memory form).
-template <int P, typename R, class LY>
+template <int P, typename R, class LY, int NC = P + 1, int NT = P + 2>
 __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict__ J1, R* __restrict__ J2, int base,
                                                const EsirkAxis<P, R> ax[3], const R coef[3]) {
-    constexpr int NW = P + 2;
     R* jx = J0 + base;
     R* jy = J1 + base;
     R* jz = J2 + base;
     {
-        R cum[NW - 1];
+        R cum[NC];
         R run = R(0);
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
 #pragma unroll
-        for (int j = 0; j < NW; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
+            for (int k = 0; k < NT; ++k) {
                 const R Az = ax[2].S0[k] + R(0.5) * ax[2].dS[k];
                 const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
                 const R Q = ax[1].S0[j] * Az + ax[1].dS[j] * Bz;
 #pragma unroll
-                for (int i = 0; i < NW - 1; ++i) atomicAdd(jx + i * LY::jX + j * LY::jY + k, cum[i] * Q);
+                for (int i = 0; i < NC; ++i) atomicAdd(jx + i * LY::jX + j * LY::jY + k, cum[i] * Q);
             }
     }
     {
-        R cum[NW - 1];
+        R cum[NC];
         R run = R(0);
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
 #pragma unroll
-        for (int i = 0; i < NW; ++i)
+        for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
+            for (int k = 0; k < NT; ++k) {
                 const R Az = ax[2].S0[k] + R(0.5) * ax[2].dS[k];
                 const R Bz = R(0.5) * ax[2].S0[k] + R(1.0 / 3.0) * ax[2].dS[k];
                 const R Q = ax[0].S0[i] * Az + ax[0].dS[i] * Bz;
 #pragma unroll
-                for (int j = 0; j < NW - 1; ++j) atomicAdd(jy + i * LY::jX + j * LY::jY + k, cum[j] * Q);
+                for (int j = 0; j < NC; ++j) atomicAdd(jy + i * LY::jX + j * LY::jY + k, cum[j] * Q);
             }
     }
     {
-        R cum[NW - 1];
+        R cum[NC];
         R run = R(0);
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
 #pragma unroll
-        for (int i = 0; i < NW; ++i)
+        for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int j = 0; j < NW; ++j) {
+            for (int j = 0; j < NT; ++j) {
                 const R Ay = ax[1].S0[j] + R(0.5) * ax[1].dS[j];
                 const R By = R(0.5) * ax[1].S0[j] + R(1.0 / 3.0) * ax[1].dS[j];
                 const R Q = ax[0].S0[i] * Ay + ax[0].dS[i] * By;
 #pragma unroll
-                for (int k = 0; k < NW - 1; ++k) atomicAdd(jz + i * LY::jX + j * LY::jY + k, cum[k] * Q);
+                for (int k = 0; k < NC; ++k) atomicAdd(jz + i * LY::jX + j * LY::jY + k, cum[k] * Q);
             }
     }
 }
@@ -153,72 +152,150 @@ __device__ __forceinline__ void red_fixed(int* lo, int* hi, float v, float vscal
     atomicAdd(hi, h);
 }
 
-template <int P, class LY>
+template <int P, class LY, int NC = P + 1, int NT = P + 2>
 __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int base, const EsirkAxis<P, float> ax[3],
                                                      const float coef[3], float vscale) {
-    constexpr int NW = P + 2;
     int* jx = sJ + base;                  // lo of J_x; hi at + jVol
     int* jy = sJ + 2 * LY::jVol + base;   // lo of J_y
     int* jz = sJ + 4 * LY::jVol + base;   // lo of J_z
     constexpr int H = LY::jVol;
     {
-        float cum[NW - 1];
+        float cum[NC];
         float run = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[0].dS[w]; cum[w] = coef[0] * run; }
 #pragma unroll
-        for (int j = 0; j < NW; ++j)
+        for (int j = 0; j < NT; ++j)
 #pragma unroll
-            for (int kk = 0; kk < NW; ++kk) {
+            for (int kk = 0; kk < NT; ++kk) {
                 const float Az = ax[2].S0[kk] + 0.5f * ax[2].dS[kk];
                 const float Bz = 0.5f * ax[2].S0[kk] + (1.0f / 3.0f) * ax[2].dS[kk];
                 const float Q = ax[1].S0[j] * Az + ax[1].dS[j] * Bz;
 #pragma unroll
-                for (int i = 0; i < NW - 1; ++i) {
+                for (int i = 0; i < NC; ++i) {
                     const int o = i * LY::jX + j * LY::jY + kk;
                     red_fixed(jx + o, jx + H + o, cum[i] * Q, vscale);
                 }
             }
     }
     {
-        float cum[NW - 1];
+        float cum[NC];
         float run = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[1].dS[w]; cum[w] = coef[1] * run; }
 #pragma unroll
-        for (int i = 0; i < NW; ++i)
+        for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int kk = 0; kk < NW; ++kk) {
+            for (int kk = 0; kk < NT; ++kk) {
                 const float Az = ax[2].S0[kk] + 0.5f * ax[2].dS[kk];
                 const float Bz = 0.5f * ax[2].S0[kk] + (1.0f / 3.0f) * ax[2].dS[kk];
                 const float Q = ax[0].S0[i] * Az + ax[0].dS[i] * Bz;
 #pragma unroll
-                for (int j = 0; j < NW - 1; ++j) {
+                for (int j = 0; j < NC; ++j) {
                     const int o = i * LY::jX + j * LY::jY + kk;
                     red_fixed(jy + o, jy + H + o, cum[j] * Q, vscale);
                 }
             }
     }
     {
-        float cum[NW - 1];
+        float cum[NC];
         float run = 0.f;
 #pragma unroll
-        for (int w = 0; w < NW - 1; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
+        for (int w = 0; w < NC; ++w) { run += ax[2].dS[w]; cum[w] = coef[2] * run; }
 #pragma unroll
-        for (int i = 0; i < NW; ++i)
+        for (int i = 0; i < NT; ++i)
 #pragma unroll
-            for (int j = 0; j < NW; ++j) {
+            for (int j = 0; j < NT; ++j) {
                 const float Ay = ax[1].S0[j] + 0.5f * ax[1].dS[j];
                 const float By = 0.5f * ax[1].S0[j] + (1.0f / 3.0f) * ax[1].dS[j];
                 const float Q = ax[0].S0[i] * Ay + ax[0].dS[i] * By;
 #pragma unroll
-                for (int kk = 0; kk < NW - 1; ++kk) {
+                for (int kk = 0; kk < NC; ++kk) {
                     const int o = i * LY::jX + j * LY::jY + kk;
                     red_fixed(jz + o, jz + H + o, cum[kk] * Q, vscale);
                 }
             }
     }
 }
+
+// Deposit of one particle into the staged J box: the window's first node is
+// (li + 2 + b_x, lj + 2 + b_y, lk + 4 + b_z) in box coordinates.  NARROW: all
+// three axes have both shapes starting at node b, so the stencil is P cumulative
+// slots by (P + 1)^2 transverse nodes (the skipped slots hold exact zeros and,
+// on the cumulative axis, the rounding residue of sum dS = 0).
+template <int P, typename R, class LY, bool NARROW>
+__device__ __forceinline__ void tile_deposit(const StepArgs<R>& A, R* sJ, int li, int lj, int lk,
+                                             const EsirkAxis<P, R> ax[3], R wq) {
+    constexpr int NC = NARROW ? P : P + 1;
+    constexpr int NT = NARROW ? P + 1 : P + 2;
+    const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
+    const int bx = li + 2 + ax[0].b, by = lj + 2 + ax[1].b, bz = lk + 4 + ax[2].b;
+    PIC_CHECK_OR(bx >= 0 && bx + P + 1 < LY::JX && by >= 0 && by + P + 1 < LY::JY && bz >= 0 && bz + P + 1 < LY::JZ,
+                 A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8), return);
+    const int base = bx * LY::jX + by * LY::jY + bz;
+    if constexpr (sizeof(R) == 4)
+        esirkepov_smem_fixed<P, LY, NC, NT>(reinterpret_cast<int*>(sJ), base,
+                                            reinterpret_cast<const EsirkAxis<P, float>*>(ax),
+                                            reinterpret_cast<const float*>(coef), A.vscale);
+    else
+        esirkepov_smem<P, R, LY, NC, NT>(sJ, sJ + LY::jVol, sJ + 2 * LY::jVol, base, ax, coef);
+}
+
+// Position of the n-th set bit (n counted from 0) of m; n < popcount(m).
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const unsigned low = (1u << w) - 1u;
+        const int c = __popc(m & low);
+        if (n >= c) {
+            n -= c;
+            m >>= w;
+            pos += w;
+        } else {
+            m &= low;
+        }
+    }
+    return pos;
+}
+
+// A move waiting for the full-window deposit: local cell, the in-cell
+// fractions before and after (relative to the old cell) and the weight.
+template <typename R> struct TileMove {
+    R f0[3], f1[3], wq;
+    int cell;  // li | lj << 8 | lk << 16
+    __device__ __forceinline__ static TileMove zero() {
+        TileMove t;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) t.f0[a] = t.f1[a] = R(0);
+        t.wq = R(0);
+        t.cell = 0;
+        return t;
+    }
+    __device__ __forceinline__ void set(int li, int lj, int lk, const R* a0, const R* a1, R w) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f0[a] = a0[a], f1[a] = a1[a];
+        wq = w;
+        cell = li | (lj << 8) | (lk << 16);
+    }
+    __device__ __forceinline__ TileMove shfl(int src) const {
+        TileMove t;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            t.f0[a] = __shfl_sync(0xffffffffu, f0[a], src);
+            t.f1[a] = __shfl_sync(0xffffffffu, f1[a], src);
+        }
+        t.wq = __shfl_sync(0xffffffffu, wq, src);
+        t.cell = __shfl_sync(0xffffffffu, cell, src);
+        return t;
+    }
+    template <int P, class LY> __device__ __forceinline__ void deposit(const StepArgs<R>& A, R* sJ) const {
+        EsirkAxis<P, R> ax[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) ax[a].init(f0[a], f1[a]);
+        tile_deposit<P, R, LY, false>(A, sJ, cell & 0xff, (cell >> 8) & 0xff, cell >> 16, ax, wq);
+    }
+};
 
 // Block size of the tile kernel: FP32-mixed 512 threads (one CTA per SM, its
 // shared memory holding the fixed-point J box), FP64 256.
@@ -279,60 +356,93 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     const int cnt = end - beg;
     const int run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
     const int nrun = (cnt + run - 1) / run;
-    for (int rr = threadIdx.x; rr < nrun; rr += blockDim.x) {
+    // Warps step their lanes' runs in lockstep.  A move whose old and new
+    // shapes start on the same node along every axis (most moves: crossing a
+    // cell face is rare) deposits the narrow stencil at once; the others go to
+    // a per-warp queue held one slot per lane in registers and are deposited
+    // 32 at a time with the full window, so neither kind runs with idle lanes.
+    const int lane = threadIdx.x & 31;
+    TileMove<R> qs = TileMove<R>::zero();  // this lane's queue slot
+    int qn = 0;                            // queued moves (warp-uniform)
+    for (int rbase = threadIdx.x - lane; rbase < nrun; rbase += blockDim.x) {
+        const int rr = rbase + lane;
         const int p0 = beg + rr * run;
-        const int p1 = min(p0 + run, end);
-        for (int p = p0; p < p1; ++p) {
-            int cell[3];
-            R f0[3], u[3], wq;
-            double xg0[3];
-            load_particle<R>(A, p, cell, f0, xg0, u, wq);
-            const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
-            // the fixed-point sums are exact for up to 65535 particles per tile
-            const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
-                                unsigned(lk) < unsigned(g.T[2]) && (!kFixed || p - beg < 65535);
-            if (!inside) {
-                const int slot = atomicAdd(A.outn, 1);
-                A.outl[slot] = p;
-                continue;
-            }
-            R EB[6];
-            {
-                GatherW<P, R> G;
-                int fn[3], fs[3];
-                gather_weights<P, R>(f0, G, fn, fs);
-                const int bnx = (li + 2 + fn[0]) * LY::eX, bsx = (li + 2 + fs[0]) * LY::eX;
-                const int bny = (lj + 2 + fn[1]) * LY::eY, bsy = (lj + 2 + fs[1]) * LY::eY;
-                const int bnz = lk + 2 + fn[2], bsz = lk + 2 + fs[2];
-                EB[0] = interp_smem<P, R, LY>(sEB + 0 * LY::eVol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
-                EB[1] = interp_smem<P, R, LY>(sEB + 1 * LY::eVol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
-                EB[2] = interp_smem<P, R, LY>(sEB + 2 * LY::eVol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
-                EB[3] = interp_smem<P, R, LY>(sEB + 3 * LY::eVol + bnx + bsy + bsz, G.wn[0], G.ws[1], G.ws[2]);
-                EB[4] = interp_smem<P, R, LY>(sEB + 4 * LY::eVol + bsx + bny + bsz, G.ws[0], G.wn[1], G.ws[2]);
-                EB[5] = interp_smem<P, R, LY>(sEB + 5 * LY::eVol + bsx + bsy + bnz, G.ws[0], G.ws[1], G.wn[2]);
-            }
-            Moved<R> mv;
-            push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
-            if (!mv.ok) {
-                raise_error(A.err, ERRBIT_PARTICLE);
-                continue;
-            }
-            EsirkAxis<P, R> ax[3];
+        const int len = rr < nrun ? min(run, end - p0) : 0;
+        const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        for (int it = 0; it < maxlen; ++it) {
+            const int p = p0 + it;
+            bool wide = false;
+            TileMove<R> mine = TileMove<R>::zero();
+            if (it < len) {
+                int cell[3];
+                R f0[3], u[3], wq;
+                double xg0[3];
+                load_particle<R>(A, p, cell, f0, xg0, u, wq);
+                const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
+                // the fixed-point sums are exact for up to 65535 particles per tile
+                const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
+                                    unsigned(lk) < unsigned(g.T[2]) && (!kFixed || p - beg < 65535);
+                if (!inside) {
+                    const int slot = atomicAdd(A.outn, 1);
+                    A.outl[slot] = p;
+                } else {
+                    R EB[6];
+                    {
+                        GatherW<P, R> G;
+                        int fn[3], fs[3];
+                        gather_weights<P, R>(f0, G, fn, fs);
+                        const int bnx = (li + 2 + fn[0]) * LY::eX, bsx = (li + 2 + fs[0]) * LY::eX;
+                        const int bny = (lj + 2 + fn[1]) * LY::eY, bsy = (lj + 2 + fs[1]) * LY::eY;
+                        const int bnz = lk + 2 + fn[2], bsz = lk + 2 + fs[2];
+                        EB[0] = interp_smem<P, R, LY>(sEB + 0 * LY::eVol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
+                        EB[1] = interp_smem<P, R, LY>(sEB + 1 * LY::eVol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
+                        EB[2] = interp_smem<P, R, LY>(sEB + 2 * LY::eVol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
+                        EB[3] = interp_smem<P, R, LY>(sEB + 3 * LY::eVol + bnx + bsy + bsz, G.wn[0], G.ws[1], G.ws[2]);
+                        EB[4] = interp_smem<P, R, LY>(sEB + 4 * LY::eVol + bsx + bny + bsz, G.ws[0], G.wn[1], G.ws[2]);
+                        EB[5] = interp_smem<P, R, LY>(sEB + 5 * LY::eVol + bsx + bsy + bnz, G.ws[0], G.ws[1], G.wn[2]);
+                    }
+                    Moved<R> mv;
+                    push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
+                    if (!mv.ok) {
+                        raise_error(A.err, ERRBIT_PARTICLE);
+                    } else {
+                        store_particle<R>(A, p, cell, mv);
+                        EsirkAxis<P, R> ax[3];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
-            const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
-            const int bx = li + 2 + ax[0].b, by = lj + 2 + ax[1].b, bz = lk + 4 + ax[2].b;
-            PIC_CHECK_OR(bx >= 0 && bx + P + 1 < LY::JX && by >= 0 && by + P + 1 < LY::JY && bz >= 0 &&
-                             bz + P + 1 < LY::JZ,
-                         A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8), continue);
-            if constexpr (kFixed)
-                esirkepov_smem_fixed<P, LY>(sJi, bx * LY::jX + by * LY::jY + bz, ax, coef, A.vscale);
-            else
-                esirkepov_smem<P, R, LY>(sJ, sJ + LY::jVol, sJ + 2 * LY::jVol, bx * LY::jX + by * LY::jY + bz, ax,
-                                         coef);
-            store_particle<R>(A, p, cell, mv);
+                        for (int a = 0; a < 3; ++a) ax[a].init(mv.f0[a], mv.f1[a]);
+                        if (ax[0].narrow && ax[1].narrow && ax[2].narrow) {
+                            tile_deposit<P, R, LY, true>(A, sJ, li, lj, lk, ax, wq);
+                        } else {
+                            wide = true;
+                            mine.set(li, lj, lk, mv.f0, mv.f1, wq);
+                        }
+                    }
+                }
+            }
+            const unsigned wm = __ballot_sync(0xffffffffu, wide);
+            if (wm == 0u) continue;
+            // queue the full-window moves: slots qn, qn+1, ... pull from the k-th wide lane
+            const int nw = __popc(wm);
+            const int take = min(nw, 32 - qn);
+            {
+                const int r = lane - qn;
+                const bool recv = r >= 0 && r < take;
+                const TileMove<R> got = mine.shfl(recv ? nth_set_bit(wm, r) : lane);
+                if (recv) qs = got;
+            }
+            qn += take;
+            if (qn == 32) {
+                qs.template deposit<P, LY>(A, sJ);
+                qn = nw - take;
+                if (qn > 0) {
+                    const bool recv = lane < qn;
+                    const TileMove<R> got = mine.shfl(recv ? nth_set_bit(wm, take + lane) : lane);
+                    if (recv) qs = got;
+                }
+            }
         }
     }
+    if (lane < qn) qs.template deposit<P, LY>(A, sJ);
     __syncthreads();
 
     // flush the tile's current into the global arrays (periodic fold)
