@@ -66,8 +66,10 @@ def measured_peaks():
 
 
 def kernel_source_hash():
+    """Hash of the sources the tile kernel is built from (its DRAM counters in
+    profiles/ hold only while this matches)."""
     h = hashlib.sha256()
-    for f in ("pic_kernels.cu", "pic_device.cuh"):
+    for f in ("pic_kernels.cu", "pic_device.cuh", "pic_step_common.cuh"):
         with open(os.path.join(ROOT, "paper_2101_12149_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -1,15 +1,19 @@
-// Particle and field kernels of libpic (sm_103a).
+// Particle kernels of libpic (sm_103a).
 //
-//  k_tile_step      fused gather + Boris + advance + Esirkepov for one tile
-//                   of cells per CTA: E/B of the tile and its halo staged in
-//                   shared memory, J accumulated in shared memory, one
-//                   vectorised atomic flush per tile (Sec. 3.1 fuses gather
-//                   and push; Sec. 3.4 discusses shared-memory buffers).
-//  k_gather_push    one particle per thread, fields read from global memory.
-//  k_deposit        one particle per thread, Esirkepov with global atomics
-//                   (the paper's GPU deposit, Sec. 3.4.1).
-//  k_yee_b/k_yee_e  Yee FDTD half-step of B / full step of E (Sec. 2.4).
-//  conversions, particle load/store, diagnostics.
+//  k_tile_step        fused gather + Boris + advance + Esirkepov for one tile
+//                     of cells per CTA: E/B of the tile and its halo staged in
+//                     shared memory, J accumulated in shared memory, one
+//                     vectorised atomic flush per tile (Sec. 3.1 fuses gather
+//                     and push; Sec. 3.4 discusses shared-memory buffers).
+//  k_tile_step_batch  the same tile body for (box, tile) items of a batch of
+//                     boxes, pulled from a queue by a persistent grid.
+//  k_outsiders        particles outside their tile (between sorts): global
+//                     gather and global atomics.
+//  k_gather_push      one particle per thread, fields read from global memory.
+//  k_deposit          one particle per thread, Esirkepov with global atomics
+//                     (the paper's GPU deposit, Sec. 3.4.1).
+// The Yee update, load/store, diagnostics and the moving window are in
+// pic_support.cu.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -687,331 +691,6 @@ __global__ void __launch_bounds__(kBlock) k_deposit(StepArgs<R> A) {
 }
 
 // ---------------------------------------------------------------------------
-// Yee FDTD
-// ---------------------------------------------------------------------------
-
-// B <- B - h curl E (forward differences: B sits half a cell above E), at cell c.
-template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>& Y, const int64_t c) {
-    const int k = int(c % Y.n[2]);
-    const int j = int((c / Y.n[2]) % Y.n[1]);
-    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
-    const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
-    const int64_t ip = c + (i + 1 == Y.n[0] ? -(int64_t)(Y.n[0] - 1) * sx : sx);
-    const int64_t jp = c + (j + 1 == Y.n[1] ? -(int64_t)(Y.n[1] - 1) * sy : sy);
-    const int64_t kp = c + (k + 1 == Y.n[2] ? -(int64_t)(Y.n[2] - 1) : 1);
-    const R ex = Y.E[0][c], ey = Y.E[1][c], ez = Y.E[2][c];
-    const bool top = Y.zopen && k + 1 == Y.n[2];  // z open: E beyond the end is zero
-    const R dEz_dy = (Y.E[2][jp] - ez) * Y.inv[1];
-    const R dEy_dz = ((top ? R(0) : Y.E[1][kp]) - ey) * Y.inv[2];
-    const R dEx_dz = ((top ? R(0) : Y.E[0][kp]) - ex) * Y.inv[2];
-    const R dEz_dx = (Y.E[2][ip] - ez) * Y.inv[0];
-    const R dEy_dx = (Y.E[1][ip] - ey) * Y.inv[0];
-    const R dEx_dy = (Y.E[0][jp] - ex) * Y.inv[1];
-    Y.B[0][c] -= Y.h * (dEz_dy - dEy_dz);
-    Y.B[1][c] -= Y.h * (dEx_dz - dEz_dx);
-    Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
-}
-
-// E <- E + dt (curl B - J) (backward differences), at cell c.
-template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>& Y, const int64_t c) {
-    const int k = int(c % Y.n[2]);
-    const int j = int((c / Y.n[2]) % Y.n[1]);
-    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
-    const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
-    const int64_t im = c - (i == 0 ? -(int64_t)(Y.n[0] - 1) * sx : sx);
-    const int64_t jm = c - (j == 0 ? -(int64_t)(Y.n[1] - 1) * sy : sy);
-    const int64_t km = c - (k == 0 ? -(int64_t)(Y.n[2] - 1) : 1);
-    const R bx = Y.B[0][c], by = Y.B[1][c], bz = Y.B[2][c];
-    const bool bottom = Y.zopen && k == 0;  // z open: B below the start is zero
-    const R dBz_dy = (bz - Y.B[2][jm]) * Y.inv[1];
-    const R dBy_dz = (by - (bottom ? R(0) : Y.B[1][km])) * Y.inv[2];
-    const R dBx_dz = (bx - (bottom ? R(0) : Y.B[0][km])) * Y.inv[2];
-    const R dBz_dx = (bz - Y.B[2][im]) * Y.inv[0];
-    const R dBy_dx = (by - Y.B[1][im]) * Y.inv[0];
-    const R dBx_dy = (bx - Y.B[0][jm]) * Y.inv[1];
-    Y.E[0][c] += Y.h * ((dBz_dy - dBy_dz) - Y.J[0][c]);
-    Y.E[1][c] += Y.h * ((dBx_dz - dBz_dx) - Y.J[1][c]);
-    Y.E[2][c] += Y.h * ((dBy_dx - dBx_dy) - Y.J[2][c]);
-}
-
-template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (Y.step && c == 0) *Y.step += 1;
-    if (c < C) yee_b_at(Y, c);
-}
-
-template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) yee_e_at(Y, c);
-}
-
-// Batch of boxes: block b updates cells [blocks[b].y, blocks[b].y + blocks[b].z)
-// of box blocks[b].x (a block never spans two boxes).  `step`, when non-null,
-// is advanced once.
-template <typename R>
-__global__ void __launch_bounds__(kBlock)
-    k_yee_b_batch(const YeeArgs<R>* __restrict__ boxes, const int4* __restrict__ blocks, long long* step) {
-    const int4 bk = blocks[blockIdx.x];
-    if (step && blockIdx.x == 0 && threadIdx.x == 0) *step += 1;
-    if (int(threadIdx.x) < bk.z) yee_b_at(boxes[bk.x], int64_t(bk.y) + threadIdx.x);
-}
-
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_yee_e_batch(const YeeArgs<R>* __restrict__ boxes, const int4* __restrict__ blocks) {
-    const int4 bk = blocks[blockIdx.x];
-    if (int(threadIdx.x) < bk.z) yee_e_at(boxes[bk.x], int64_t(bk.y) + threadIdx.x);
-}
-
-template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
-    YeeArgs<R> Y;
-    for (int d = 0; d < 3; ++d) {
-        Y.E[d] = static_cast<R*>(c->F[d]);
-        Y.B[d] = static_cast<R*>(c->F[3 + d]);
-        Y.J[d] = static_cast<const R*>(c->F[6 + d]);
-        Y.n[d] = c->g.n[d];
-        Y.inv[d] = R(1.0 / c->g.d[d]);
-    }
-    Y.h = R(h);
-    Y.step = nullptr;
-    Y.zopen = c->g.zopen;
-    return Y;
-}
-
-// ---------------------------------------------------------------------------
-// particle load / store, field conversion, diagnostics
-// ---------------------------------------------------------------------------
-template <typename R>
-__global__ void k_load(StepArgs<R> A, const double* x, const double* y, const double* z, const double* ux,
-                       const double* uy, const double* uz, const double* w, int* id, unsigned long long* wmax) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= A.np) return;
-    const Geom& g = A.g;
-    const double xs[3] = {x[p], y[p], z[p]};
-    const double us[3] = {ux[p], uy[p], uz[p]};
-    bool ok = isfinite(w[p]);
-    int cell[3];
-    bool gone = false;  // z open: a particle loaded outside [0, Lz) is dropped by the first sort
-    for (int a = 0; a < 3; ++a) {
-        ok = ok && isfinite(xs[a]) && isfinite(us[a]);
-        double xv = isfinite(xs[a]) ? xs[a] : 0.0;
-        if (a == 2 && g.zopen && !(xv >= 0.0 && xv < g.L[2])) gone = true, xv = 0.0;
-        xv = fmod(xv, g.L[a]);
-        xv = wrap_pos(xv, g.L[a]);
-        double f;
-        split_pos(xv, g.d[a], g.n[a], cell[a], f);
-        if (sizeof(R) == 8) {
-            A.pa[a][p] = R(xv);
-        } else {
-            float ff = float(f);
-            if (ff >= 1.0f) {  // rounds up to the next cell
-                ff = 0.0f;
-                cell[a] = wrap_once(cell[a] + 1, g.n[a]);
-            }
-            A.pa[a][p] = R(ff);
-        }
-        A.pa[3 + a][p] = R(us[a]);
-    }
-    A.pa[6][p] = R(w[p]);
-    A.key[p] = gone ? dead_key(g) : key_of(g, cell[0], cell[1], cell[2]);
-    id[p] = int(p);
-    // largest |w|: non-negative doubles order like their bit patterns
-    if (isfinite(w[p])) atomicMax(wmax, (unsigned long long)__double_as_longlong(fabs(double(R(w[p])))));
-    if (!ok) raise_error(A.err, ERRBIT_PARTICLE);
-}
-
-template <typename R>
-__global__ void k_store(StepArgs<R> A, double* x, double* y, double* z, double* ux, double* uy, double* uz,
-                        double* w, const int* idsrc, int32_t* id) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= A.np) return;
-    const Geom& g = A.g;
-    double* xs[3] = {x, y, z};
-    double* us[3] = {ux, uy, uz};
-    int cell[3];
-    if (sizeof(R) == 4) cell_of(g, A.key[p], cell[0], cell[1], cell[2]);
-    for (int a = 0; a < 3; ++a) {
-        if (xs[a]) {
-            double v = sizeof(R) == 8 ? double(A.pa[a][p]) : (double(cell[a]) + double(A.pa[a][p])) * g.d[a];
-            xs[a][p] = wrap_pos(v, g.L[a]);
-        }
-        if (us[a]) us[a][p] = double(A.pa[3 + a][p]);
-    }
-    if (w) w[p] = double(A.pa[6][p]);
-    if (id) id[p] = idsrc[p];
-}
-
-template <typename S, typename D> __global__ void k_convert(const S* src, D* dst, int64_t n) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = D(src[i]);
-}
-
-// out[0] += sum |F|^2 / 2 over Ex..Bz (times dV on the host), out[1] kinetic,
-// out[2] charge, out[3] max |div B| (as a bit pattern, max via atomicMax).
-template <typename R>
-__global__ void k_diag_fields(const R* const* F, int64_t C, double* out) {
-    double s = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < C; i += (int64_t)gridDim.x * blockDim.x)
-        for (int c = 0; c < 6; ++c) {
-            const double v = double(F[c][i]);
-            s += v * v;
-        }
-    for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __shared__ double red[kBlock / 32];
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(out, 0.5 * t);
-    }
-}
-
-template <typename R>
-__global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out) {
-    double ke = 0.0, ch = 0.0;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.np;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const double u0 = A.pa[3][p], u1 = A.pa[4][p], u2 = A.pa[5][p], w = A.pa[6][p];
-        ke += w * m * (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0);
-        ch += q * w;
-    }
-    for (int o = 16; o; o >>= 1) {
-        ke += __shfl_down_sync(0xffffffffu, ke, o);
-        ch += __shfl_down_sync(0xffffffffu, ch, o);
-    }
-    __shared__ double red[2][kBlock / 32];
-    if ((threadIdx.x & 31) == 0) {
-        red[0][threadIdx.x >> 5] = ke;
-        red[1][threadIdx.x >> 5] = ch;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[0][w], b += red[1][w];
-        atomicAdd(out + 1, a);
-        atomicAdd(out + 2, b);
-    }
-}
-
-template <typename R>
-__global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int ny, int nz, double dx, double dy,
-                            double dz, int zopen, unsigned long long* out) {
-    const int64_t C = (int64_t)nx * ny * nz;
-    double mx = 0.0;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        const int k = int(c % nz), j = int((c / nz) % ny), i = int(c / ((int64_t)ny * nz));
-        const int64_t ip = ((int64_t)wrap_once(i + 1, nx) * ny + j) * nz + k;
-        const int64_t jp = ((int64_t)i * ny + wrap_once(j + 1, ny)) * nz + k;
-        const int64_t kp = ((int64_t)i * ny + j) * nz + wrap_once(k + 1, nz);
-        const double bz_up = zopen && k + 1 == nz ? 0.0 : double(Bz[kp]);  // z open: zero beyond the end
-        const double v = (double(Bx[ip]) - double(Bx[c])) / dx + (double(By[jp]) - double(By[c])) / dy +
-                         (bz_up - double(Bz[c])) / dz;
-        mx = fmax(mx, fabs(v));
-    }
-    for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
-}
-
-// ---------------------------------------------------------------------------
-// moving window (z open)
-// ---------------------------------------------------------------------------
-// F(i,j,k) <- F(i,j,k+1), F(i,j,nz-1) <- 0 in place: one warp per z column
-// walks it in chunks of 32 (each element is read before it is overwritten:
-// in the same chunk by the warp's load, or by the previous chunk's).
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_shift_fields(R* F0, int64_t C, int nz, int64_t columns) {
-    const int64_t col = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (col >= columns) return;
-    R* f = F0 + (int64_t)blockIdx.y * C + col * nz;
-    for (int k0 = 0; k0 < nz; k0 += 32) {
-        const int k = k0 + lane;
-        const R v = k + 1 < nz ? f[k + 1] : R(0);
-        __syncwarp();
-        if (k < nz) f[k] = v;
-        __syncwarp();
-    }
-}
-
-// Particles move down one cell along z; those below z = 0 get the removed key.
-template <typename R> __global__ void __launch_bounds__(kBlock) k_shift_particles(StepArgs<R> A) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= A.np) return;
-    const Geom& g = A.g;
-    const int dead = dead_key(g);
-    const int key = A.key[p];
-    if (key == dead) return;
-    int i, j, k;
-    if (sizeof(R) == 8) {
-        const double z = double(A.pa[2][p]) - g.d[2];
-        A.pa[2][p] = R(z);
-        if (!(z >= 0.0)) {
-            A.key[p] = dead;
-            return;
-        }
-        double f;
-        split_pos(double(A.pa[0][p]), g.d[0], g.n[0], i, f);
-        split_pos(double(A.pa[1][p]), g.d[1], g.n[1], j, f);
-        split_pos(z, g.d[2], g.n[2], k, f);
-    } else {
-        cell_of(g, key, i, j, k);
-        k -= 1;  // the in-cell offset is unchanged
-        if (k < 0) {
-            A.key[p] = dead;
-            return;
-        }
-    }
-    A.key[p] = key_of(g, i, j, k);
-}
-
-struct InjectArgs {
-    int64_t first;     // first slot (particle index) written
-    int64_t first_id;  // id of slot `first`
-    int ppc;
-    double n0, ramp_start, ramp_length;
-    double zlab0;      // lab-frame z of the front slab's lower face
-};
-
-// The front slab k = nz-1: in each cell particles m = 0..ppc-1 at in-cell
-// offset (m + 1/2)/ppc on every axis, at rest, weight density(lab z) dV / ppc
-// with the density rising linearly from 0 at ramp_start over ramp_length to
-// n0; where the density is zero the slot gets the removed key.  Slot and id
-// follow (i ny + j) ppc + m.
-template <typename R> __global__ void __launch_bounds__(kBlock) k_inject(StepArgs<R> A, InjectArgs I, int* id) {
-    const Geom& g = A.g;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t total = (int64_t)g.n[0] * g.n[1] * I.ppc;
-    if (t >= total) return;
-    const int m = int(t % I.ppc);
-    const int64_t ij = t / I.ppc;
-    const int j = int(ij % g.n[1]), i = int(ij / g.n[1]);
-    const int k = g.n[2] - 1;
-    const double off = (m + 0.5) / I.ppc;
-    const double zl = I.zlab0 + off * g.d[2];
-    double dens;
-    if (I.ramp_length > 0.0) dens = I.n0 * fmin(fmax((zl - I.ramp_start) / I.ramp_length, 0.0), 1.0);
-    else dens = zl >= I.ramp_start ? I.n0 : 0.0;
-    const int64_t p = I.first + t;
-    if (sizeof(R) == 8) {
-        A.pa[0][p] = R((i + off) * g.d[0]);
-        A.pa[1][p] = R((j + off) * g.d[1]);
-        A.pa[2][p] = R((k + off) * g.d[2]);
-    } else {
-        A.pa[0][p] = R(off);
-        A.pa[1][p] = R(off);
-        A.pa[2][p] = R(off);
-    }
-    A.pa[3][p] = R(0);
-    A.pa[4][p] = R(0);
-    A.pa[5][p] = R(0);
-    A.pa[6][p] = R(dens * g.d[0] * g.d[1] * g.d[2] / I.ppc);
-    A.key[p] = dens > 0.0 ? key_of(g, i, j, k) : dead_key(g);
-    id[p] = int(I.first_id + t);
-}
-
-// ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n) { return unsigned((n + kBlock - 1) / kBlock); }
@@ -1102,38 +781,6 @@ cudaError_t launch_tile_step_batch(int prec, const BatchTileLaunch& L, cudaStrea
     }
 }
 
-template <typename R>
-cudaError_t yee_batch_impl(const void* yb, const void* ye, const int4* blocks, int nblocks, long long* step,
-                           cudaStream_t s) {
-    if (nblocks <= 0) return cudaSuccess;
-    const auto* B = static_cast<const YeeArgs<R>*>(yb);
-    const auto* E = static_cast<const YeeArgs<R>*>(ye);
-    k_yee_b_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(B, blocks, nullptr);
-    k_yee_e_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(E, blocks);
-    k_yee_b_batch<R><<<unsigned(nblocks), kBlock, 0, s>>>(B, blocks, step);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_yee_batch(int prec, const void* yb, const void* ye, const int4* blocks, int nblocks,
-                             long long* step, cudaStream_t s) {
-    return prec == PIC_FP64 ? yee_batch_impl<double>(yb, ye, blocks, nblocks, step, s)
-                            : yee_batch_impl<float>(yb, ye, blocks, nblocks, step, s);
-}
-
-__global__ void k_rekey(int* key, int64_t n, Geom from, Geom to) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    int i, j, k;
-    cell_of(from, key[p], i, j, k);
-    key[p] = key_of(to, i, j, k);
-}
-
-cudaError_t launch_rekey(int* key, int64_t n, const Geom& from, const Geom& to, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_rekey<<<blocks_for(n), kBlock, 0, s>>>(key, n, from, to);
-    return cudaGetLastError();
-}
-
 cudaError_t configure_batch_kernels() {
     auto set = [](auto kernel, size_t bytes) {
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
@@ -1191,138 +838,6 @@ cudaError_t launch_deposit_global(pic_ctx* c) {
     case 2: return dep_impl<float, 2>(c);
     default: return dep_impl<float, 3>(c);
     }
-}
-
-cudaError_t launch_yee_b(pic_ctx* c, double h) {
-    if (c->prec == PIC_FP64) {
-        auto Y = make_yee<double>(c, h);
-        k_yee_b<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-    } else {
-        auto Y = make_yee<float>(c, h);
-        k_yee_b<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_yee_e(pic_ctx* c) {
-    if (c->prec == PIC_FP64) {
-        auto Y = make_yee<double>(c, c->dt);
-        k_yee_e<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-    } else {
-        auto Y = make_yee<float>(c, c->dt);
-        k_yee_e<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-    }
-    return cudaGetLastError();
-}
-
-__global__ void k_step_counter(long long* s) { *s += 1; }
-
-cudaError_t launch_step_counter(pic_ctx* c) {
-    k_step_counter<<<1, 1, 0, c->stream>>>(c->d_step);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n) {
-    if (n == 0) return cudaSuccess;
-    if (c->prec == PIC_FP64) {
-        auto A = make_args<double>(c);
-        k_load<double><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                               src[6], c->P[c->cur].id,
-                                                               reinterpret_cast<unsigned long long*>(c->err + 6));
-    } else {
-        auto A = make_args<float>(c);
-        k_load<float><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                              src[6], c->P[c->cur].id,
-                                                              reinterpret_cast<unsigned long long*>(c->err + 6));
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id) {
-    if (c->np == 0) return cudaSuccess;
-    if (c->prec == PIC_FP64) {
-        auto A = make_args<double>(c);
-        k_store<double><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
-                                                                    dst[5], dst[6], c->P[c->cur].id, id);
-    } else {
-        auto A = make_args<float>(c);
-        k_store<float><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
-                                                                   dst[5], dst[6], c->P[c->cur].id, id);
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst) {
-    if (c->prec == PIC_FP64)
-        return cudaMemcpyAsync(dst, c->F[which], c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    k_convert<float, double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(static_cast<const float*>(c->F[which]),
-                                                                         dst, c->g.C);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src) {
-    if (c->prec == PIC_FP64)
-        return cudaMemcpyAsync(c->F[which], src, c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    k_convert<double, float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(src, static_cast<float*>(c->F[which]),
-                                                                         c->g.C);
-    return cudaGetLastError();
-}
-
-template <typename R> cudaError_t diag_impl(pic_ctx* c, double* d_out) {
-    // F pointer table lives in the scratch after the four outputs
-    const R** tab = reinterpret_cast<const R**>(d_out + 8);
-    const R* host_tab[6];
-    for (int i = 0; i < 6; ++i) host_tab[i] = static_cast<const R*>(c->F[i]);
-    cudaError_t e = cudaMemcpyAsync(tab, host_tab, sizeof(host_tab), cudaMemcpyHostToDevice, c->stream);
-    if (e != cudaSuccess) return e;
-    const unsigned nb = 152 * 4;
-    k_diag_fields<R><<<nb, kBlock, 0, c->stream>>>(tab, c->g.C, d_out);
-    if (c->np > 0) {
-        auto A = make_args<R>(c);
-        k_diag_particles<R><<<nb, kBlock, 0, c->stream>>>(A, c->m, c->q, d_out);
-    }
-    k_diag_divb<R><<<nb, kBlock, 0, c->stream>>>(static_cast<const R*>(c->F[3]), static_cast<const R*>(c->F[4]),
-                                                 static_cast<const R*>(c->F[5]), c->g.n[0], c->g.n[1], c->g.n[2],
-                                                 c->g.d[0], c->g.d[1], c->g.d[2], c->g.zopen,
-                                                 reinterpret_cast<unsigned long long*>(d_out + 3));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_diagnostics(pic_ctx* c, double* d_out) {
-    return c->prec == PIC_FP64 ? diag_impl<double>(c, d_out) : diag_impl<float>(c, d_out);
-}
-
-template <typename R> cudaError_t window_shift_impl(pic_ctx* c) {
-    const int64_t columns = int64_t(c->g.n[0]) * c->g.n[1];
-    const dim3 grid(unsigned((columns * 32 + kBlock - 1) / kBlock), 9);
-    k_shift_fields<R><<<grid, kBlock, 0, c->stream>>>(static_cast<R*>(c->F[0]), c->g.C, c->g.n[2], columns);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || c->np == 0) return e;
-    k_shift_particles<R><<<blocks_for(c->np), kBlock, 0, c->stream>>>(make_args<R>(c));
-    return cudaGetLastError();
-}
-
-cudaError_t launch_window_shift(pic_ctx* c) {
-    return c->prec == PIC_FP64 ? window_shift_impl<double>(c) : window_shift_impl<float>(c);
-}
-
-template <typename R> cudaError_t inject_impl(pic_ctx* c) {
-    InjectArgs I;
-    I.first = c->np;
-    I.first_id = c->next_id;
-    I.ppc = c->inj_ppc;
-    I.n0 = c->inj_n0;
-    I.ramp_start = c->inj_ramp_start;
-    I.ramp_length = c->inj_ramp_length;
-    I.zlab0 = double(c->shifts + c->g.n[2] - 1) * c->g.d[2];
-    const int64_t total = int64_t(c->g.n[0]) * c->g.n[1] * c->inj_ppc;
-    if (total == 0) return cudaSuccess;
-    k_inject<R><<<blocks_for(total), kBlock, 0, c->stream>>>(make_args<R>(c), I, c->P[c->cur].id);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_inject(pic_ctx* c) {
-    return c->prec == PIC_FP64 ? inject_impl<double>(c) : inject_impl<float>(c);
 }
 
 }  // namespace pic

@@ -1,0 +1,129 @@
+"""Full-size checks in the launch configuration bench.py times.
+
+256^3 x 8 ppc, order 3 (uniform-plasma workload): two steps on the GPU
+from the full initial state; the oracle reruns a 44^3 periodic sub-box cut
+from the same initial particles.  Within one step a value depends on the
+state within about 6.5 cells (a field through the Yee stencil, 1 cell, on the
+current, whose order-3 window reaches particles 3 cells away, whose push
+gathers fields 2.5 cells around them); from the field-free start the first
+step reaches only the particles' 4 cells.  So after two steps the central
+16^3 cells and the particles that started there are unaffected by the
+sub-box's 14-cell margin: they must match the full run (the second step
+gathers the fields the first step made).  FP64 to 1e-12, FP32-mixed with
+its error stated.
+
+64^3 x 4 ppc, order 2 (differentiation workload): the FP64 GPU adjoint
+against central differences of the GPU's own FP64 forward run, and the
+FP32-mixed adjoint against the FP64 one (see the test's docstring for the
+horizon)."""
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_l2
+from oracle import Oracle
+from paper_2101_12149_gb300 import inputs, pic
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+W = inputs.WORKLOADS["uniform_256"]
+S, M = 16, 14           # interior and margin of the sub-box (cells)
+C0 = 100                # interior starts at cell C0 on every axis
+STEPS = 2
+
+
+def _subbox(parts, n):
+    lo, hi = C0 - M, C0 + S + M
+    cell = [np.floor(parts[k]).astype(np.int64) for k in ("x", "y", "z")]
+    sel = (cell[0] >= lo) & (cell[0] < hi) & (cell[1] >= lo) & (cell[1] < hi) & (cell[2] >= lo) & (cell[2] < hi)
+    ids = np.nonzero(sel)[0]
+    sub = {k: np.ascontiguousarray(v[ids]) for k, v in parts.items()}
+    for k in ("x", "y", "z"):
+        sub[k] = sub[k] - lo
+    inner = ((cell[0][ids] >= C0) & (cell[0][ids] < C0 + S) & (cell[1][ids] >= C0) & (cell[1][ids] < C0 + S) &
+             (cell[2][ids] >= C0) & (cell[2][ids] < C0 + S))
+    return sub, ids, inner
+
+
+@pytest.mark.parametrize("precision", [pic.FP32_MIXED, pic.FP64])
+def test_uniform_256_local_cone_against_oracle(precision):
+    import torch
+    n = W["n"]
+    parts = inputs.workload_particles("uniform_256")
+    stream = torch.cuda.Stream()
+    with pic.Context(n, cfl=W["cfl"], order=W["order"], precision=precision, stream=stream) as c:
+        c.load_particles(-1.0, 1.0, parts)
+        c.step(STEPS)
+        G = np.stack([c.get_field(i)[C0:C0 + S, C0:C0 + S, C0:C0 + S].copy() for i in range(9)])
+        q = c.get_particles()
+    sub, ids, inner = _subbox(parts, n)
+    O = Oracle()
+    L = S + 2 * M
+    g = O.grid((L, L, L))
+    dt = inputs.dt_from_cfl((1, 1, 1), W["cfl"])
+    F = np.zeros((9, L, L, L))
+    for s in range(STEPS):
+        O.pic_step(g, W["order"], dt, -1.0, 1.0, sub, F, 0.0, 0.0, s * dt)
+    Fi = F[:, M:M + S, M:M + S, M:M + S]
+    # particles that started in the interior, by id (positions back in full-grid coordinates)
+    slot = np.empty(q["id"].size, dtype=np.int64)
+    slot[q["id"]] = np.arange(q["id"].size)
+    want = ids[inner]
+    got = {k: q[k][slot[want]] for k in ("x", "y", "z", "ux", "uy", "uz")}
+    ref = {k: sub[k][inner] for k in ("x", "y", "z", "ux", "uy", "uz")}
+    for k in ("x", "y", "z"):
+        ref[k] = ref[k] + (C0 - M)
+    pos = np.concatenate([got[k] - ref[k] for k in ("x", "y", "z")])
+    mom = np.concatenate([got[k] - ref[k] for k in ("ux", "uy", "uz")])
+    e = {"EB": rel_l2(G[:6], Fi[:6]), "J": rel_l2(G[6:], Fi[6:]),
+         "pos": float(np.linalg.norm(pos) / np.linalg.norm(np.concatenate([ref[k] for k in ("x", "y", "z")]))),
+         "mom": float(np.linalg.norm(mom) / np.linalg.norm(np.concatenate([ref[k] for k in ("ux", "uy", "uz")])))}
+    print(f"256^3 local cone, precision {precision}, {want.size} particles:", e)
+    assert want.size > 30000
+    if precision == pic.FP64:
+        assert max(e.values()) < 1e-12, e
+    else:
+        # measured on GB300: EB 1.9e-6, J 3.1e-6, pos 2.2e-10, mom 8.7e-8 (fields two steps from zero)
+        assert e["EB"] < 1e-5 and e["J"] < 2e-5 and e["pos"] < 1e-8 and e["mom"] < 1e-6, e
+
+
+def test_adjoint_64_full_size_against_central_differences():
+    """The differentiation workload at full size (64^3, 4 ppc, order 2,
+    checkpoints every 20).  Over 50 steps the FP64 adjoint meets central
+    differences with h = 1e-4 to 1e-6.  Over the full 200 steps the discrete
+    map is curved enough that the h = 1e-4 difference quotient is itself a
+    few per cent off (the map is smooth only piecewise, and the drive has
+    grown the fields by then); there the quotient must converge towards the
+    adjoint as h shrinks (measured on GB300: 4.5e-2, 1.7e-3, 1.5e-4 at
+    h = 1e-4, 1e-5, 1e-6).  The FP32-mixed adjoint is stated against FP64."""
+    w = inputs.WORKLOADS["adjoint_64"]
+    parts = inputs.workload_particles("adjoint_64")
+    A = inputs.drive_amplitude(w["seed"])
+    kd = 2 * np.pi / w["n"][0]
+
+    def run(prec, amp, steps, adjoint=False):
+        with pic.Context(w["n"], cfl=w["cfl"], order=w["order"], precision=prec) as c:
+            c.load_particles(-1.0, 1.0, parts)
+            c.set_external_drive(amp, kd)
+            if adjoint:
+                return c.step_adjoint(steps, 20)
+            c.step(steps)
+            return c.diagnostics()["field_energy"]
+
+    def fd(steps, h):
+        return (run(pic.FP64, A + h, steps) - run(pic.FP64, A - h, steps)) / (2 * h)
+
+    _, dA50, _ = run(pic.FP64, A, 50, True)
+    f50 = fd(50, 1e-4)
+    print(f"adjoint_64, 50 steps: dL/dA {dA50:.9e} central difference {f50:.9e} rel {abs(f50 - dA50) / abs(f50):.2e}")
+    assert abs(f50 - dA50) < 1e-6 * abs(f50)
+
+    loss, dA, du = run(pic.FP64, A, w["steps"], True)
+    err = {h: abs(fd(w["steps"], h) - dA) / abs(dA) for h in (1e-5, 1e-6)}
+    print(f"adjoint_64, 200 steps: dL/dA {dA:.9e}, difference quotient error {err}")
+    assert err[1e-6] < 1e-3 and err[1e-6] < err[1e-5]
+
+    _, dA32, du32 = run(pic.FP32_MIXED, A, w["steps"], True)
+    rel_A = abs(dA32 - dA) / abs(dA)
+    rel_u = float(np.linalg.norm(du32 - du) / np.linalg.norm(du))
+    print(f"adjoint_64 FP32-mixed vs FP64, 200 steps: dL/dA {rel_A:.2e}, dL/du {rel_u:.2e}")
+    assert rel_A < 1e-3 and rel_u < 1e-2
