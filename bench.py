@@ -182,20 +182,59 @@ def cpu_baseline(seconds_target=15.0):
                       f"{el:.1f} s, 1 host core"}
 
 
+def dist_env():
+    """(rank, world size, local rank) from the launcher's environment."""
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(t, dist, device):
+    """The whole job's time: the slowest rank's (every rank gets it)."""
+    if dist is None:
+        return t
+    import torch
+    tt = torch.tensor([float(t)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_throughput(world, units_per_rank, steps, t):
+    """Units all ranks processed (independent replicas, same work each) per second of the job."""
+    return world * units_per_rank * steps / t
+
+
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    """The reference arm: the FP64 CPU oracle as it stands, one host core, on a
+    bounded sample of the same workload (a 32^3 box of the recipe, 262,144
+    particles); W untimed steps, then K timed steps.  Rank 0 only."""
+    rank, _, _ = dist_env()
     if rank != 0:
         return
     from __graft_entry__ import build
     build()
-    base = cpu_baseline(seconds_target=max(5.0, 2.0 * (args.steps + args.warmup)))
-    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256^3", "ppc": 8, "order": 3,
-                       "sample": "32^3 box of the same recipe (CPU oracle)"},
-            "cpu_baseline": base,
-            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    from oracle import Oracle
+    from paper_2101_12149_gb300 import inputs
+    w = inputs.WORKLOADS[WORKLOAD]
+    n = (32, 32, 32)
+    parts = inputs.uniform_plasma(w["seed"], n, w["ppc"], sigma_u=w["sigma_u"], density=w["density"])
+    O = Oracle()
+    g = O.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+    F = np.zeros((9,) + n)
+    for s in range(args.warmup):
+        O.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F, 0.0, 0.0, s * dt)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        O.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F, 0.0, 0.0, (args.warmup + s) * dt)
+    t = time.perf_counter() - t0
+    N = parts["x"].size
+    value = N * args.steps / t
+    sample = f"oracle on a 32^3 box of the same recipe ({N} particles, order 3, 8 ppc), {args.steps} timed steps"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "256^3", "ppc": 8, "order": 3, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
@@ -321,9 +360,7 @@ def main():
         return
 
     import torch
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -372,12 +409,10 @@ def main():
     launches = ctx.launch_count() - l0
     timings = ctx.get_timing()
     ctx.set_timing(False)
+    t = max_over_ranks(t, dist, f"cuda:{local}")
     if dist:
-        tt = torch.tensor([t], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
         dist.barrier()
-    value = world * N * args.steps / t
+    value = job_throughput(world, N, args.steps, t)
     ms_step = 1e3 * t / args.steps
     ctx.close()
 
@@ -427,10 +462,12 @@ def main():
         torch.cuda.empty_cache()
         ms64, n64 = tm64.get("k_tile_step", (0.0, 0))
         fl64 = N * flops_per_particle(order) / (ms64 / max(n64, 1) / 1e3) / 1e12 if n64 else None
-        line["fp64"] = {"value": world * N * args.fp64_steps / t64, "ms_per_step": 1e3 * t64 / args.fp64_steps,
+        t64 = max_over_ranks(t64, dist, f"cuda:{local}")
+        line["fp64"] = {"value": job_throughput(world, N, args.fp64_steps, t64),
+                        "ms_per_step": 1e3 * t64 / args.fp64_steps,
                         "steps": args.fp64_steps, "tile_kernel_tflops": fl64,
                         "tile_kernel_frac_of_fp64_peak": fl64 / FP64_PEAK_TFLOPS if fl64 else None,
-                        "fp32_mixed_speedup": value / (world * N * args.fp64_steps / t64)}
+                        "fp32_mixed_speedup": value / job_throughput(world, N, args.fp64_steps, t64)}
         # ---- stated error of FP32-mixed ----------------------------------
         if rank == 0:
             line["error"] = field_error_statement(torch)
@@ -448,7 +485,8 @@ def main():
         ctx2.close()
         h2d = 7 * 8 * N
         d2h = e2e_steps * 4 * 8 + ex.nbytes
-        line["e2e"] = {"value": world * N * e2e_steps / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(t_e2e, dist, f"cuda:{local}")
+        line["e2e"] = {"value": job_throughput(world, N, e2e_steps, t_e2e), "unit": UNIT,
                        "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                        "what": "context creation + pic_load_particles from pinned host FP64 arrays + "
                                f"{e2e_steps} x (pic_step + pic_diagnostics read-back) + E_x field read-back"}
