@@ -316,6 +316,65 @@ def ensemble_statement(torch, stream, steps=20):
     return res
 
 
+def wakefield_statement(torch, steps_cmp=50, steps_fp32=150):
+    """The laser-wakefield-shaped run (128 x 128 x 1024, window moving at c,
+    laser a0 = 2, ramped plasma at 2 ppc, order 2): FP64 and FP32-mixed for
+    `steps_cmp` steps from the same start, then their field difference
+    (relative L2 of E and B) and each run's energy drift (field + kinetic,
+    relative to the start); FP32-mixed then runs `steps_fp32` more steps,
+    timed with CUDA events on its stream."""
+    from paper_2101_12149_gb300 import inputs, pic
+    cfg = inputs.WAKEFIELD
+    parts = inputs.wakefield_particles(cfg)
+    F0 = inputs.laser_fields(cfg)
+    n0 = inputs.wakefield_plasma_density(cfg)
+    C = int(np.prod(cfg["n"]))
+    res = {"grid": "128x128x1024", "particles_start": int(parts["x"].size), "order": cfg["order"],
+           "ppc": cfg["ppc"], "a0": cfg["a0"]}
+    s = torch.cuda.Stream()
+    fields = {}
+    for prec, name in ((pic.FP64, "fp64"), (pic.FP32_MIXED, "fp32_mixed")):
+        with pic.Context(cfg["n"], cfl=cfg["cfl"], order=cfg["order"], precision=prec, window_speed=cfg["speed"],
+                         stream=s) as c:
+            c.set_window_plasma(cfg["ppc"], n0, cfg["ramp_start"], cfg["ramp_length"])
+            c.set_fields(F0)
+            c.load_particles(-1.0, 1.0, parts)
+            d0 = c.diagnostics()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(s)
+            c.step(steps_cmp)
+            e1.record(s)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            d1 = c.diagnostics()
+            fields[name] = np.stack([c.get_field(i) for i in range(6)])
+            r = {"ms_per_step": 1e3 * t / steps_cmp, "steps": steps_cmp,
+                 "particle_steps_per_s": 0.5 * (parts["x"].size + c.num_particles()) * steps_cmp / t,
+                 "cell_steps_per_s": C * steps_cmp / t, "shifts": c.window()["shifts"],
+                 "particles_end": c.num_particles(),
+                 "energy_drift": (d1["field_energy"] + d1["kinetic_energy"]) / (d0["field_energy"] + d0["kinetic_energy"]) - 1.0}
+            if prec == pic.FP32_MIXED and steps_fp32 > 0:
+                np0 = c.num_particles()
+                torch.cuda.synchronize()
+                e0.record(s)
+                c.step(steps_fp32)
+                e1.record(s)
+                torch.cuda.synchronize()
+                t2 = e0.elapsed_time(e1) / 1e3
+                r["timed_steps"] = steps_fp32
+                r["ms_per_step"] = 1e3 * t2 / steps_fp32
+                r["particle_steps_per_s"] = 0.5 * (np0 + c.num_particles()) * steps_fp32 / t2
+                r["cell_steps_per_s"] = C * steps_fp32 / t2
+                r["shifts_end"] = c.window()["shifts"]
+            res[name] = r
+    res["fp32_field_rel_l2_vs_fp64"] = float(np.linalg.norm(fields["fp32_mixed"] - fields["fp64"]) /
+                                             np.linalg.norm(fields["fp64"]))
+    res["compared_after_steps"] = steps_cmp
+    return res
+
+
 def adjoint_statement(torch):
     """The differentiation workload: 64^3, 4 ppc, order 2, drive A from seed 4,
     200 steps with checkpoints every 20; forward + checkpointed reverse timed
@@ -493,6 +552,7 @@ def main():
         if rank == 0:
             line["ensemble"] = ensemble_statement(torch, stream)
             line["adjoint"] = adjoint_statement(torch)
+            line["wakefield"] = wakefield_statement(torch)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline()
 
