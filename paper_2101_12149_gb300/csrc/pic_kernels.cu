@@ -142,23 +142,24 @@ __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict
 //
 // Every Esirkepov contribution obeys |v| <= |coef|: the cumulative sum of dS
 // is a difference of two cumulative shape distributions, bounded by the move
-// (< 1 cell), and Q <= 1.  With vscale = 2^30 / max|coef|, x = rn(v vscale)
-// fits in 31 bits; it is split as x = hi 2^15 + lo (hi = x rounded to a
-// multiple of 2^15, |lo| <= 2^14) and the halves go to two int32 arrays by
-// native shared-memory integer reductions.  Integer sums are exact and
-// independent of order; with at most 65535 particles per tile neither sum
-// can overflow (65535 * 2^15 < 2^31).  The flush rebuilds hi 2^15 + lo.
-__device__ __forceinline__ void red_fixed(int* lo, int* hi, float v, float vscale) {
-    const int x = __float2int_rn(v * vscale);
-    const int h = (x + (1 << 14)) >> 15;
-    const int l = x - (h << 15);
-    atomicAdd(lo, l);
-    atomicAdd(hi, h);
+// (< 1 cell), and Q <= 1.  vscale is the largest power of two with
+// vscale max|coef| <= 2^30, so x = rn(v vscale) fits in 31 bits, and because
+// scaling by a power of two is exact, vscale is folded into the particle's
+// coefficient.  x is split as x = hi 2^15 + lo (hi = x >> 15, lo = x & 0x7fff)
+// and the halves go to two int32 arrays by native shared-memory integer
+// reductions.  Integer sums are exact and independent of order; with at most
+// 65535 particles per tile neither sum can overflow (65535 * 2^15 and
+// 65535 * (2^15 - 1) are below 2^31).  The flush rebuilds hi 2^15 + lo.
+__device__ __forceinline__ void red_fixed(int* lo, int* hi, float v_scaled) {
+    const int x = __float2int_rn(v_scaled);
+    atomicAdd(lo, x & 0x7fff);
+    atomicAdd(hi, x >> 15);
 }
 
 template <int P, class LY, int NC = P + 1, int NT = P + 2>
 __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int base, const EsirkAxis<P, float> ax[3],
-                                                     const float coef[3], float vscale) {
+                                                     const float coef_in[3], float vscale) {
+    const float coef[3] = {coef_in[0] * vscale, coef_in[1] * vscale, coef_in[2] * vscale};  // exact: power of two
     int* jx = sJ + base;                  // lo of J_x; hi at + jVol
     int* jy = sJ + 2 * LY::jVol + base;   // lo of J_y
     int* jz = sJ + 4 * LY::jVol + base;   // lo of J_z
@@ -178,7 +179,7 @@ __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int b
 #pragma unroll
                 for (int i = 0; i < NC; ++i) {
                     const int o = i * LY::jX + j * LY::jY + kk;
-                    red_fixed(jx + o, jx + H + o, cum[i] * Q, vscale);
+                    red_fixed(jx + o, jx + H + o, cum[i] * Q);
                 }
             }
     }
@@ -197,7 +198,7 @@ __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int b
 #pragma unroll
                 for (int j = 0; j < NC; ++j) {
                     const int o = i * LY::jX + j * LY::jY + kk;
-                    red_fixed(jy + o, jy + H + o, cum[j] * Q, vscale);
+                    red_fixed(jy + o, jy + H + o, cum[j] * Q);
                 }
             }
     }
@@ -216,7 +217,7 @@ __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int b
 #pragma unroll
                 for (int kk = 0; kk < NC; ++kk) {
                     const int o = i * LY::jX + j * LY::jY + kk;
-                    red_fixed(jz + o, jz + H + o, cum[kk] * Q, vscale);
+                    red_fixed(jz + o, jz + H + o, cum[kk] * Q);
                 }
             }
     }

@@ -80,7 +80,7 @@ template <typename R> struct StepArgs {
     const long long* step;
     double drive_amp, drive_k;
     int run;            // tile kernel: particles per lane run (0 = about one cell's worth)
-    float vscale;       // FP32-mixed fixed-point scale of the deposit (2^30 / max|coef|)
+    float vscale;       // FP32-mixed fixed-point scale of the deposit (largest power of two <= 2^30 / max|coef|)
     double inv_vscale;
     int64_t np;
 };
@@ -118,7 +118,9 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
             cmax = fmax(cmax, fabs(c->q) * c->w_max / (c->dt * c->g.d[t1] * c->g.d[t2]));
         }
         if (!(cmax > 0.0)) cmax = 1.0;
-        a.vscale = float(1073741824.0 / cmax);
+        int e = 0;
+        std::frexp(1073741824.0 / cmax, &e);  // 2^30 / cmax = m 2^e, m in [0.5, 1)
+        a.vscale = float(std::ldexp(1.0, e - 1));
         a.inv_vscale = 1.0 / double(a.vscale);
     }
     a.np = c->np;
