@@ -37,13 +37,16 @@ def _declare(lib):
     sig = {
         "orc_shape": (D, [I, D]),
         "orc_gather_many": (None, [G, I, P, L, P, P, P, P]),
+        "orc_gather_ec_many": (None, [G, I, P, L, P, P, P, P]),
         "orc_boris_many": (None, [D, D, D, L, P, P, P, P]),
+        "orc_vay_many": (None, [D, D, D, L, P, P, P, P]),
         "orc_deposit_many": (None, [G, I, D, D, L, P, P, P, P, P, P, P, P]),
         "orc_rho_many": (None, [G, I, D, L, P, P, P, P, P]),
         "orc_yee_b": (None, [G, D, P, P]),
         "orc_yee_e": (None, [G, D, P, P, P]),
         "orc_yee_step": (None, [G, D, P, P, P]),
         "orc_pic_step": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D]),
+        "orc_pic_step_alg": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I]),
         "orc_div_edge": (None, [G, P, P]),
         "orc_div_face": (None, [G, P, P]),
         "orc_field_energy": (D, [G, P]),
@@ -110,14 +113,23 @@ class Oracle:
         f = self.lib.orc_shape
         return np.array([f(int(p), float(v)) for v in xi.ravel()]).reshape(xi.shape)
 
-    def gather(self, g, p, fields, x, y, z):
-        """E,B at the particle positions; returns (np, 6)."""
+    def gather(self, g, p, fields, x, y, z, energy=False):
+        """E,B at the particle positions; returns (np, 6).  energy=True: the
+        energy-conserving gather (order p - 1 along staggered axes)."""
         F = [self._f64(fields[c]) for c in range(6)]
         x, y, z = self._f64(x), self._f64(y), self._f64(z)
         out = np.zeros((x.size, 6))
-        self.lib.orc_gather_many(ct.byref(g), int(p), self._ptr_array(F), x.size,
-                                 self._ptr(x), self._ptr(y), self._ptr(z), self._ptr(out))
+        f = self.lib.orc_gather_ec_many if energy else self.lib.orc_gather_many
+        f(ct.byref(g), int(p), self._ptr_array(F), x.size, self._ptr(x), self._ptr(y), self._ptr(z), self._ptr(out))
         return out
+
+    def vay(self, q, m, dt, EB, ux, uy, uz):
+        """Vay's pusher; returns the pushed (ux, uy, uz)."""
+        EB = self._f64(EB)
+        ux, uy, uz = (self._f64(a).copy() for a in (ux, uy, uz))
+        self.lib.orc_vay_many(float(q), float(m), float(dt), ux.size, self._ptr(EB),
+                              self._ptr(ux), self._ptr(uy), self._ptr(uz))
+        return ux, uy, uz
 
     def boris(self, q, m, dt, EB, ux, uy, uz):
         """Returns the pushed (ux, uy, uz)."""
@@ -161,17 +173,18 @@ class Oracle:
                               self._ptr_array([fields[3], fields[4], fields[5]]),
                               self._ptr_array([fields[6], fields[7], fields[8]]))
 
-    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0):
+    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0, pusher=0, gather=0):
         """One PIC step, in place on parts (dict of x,y,z,ux,uy,uz,w float64
-        arrays) and fields (9, nx, ny, nz)."""
+        arrays) and fields (9, nx, ny, nz); pusher 0 Boris / 1 Vay, gather 0
+        momentum- / 1 energy-conserving."""
         keys = ("x", "y", "z", "ux", "uy", "uz", "w")
         for k in keys:
             assert parts[k].dtype == np.float64 and parts[k].flags.c_contiguous
         assert fields.dtype == np.float64 and fields.flags.c_contiguous
-        self.lib.orc_pic_step(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
-                              *[self._ptr(parts[k]) for k in keys],
-                              self._ptr_array([fields[c] for c in range(9)]),
-                              float(drive_amp), float(drive_k), float(t))
+        self.lib.orc_pic_step_alg(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
+                                  *[self._ptr(parts[k]) for k in keys],
+                                  self._ptr_array([fields[c] for c in range(9)]),
+                                  float(drive_amp), float(drive_k), float(t), int(pusher), int(gather))
 
     # -- moving window (z open) -----------------------------------------
     # Readings of the wakefield run: z is open (fields beyond the ends are

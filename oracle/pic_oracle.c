@@ -82,8 +82,10 @@ static const double STAG[6][3] = {
 /* ------------------------------------------------------------------ */
 
 /* s_p(xi): the order-p cardinal B-spline (the (p+1)-fold convolution of the
- * unit box), centred on 0, support |xi| < (p+1)/2. */
+ * unit box), centred on 0, support |xi| < (p+1)/2; p = 0 is the unit box on
+ * [-1/2, 1/2) (used by the energy-conserving gather at order 1). */
 double orc_shape(int p, double xi) {
+    if (p == 0) return (xi >= -0.5 && xi < 0.5) ? 1.0 : 0.0; /* the unit box, half-open */
     double a = fabs(xi);
     switch (p) {
     case 1:
@@ -116,11 +118,10 @@ double orc_shape(int p, double xi) {
  *   F_c(x) = sum_{ijk} s_p(x/dx - i - dx_c) s_p(y/dy - j - dy_c) s_p(z/dz - k - dz_c) F_c[ijk].
  * The node ranges below cover the support with room to spare; nodes outside
  * the support contribute exactly zero. */
-void orc_gather(const orc_grid* g, int p, const double* const F[6],
-                double x, double y, double z, double EB[6]) {
+static void gather_orders(const orc_grid* g, int p, int energy, const double* const F[6], double x, double y,
+                          double z, double EB[6]) {
     enum { NR = 8 };
     const double pos[3] = {x / g->d[0], y / g->d[1], z / g->d[2]};
-    const double half = 0.5 * (p + 1);
     for (int c = 0; c < 6; ++c) {
         /* per axis: the first node of a range that covers the support, and the weights on it */
         int64_t first[3];
@@ -131,8 +132,13 @@ void orc_gather(const orc_grid* g, int p, const double* const F[6],
 #else
             const double sh = pos[a] - STAG[c][a];
 #endif
-            first[a] = (int64_t)floor(sh - half) - 1;
-            for (int r = 0; r < NR; ++r) wt[a][r] = orc_shape(p, sh - (double)(first[a] + r));
+#if ORC_MUTANT == 9
+            const int order = (energy && STAG[c][a] != 0.0 && c != 1) ? p - 1 : p; /* planted: E_y keeps order p */
+#else
+            const int order = (energy && STAG[c][a] != 0.0) ? p - 1 : p;
+#endif
+            first[a] = (int64_t)floor(sh - 0.5 * (order + 1)) - 1;
+            for (int r = 0; r < NR; ++r) wt[a][r] = orc_shape(order, sh - (double)(first[a] + r));
         }
         double acc = 0.0;
         for (int r0 = 0; r0 < NR; ++r0)
@@ -144,6 +150,21 @@ void orc_gather(const orc_grid* g, int p, const double* const F[6],
                 }
         EB[c] = acc;
     }
+}
+
+void orc_gather(const orc_grid* g, int p, const double* const F[6],
+                double x, double y, double z, double EB[6]) {
+    gather_orders(g, p, 0, F, x, y, z, EB);
+}
+
+/* Energy-conserving gather (Sec. 4.2 lists it among the plasma-acceleration
+ * run's options): along every axis where a component is staggered the shape
+ * order drops to p - 1, the order of the Esirkepov current along its own
+ * direction, so that sum_cells J . E dV equals q w v . E(particle) as the
+ * step shrinks; unstaggered axes keep order p. */
+void orc_gather_ec(const orc_grid* g, int p, const double* const F[6],
+                   double x, double y, double z, double EB[6]) {
+    gather_orders(g, p, 1, F, x, y, z, EB);
 }
 
 /* ------------------------------------------------------------------ */
@@ -173,6 +194,36 @@ void orc_boris(double q, double m, double dt, const double E[3], const double B[
     u[1] = upl[1] + k * E[1];
     u[2] = upl[2] + k * E[2];
 #endif
+}
+
+/* Vay's pusher (Vay 2008, named among the plasma-acceleration run's options
+ * in Sec. 4.2), u = gamma*v:
+ *   u^{n+1/2} = u^{n-1/2} + (q dt/m) (E + (v^{n-1/2} + v^{n+1/2})/2 x B),
+ * solved as u' = u + (q dt/m)(E + v x B/2) with v = u/gamma, tau = (q dt/2m) B,
+ * u* = u'.tau, sigma = 1 + |u'|^2 - |tau|^2,
+ * gamma_new = sqrt((sigma + sqrt(sigma^2 + 4 (|tau|^2 + u*^2)))/2),
+ * t = tau/gamma_new, s = 1/(1 + |t|^2), u_new = s (u' + (u'.t) t + u' x t). */
+void orc_vay(double q, double m, double dt, const double E[3], const double B[3], double u[3]) {
+    const double k = q * dt / m;
+    const double g0 = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const double v[3] = {u[0] / g0, u[1] / g0, u[2] / g0};
+    const double vxB[3] = {v[1] * B[2] - v[2] * B[1], v[2] * B[0] - v[0] * B[2], v[0] * B[1] - v[1] * B[0]};
+    double up[3];
+#if ORC_MUTANT == 10
+    for (int a = 0; a < 3; ++a) up[a] = u[a] + k * E[a]; /* planted: explicit half of v x B dropped */
+#else
+    for (int a = 0; a < 3; ++a) up[a] = u[a] + k * (E[a] + 0.5 * vxB[a]);
+#endif
+    const double tau[3] = {0.5 * k * B[0], 0.5 * k * B[1], 0.5 * k * B[2]};
+    const double tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const double ustar = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+    const double sigma = 1.0 + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
+    const double gnew = sqrt(0.5 * (sigma + sqrt(sigma * sigma + 4.0 * (tau2 + ustar * ustar))));
+    const double t[3] = {tau[0] / gnew, tau[1] / gnew, tau[2] / gnew};
+    const double s = 1.0 / (1.0 + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const double ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+    const double uxt[3] = {up[1] * t[2] - up[2] * t[1], up[2] * t[0] - up[0] * t[2], up[0] * t[1] - up[1] * t[0]};
+    for (int a = 0; a < 3; ++a) u[a] = s * (up[a] + ut * t[a] + uxt[a]);
 }
 
 /* x^{n+1} = x^n + dt u/gamma with gamma = sqrt(1+|u|^2); no wrap. */
@@ -357,6 +408,15 @@ void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64
                   double* x, double* y, double* z, double* ux, double* uy, double* uz,
                   const double* w, double* const fields[9],
                   double drive_amp, double drive_k, double t) {
+    orc_pic_step_alg(g, p, dt, q, m, np, x, y, z, ux, uy, uz, w, fields, drive_amp, drive_k, t, 0, 0);
+}
+
+/* The same step with a choice of pusher (0 Boris, 1 Vay) and gather
+ * (0 momentum-conserving, 1 energy-conserving). */
+void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, int64_t np,
+                      double* x, double* y, double* z, double* ux, double* uy, double* uz,
+                      const double* w, double* const fields[9],
+                      double drive_amp, double drive_k, double t, int pusher, int gather) {
     const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
     double* const E[3] = {fields[0], fields[1], fields[2]};
     double* const B[3] = {fields[3], fields[4], fields[5]};
@@ -366,10 +426,12 @@ void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64
     for (int c = 0; c < 3; ++c) memset(J[c], 0, (size_t)C * sizeof(double));
     for (int64_t n = 0; n < np; ++n) {
         double EB[6];
-        orc_gather(g, p, F, x[n], y[n], z[n], EB);
+        if (gather) orc_gather_ec(g, p, F, x[n], y[n], z[n], EB);
+        else orc_gather(g, p, F, x[n], y[n], z[n], EB);
         if (drive_amp != 0.0) EB[1] += drive_amp * cos(drive_k * x[n] - drive_k * t);
         double u[3] = {ux[n], uy[n], uz[n]};
-        orc_boris(q, m, dt, EB, EB + 3, u);
+        if (pusher) orc_vay(q, m, dt, EB, EB + 3, u);
+        else orc_boris(q, m, dt, EB, EB + 3, u);
         double x0[3] = {x[n], y[n], z[n]};
         double x1[3] = {x[n], y[n], z[n]};
         orc_advance(dt, u, x1);
@@ -440,6 +502,22 @@ double orc_kinetic_energy(double m, int64_t np, const double* ux, const double* 
 void orc_gather_many(const orc_grid* g, int p, const double* const F[6], int64_t np,
                      const double* x, const double* y, const double* z, double* out /* [np][6] */) {
     for (int64_t n = 0; n < np; ++n) orc_gather(g, p, F, x[n], y[n], z[n], out + 6 * n);
+}
+
+void orc_gather_ec_many(const orc_grid* g, int p, const double* const F[6], int64_t np, const double* x,
+                        const double* y, const double* z, double* out /* [np][6] */) {
+    for (int64_t n = 0; n < np; ++n) orc_gather_ec(g, p, F, x[n], y[n], z[n], out + 6 * n);
+}
+
+void orc_vay_many(double q, double m, double dt, int64_t np, const double* EB /* [np][6] */, double* ux,
+                  double* uy, double* uz) {
+    for (int64_t n = 0; n < np; ++n) {
+        double u[3] = {ux[n], uy[n], uz[n]};
+        orc_vay(q, m, dt, EB + 6 * n, EB + 6 * n + 3, u);
+        ux[n] = u[0];
+        uy[n] = u[1];
+        uz[n] = u[2];
+    }
 }
 
 void orc_boris_many(double q, double m, double dt, int64_t np, const double* EB /* [np][6] */,

@@ -15,7 +15,9 @@ typedef struct {
 
 double orc_shape(int p, double xi);
 void orc_gather(const orc_grid* g, int p, const double* const F[6], double x, double y, double z, double EB[6]);
+void orc_gather_ec(const orc_grid* g, int p, const double* const F[6], double x, double y, double z, double EB[6]);
 void orc_boris(double q, double m, double dt, const double E[3], const double B[3], double u[3]);
+void orc_vay(double q, double m, double dt, const double E[3], const double B[3], double u[3]);
 void orc_advance(double dt, const double u[3], double x[3]);
 double orc_wrap(double x, double L);
 void orc_deposit_esirkepov(const orc_grid* g, int p, double dt, double qw, const double x0[3], const double x1[3],
@@ -27,6 +29,9 @@ void orc_yee_step(const orc_grid* g, double dt, double* const E[3], double* cons
 void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
                   double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
                   double drive_amp, double drive_k, double t);
+void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                      double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                      double drive_amp, double drive_k, double t, int pusher, int gather);
 void orc_div_edge(const orc_grid* g, const double* const F[3], double* out);
 void orc_div_face(const orc_grid* g, const double* const F[3], double* out);
 double orc_field_energy(const orc_grid* g, const double* const F[6]);

@@ -429,3 +429,60 @@ def pin_free_streaming(O):
 
 
 ALL_PINS.append(pin_free_streaming)
+
+
+def pin_vay(O):
+    """Vay's pusher: the result satisfies its defining equation
+    u_new - u = (q dt/m)(E + (v + v_new)/2 x B), and a particle on the E x B
+    drift (E = -v x B) keeps its momentum, at gamma ~ 5."""
+    q, m, dt = -1.0, 1.0, 0.45
+    k = 40
+    E = np.stack([_rand(120, k, -0.8, 0.8, a) for a in range(3)], 1)
+    B = np.stack([_rand(121, k, -2.0, 2.0, a) for a in range(3)], 1)
+    u = np.stack([_rand(122, k, -4.0, 4.0, a) for a in range(3)], 1)
+    un = np.stack(O.vay(q, m, dt, np.concatenate([E, B], 1), u[:, 0], u[:, 1], u[:, 2]), 1)
+    v = u / np.sqrt(1 + np.sum(u * u, 1))[:, None]
+    vn = un / np.sqrt(1 + np.sum(un * un, 1))[:, None]
+    assert np.max(np.abs((un - u) - q * dt / m * (E + np.cross(0.5 * (v + vn), B)))) < 1e-13
+    Bd = np.array([0.3, -1.1, 0.7])
+    d = np.array([1.0, 0.4, 0.2])
+    d -= d @ Bd * Bd / (Bd @ Bd)
+    ud = 5.0 * d / np.linalg.norm(d)
+    Ed = -np.cross(ud / np.sqrt(1 + ud @ ud), Bd)
+    got = np.array(O.vay(q, m, dt, np.concatenate([Ed, Bd])[None, :], [ud[0]], [ud[1]], [ud[2]])).ravel()
+    assert np.max(np.abs(got - ud)) < 1e-12
+
+
+ALL_PINS.append(pin_vay)
+
+
+def pin_energy_gather_work(O):
+    """Energy-conserving gather with the Esirkepov current: for a move along
+    y, sum J.E dV dt equals q w times the path integral of the gathered E_y
+    (order p - 1 along y), computed exactly piece by piece between knots."""
+    n = (7, 8, 6)
+    g = O.grid(n)
+    p = 2
+    F = np.zeros((6,) + n)
+    F[:3] = (2 * inputs.uniform(130, 0, 3 * int(np.prod(n)), 0) - 1).reshape((3,) + n)
+    q, w, dt = -1.0, 0.6, 0.5
+    glx, glw = np.polynomial.legendre.leggauss(6)
+    for t in range(4):
+        x0 = np.array([3.1, 3.6 + 0.2 * t, 2.9])
+        x1 = x0 + np.array([0.0, 0.8 - 0.45 * t, 0.0])
+        J = O.deposit(g, p, dt, q, [x0[0]], [x0[1]], [x0[2]], [x1[0]], [x1[1]], [x1[2]], [w])
+        work = np.sum(J * F[:3]) * dt
+        lo, hi = sorted((x0[1], x1[1]))
+        knots = np.arange(np.ceil(lo - 0.5), np.floor(hi - 0.5) + 1) + 0.5
+        pts = np.concatenate([[lo], knots[(knots > lo) & (knots < hi)], [hi]])
+        integral = 0.0
+        for a, b in zip(pts[:-1], pts[1:]):
+            s = 0.5 * (a + b) + 0.5 * (b - a) * glx
+            P = np.repeat(x0[None, :], s.size, 0)
+            P[:, 1] = s
+            integral += 0.5 * (b - a) * np.sum(glw * O.gather(g, p, F, P[:, 0], P[:, 1], P[:, 2], energy=True)[:, 1])
+        integral *= np.sign(x1[1] - x0[1])
+        assert abs(work - q * w * integral) < 1e-12 * max(1.0, abs(work))
+
+
+ALL_PINS.append(pin_energy_gather_work)

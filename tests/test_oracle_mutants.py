@@ -4,7 +4,9 @@ Each mutant is the oracle rebuilt with one planted mistake (ORC_MUTANT in
 oracle/pic_oracle.c): a wrong shape piece, a missing staggering offset, a
 dropped Boris half kick, an Esirkepov window off by one node, 1/2 for 1/3 in
 Esirkepov's W, a flipped curl sign, a flipped current sign, momentum used as
-velocity.  Every mutant must fail at least one pin.
+velocity, an energy-conserving gather that keeps order p for one component,
+a Vay pusher without its explicit magnetic half.  Every mutant must fail at
+least one pin.
 """
 import pytest
 
@@ -20,6 +22,8 @@ MUTANTS = {
     6: "curl sign in the B update",
     7: "current sign in the E update",
     8: "momentum used as velocity",
+    9: "energy-conserving gather keeps order p for E_y",
+    10: "Vay without the explicit half of v x B",
 }
 
 
