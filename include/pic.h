@@ -140,6 +140,17 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 pic_status pic_set_window_plasma(pic_ctx* ctx, int32_t ppc, double n0, double ramp_start,
                                  double ramp_length);
 
+/* Particle algorithms (Sec. 4.2 lists both options for the plasma-
+ * acceleration run): pusher 0 = Boris (default), 1 = Vay (Vay 2008: the
+ * average velocity (v^{n-1/2} + v^{n+1/2})/2 in the magnetic force, which
+ * keeps the E x B drift exact at relativistic speed); gather 0 =
+ * momentum-conserving (order p along every axis, default), 1 =
+ * energy-conserving (order p - 1 along each axis where the component is
+ * staggered, the order of the Esirkepov current along its own direction).
+ * Applies to pic_step and the split API; pic_step_adjoint needs the defaults
+ * (PIC_ERR_STATE otherwise).  PIC_ERR_ARG for other values.  Waits. */
+pic_status pic_set_particle_algorithms(pic_ctx* ctx, int32_t pusher, int32_t gather);
+
 /* Number of window shifts so far and the lab-frame z of the window's
  * lower end (shifts * dz).  Either pointer may be NULL. */
 pic_status pic_get_window(pic_ctx* ctx, int64_t* shifts, double* z_lab);

@@ -229,7 +229,8 @@ class Oracle:
         ramp_start, ramp_length).  Returns the new particle dict."""
         assert g.zopen
         Lz = g.n[2] * g.d[2]
-        self.pic_step(g, p, dt, q, m, parts, fields, 0.0, 0.0, win["step"] * dt)
+        self.pic_step(g, p, dt, q, m, parts, fields, 0.0, 0.0, win["step"] * dt, pusher=win.get("pusher", 0),
+                      gather=win.get("gather", 0))
         keep = (parts["z"] >= 0.0) & (parts["z"] < Lz)
         parts = {k: np.ascontiguousarray(v[keep]) for k, v in parts.items()}
         win["step"] += 1

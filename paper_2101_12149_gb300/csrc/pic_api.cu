@@ -635,6 +635,20 @@ pic_status pic_set_window_plasma(pic_ctx* c, int32_t ppc, double n0, double ramp
     return PIC_OK;
 }
 
+pic_status pic_set_particle_algorithms(pic_ctx* c, int32_t pusher, int32_t gather) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (pusher < 0 || pusher > 1 || gather < 0 || gather > 1)
+        return fail(PIC_ERR_ARG, "pusher must be 0 (Boris) or 1 (Vay), gather 0 (momentum) or 1 (energy)");
+    PIC_CUDA(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->graph) {  // the choice is a kernel argument baked into the graph
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->pusher = pusher;
+    c->egather = gather;
+    return PIC_OK;
+}
+
 pic_status pic_get_window(pic_ctx* c, int64_t* shifts, double* z_lab) {
     if (pic_status s = check_ctx(c)) return s;
     if (shifts) *shifts = c->shifts;
@@ -727,6 +741,8 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (pic_status s = check_ctx(c)) return s;
     if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
     if (c->window) return fail(PIC_ERR_STATE, "the adjoint runs periodic grids only");
+    if (c->pusher || c->egather)
+        return fail(PIC_ERR_STATE, "the adjoint differentiates the Boris push and momentum-conserving gather only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (pic_status s = read_error_word(c)) return s;

@@ -94,6 +94,8 @@ struct pic_ctx {
     double* dsum = nullptr;        // diagnostics scratch
     int64_t step = 0;
     double drive_amp = 0.0, drive_k = 0.0;
+    int pusher = 0;   // 0 Boris, 1 Vay
+    int egather = 0;  // 0 momentum-conserving, 1 energy-conserving gather
 
     bool timing = false;
     pic::Timer timers[16];

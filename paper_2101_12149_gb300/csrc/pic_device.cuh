@@ -66,6 +66,14 @@ template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqr
 // ---------------------------------------------------------------------------
 template <int P, typename R> struct Shape;
 
+// Order 0 (the unit box on [-1/2, 1/2)): used by the energy-conserving gather at order 1.
+template <typename R> struct Shape<0, R> {
+    __device__ __forceinline__ static void weights(R f, int& first, R w[1]) {
+        first = f >= R(0.5) ? 1 : 0;
+        w[0] = R(1);
+    }
+};
+
 template <typename R> struct Shape<1, R> {
     __device__ __forceinline__ static void weights(R f, int& first, R w[2]) {
         first = 0;
@@ -146,6 +154,19 @@ __device__ __forceinline__ void staggered_weights(R f, int& first, R w[P + 1]) {
     if (!hi) first -= 1;
 }
 
+// Energy-conserving gather (an option of the paper's plasma-acceleration run,
+// Sec. 4.2): along a staggered axis the order drops to P - 1, the order of
+// the Esirkepov current along its own direction; the weights fill the first P
+// of the P + 1 stencil slots and the last is zero.
+template <int P, typename R>
+__device__ __forceinline__ void staggered_weights_ec(R f, int& first, R w[P + 1]) {
+    R v[P];
+    staggered_weights<P - 1, R>(f, first, v);
+#pragma unroll
+    for (int r = 0; r < P; ++r) w[r] = v[r];
+    w[P] = R(0);
+}
+
 // ---------------------------------------------------------------------------
 // Relativistic Boris push (u = gamma v):
 //   k = q dt / (2 m);  u- = u + k E;  g- = sqrt(1 + |u-|^2);  t = k B / g-;
@@ -185,6 +206,51 @@ __device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
     u[0] = um[0] + k * E[0];
     u[1] = um[1] + k * E[1];
     u[2] = um[2] + k * E[2];
+}
+
+// ---------------------------------------------------------------------------
+// Vay's pusher (Vay 2008; an option of the paper's plasma-acceleration run,
+// Sec. 4.2): u_new - u = (q dt/m)(E + (v + v_new)/2 x B), solved in closed
+// form: u' = u + (q dt/m)(E + v x B / 2), tau = (q dt / 2m) B, u* = u'.tau,
+// sigma = 1 + |u'|^2 - |tau|^2, gamma_new^2 = (sigma + sqrt(sigma^2 +
+// 4(|tau|^2 + u*^2)))/2, t = tau/gamma_new, s = 1/(1 + |t|^2),
+// u_new = s (u' + (u'.t) t + u' x t).  kq = q dt / (2 m).  The FP32
+// instantiation works in FP64 when |u'| > 1e3.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void vay_core(T kq, const T B[3], const T up[3], T u[3]) {
+    const T tau[3] = {kq * B[0], kq * B[1], kq * B[2]};
+    const T tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
+    const T ustar = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
+    const T sigma = T(1) + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
+    const T gnew = rsqrt_<T>(T(0.5) * (sigma + rsqrt_<T>(sigma * sigma + T(4) * (tau2 + ustar * ustar))));
+    const T t[3] = {tau[0] / gnew, tau[1] / gnew, tau[2] / gnew};
+    const T s = T(1) / (T(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
+    const T ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
+    u[0] = s * (up[0] + ut * t[0] + (up[1] * t[2] - up[2] * t[1]));
+    u[1] = s * (up[1] + ut * t[1] + (up[2] * t[0] - up[0] * t[2]));
+    u[2] = s * (up[2] + ut * t[2] + (up[0] * t[1] - up[1] * t[0]));
+}
+
+template <typename R>
+__device__ __forceinline__ void vay(R kq, const R E[3], const R B[3], R u[3]) {
+    const R g0 = rsqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R v[3] = {u[0] / g0, u[1] / g0, u[2] / g0};
+    R up[3];
+    up[0] = u[0] + R(2) * kq * E[0] + kq * (v[1] * B[2] - v[2] * B[1]);
+    up[1] = u[1] + R(2) * kq * E[1] + kq * (v[2] * B[0] - v[0] * B[2]);
+    up[2] = u[2] + R(2) * kq * E[2] + kq * (v[0] * B[1] - v[1] * B[0]);
+    if (sizeof(R) == 4 && up[0] * up[0] + up[1] * up[1] + up[2] * up[2] > R(1e6)) {
+        const double Bd[3] = {double(B[0]), double(B[1]), double(B[2])};
+        const double upd[3] = {double(up[0]), double(up[1]), double(up[2])};
+        double ud[3];
+        vay_core<double>(double(kq), Bd, upd, ud);
+        u[0] = R(ud[0]);
+        u[1] = R(ud[1]);
+        u[2] = R(ud[2]);
+    } else {
+        vay_core<R>(kq, B, up, u);
+    }
 }
 
 // ---------------------------------------------------------------------------

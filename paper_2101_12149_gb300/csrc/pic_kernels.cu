@@ -395,7 +395,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                     {
                         GatherW<P, R> G;
                         int fn[3], fs[3];
-                        gather_weights<P, R>(f0, G, fn, fs);
+                        gather_weights<P, R>(f0, G, fn, fs, A.egather != 0);
                         const int bnx = (li + 2 + fn[0]) * LY::eX, bsx = (li + 2 + fs[0]) * LY::eX;
                         const int bny = (lj + 2 + fn[1]) * LY::eY, bsy = (lj + 2 + fs[1]) * LY::eY;
                         const int bnz = lk + 2 + fn[2], bsz = lk + 2 + fs[2];
@@ -549,7 +549,7 @@ __device__ __forceinline__ void outsider_body(const StepArgs<R>& A, const int p)
     {
         GatherW<P, R> G;
         int fn[3], fs[3];
-        gather_weights<P, R>(f0, G, fn, fs);
+        gather_weights<P, R>(f0, G, fn, fs, A.egather != 0);
         offsets_global<P, R>(G, A.g, cell, fn, fs);
         gather6<P, R>(G, A.E, A.B, EB);
     }
@@ -619,7 +619,7 @@ __global__ void __launch_bounds__(kBlock) k_gather_push(StepArgs<R> A) {
     R u[3] = {A.pa[3][p], A.pa[4][p], A.pa[5][p]};
     GatherW<P, R> G;
     int fn[3], fs[3];
-    gather_weights<P, R>(f0, G, fn, fs);
+    gather_weights<P, R>(f0, G, fn, fs, A.egather != 0);
     offsets_global<P, R>(G, g, cell, fn, fs);
     R EB[6];
     gather6<P, R>(G, A.E, A.B, EB);

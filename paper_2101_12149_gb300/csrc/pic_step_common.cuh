@@ -80,6 +80,8 @@ template <typename R> struct StepArgs {
     const long long* step;
     double drive_amp, drive_k;
     int run;            // tile kernel: particles per lane run (0 = about one cell's worth)
+    int pusher;         // 0 Boris, 1 Vay
+    int egather;        // 0 momentum-conserving gather, 1 energy-conserving
     float vscale;       // FP32-mixed fixed-point scale of the deposit (largest power of two <= 2^30 / max|coef|)
     double inv_vscale;
     int64_t np;
@@ -110,6 +112,8 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.step = c->d_step;
     a.drive_amp = c->drive_amp;
     a.drive_k = c->drive_k;
+    a.pusher = c->pusher;
+    a.egather = c->egather;
     a.run = 0;
     {
         double cmax = 0.0;
@@ -185,12 +189,15 @@ __device__ __forceinline__ void gather6(const GatherW<P, R>& G, const R* const E
 // Weights from the in-cell fractions; offsets either into a staged tile
 // (cell at local index l + halo, strides st) or into the global arrays with
 // periodic wrap.
+// ec: energy-conserving gather (staggered axes at order P - 1).
 template <int P, typename R>
-__device__ __forceinline__ void gather_weights(const R f[3], GatherW<P, R>& G, int first_n[3], int first_s[3]) {
+__device__ __forceinline__ void gather_weights(const R f[3], GatherW<P, R>& G, int first_n[3], int first_s[3],
+                                               bool ec = false) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         Shape<P, R>::weights(f[a], first_n[a], G.wn[a]);
-        staggered_weights<P, R>(f[a], first_s[a], G.ws[a]);
+        if (ec) staggered_weights_ec<P, R>(f[a], first_s[a], G.ws[a]);
+        else staggered_weights<P, R>(f[a], first_s[a], G.ws[a]);
     }
 }
 
@@ -351,7 +358,8 @@ __device__ __forceinline__ void push_particle(const StepArgs<R>& A, R EB[6], con
         const double xp = sizeof(R) == 8 ? xg0[0] : (double(cell[0]) + double(f0[0])) * A.g.d[0];
         EB[1] += R(A.drive_amp * cos(A.drive_k * xp - A.drive_k * t));
     }
-    boris<R>(A.kq, EB, EB + 3, u);
+    if (A.pusher) vay<R>(A.kq, EB, EB + 3, u);
+    else boris<R>(A.kq, EB, EB + 3, u);
     mv.ok = true;
     if (sizeof(R) == 8) {
         const double gi = 1.0 / sqrt(1.0 + double(u[0]) * double(u[0]) + double(u[1]) * double(u[1]) +

@@ -64,6 +64,7 @@ def load_library(path: str = LIB_PATH):
             "pic_step": [P, I32],
             "pic_step_adjoint": [P, I32, I32, P, P, P, ct.c_int],
             "pic_set_window_plasma": [P, I32, D, D, D],
+            "pic_set_particle_algorithms": [P, I32, I32],
             "pic_get_window": [P, ct.POINTER(I64), ct.POINTER(D)],
             "pic_get_field": [P, I32, P, ct.c_int],
             "pic_set_field": [P, I32, P, ct.c_int],
@@ -211,6 +212,12 @@ class Context:
 
     def step(self, nsteps=1):
         _check(self.lib.pic_step(self.h, int(nsteps)))
+
+    def set_particle_algorithms(self, pusher="boris", gather="momentum"):
+        """pusher "boris" | "vay"; gather "momentum" | "energy" (conserving)."""
+        pu = {"boris": 0, "vay": 1}[pusher] if isinstance(pusher, str) else int(pusher)
+        ga = {"momentum": 0, "energy": 1}[gather] if isinstance(gather, str) else int(gather)
+        _check(self.lib.pic_set_particle_algorithms(self.h, pu, ga))
 
     def set_window_plasma(self, ppc, n0, ramp_start, ramp_length):
         _check(self.lib.pic_set_window_plasma(self.h, int(ppc), float(n0), float(ramp_start), float(ramp_length)))

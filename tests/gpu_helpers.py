@@ -41,7 +41,7 @@ class Case:
 
     def __init__(self, n, order, ppc, sigma_u, seed, precision=pic.FP64, d=(1.0, 1.0, 1.0), cfl=0.99,
                  field_scale=0.0, sort_every=1, tile=(0, 0, 0), stream=None, density=1.0, pert=(0.0, 0.0),
-                 q=-1.0, m=1.0):
+                 q=-1.0, m=1.0, pusher=0, gather=0):
         self.n, self.order, self.d = tuple(n), order, tuple(d)
         self.L = [n[a] * d[a] for a in range(3)]
         self.q, self.m = q, m
@@ -55,6 +55,9 @@ class Case:
                                tile=tile, stream=stream)
         self.ctx.set_fields(self.F)
         self.ctx.load_particles(q, m, self.parts)
+        self.pusher, self.gather = pusher, gather
+        if pusher or gather:
+            self.ctx.set_particle_algorithms(pusher, gather)
         self.O = Oracle()
         self.g = self.O.grid(n, d)
         self.ref = {k: v.copy() for k, v in self.parts.items()}
@@ -64,7 +67,7 @@ class Case:
     def oracle_steps(self, k, drive=(0.0, 0.0)):
         for _ in range(k):
             self.O.pic_step(self.g, self.order, self.dt, self.q, self.m, self.ref, self.Fref,
-                            drive[0], drive[1], self.nsteps * self.dt)
+                            drive[0], drive[1], self.nsteps * self.dt, pusher=self.pusher, gather=self.gather)
             self.nsteps += 1
 
     def errors(self):

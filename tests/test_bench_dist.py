@@ -34,7 +34,7 @@ def _rank(rank, world, port, times, out):
 def test_two_ranks_take_the_slowest_time_and_count_all_replicas():
     world = 2
     times = [0.5, 2.0]
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), times, out), nprocs=world, join=True)
         res = dict(out)
