@@ -47,6 +47,9 @@ def _declare(lib):
         "orc_yee_step": (None, [G, D, P, P, P]),
         "orc_pic_step": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D]),
         "orc_pic_step_alg": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I]),
+        "orc_pic_step_full": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I, I]),
+        "orc_yee_b_ckc": (None, [G, D, P, P]),
+        "orc_yee_step_ckc": (None, [G, D, P, P, P]),
         "orc_div_edge": (None, [G, P, P]),
         "orc_div_face": (None, [G, P, P]),
         "orc_field_energy": (D, [G, P]),
@@ -166,14 +169,20 @@ class Oracle:
         self.lib.orc_yee_e(ct.byref(g), float(dt), self._ptr_array([E[0], E[1], E[2]]),
                            self._ptr_array([B[0], B[1], B[2]]), self._ptr_array([J[0], J[1], J[2]]))
 
-    def yee_step(self, g, dt, fields):
-        """In place on fields (9, nx, ny, nz)."""
-        self.lib.orc_yee_step(ct.byref(g), float(dt),
+    def yee_b_ckc(self, g, h, E, B):
+        self.lib.orc_yee_b_ckc(ct.byref(g), float(h), self._ptr_array([E[0], E[1], E[2]]),
+                               self._ptr_array([B[0], B[1], B[2]]))
+
+    def yee_step(self, g, dt, fields, solver=0):
+        """In place on fields (9, nx, ny, nz); solver 0 Yee, 1 CKC."""
+        f = self.lib.orc_yee_step_ckc if solver else self.lib.orc_yee_step
+        f(ct.byref(g), float(dt),
                               self._ptr_array([fields[0], fields[1], fields[2]]),
                               self._ptr_array([fields[3], fields[4], fields[5]]),
                               self._ptr_array([fields[6], fields[7], fields[8]]))
 
-    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0, pusher=0, gather=0):
+    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0, pusher=0, gather=0,
+                 solver=0):
         """One PIC step, in place on parts (dict of x,y,z,ux,uy,uz,w float64
         arrays) and fields (9, nx, ny, nz); pusher 0 Boris / 1 Vay, gather 0
         momentum- / 1 energy-conserving."""
@@ -181,10 +190,10 @@ class Oracle:
         for k in keys:
             assert parts[k].dtype == np.float64 and parts[k].flags.c_contiguous
         assert fields.dtype == np.float64 and fields.flags.c_contiguous
-        self.lib.orc_pic_step_alg(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
-                                  *[self._ptr(parts[k]) for k in keys],
-                                  self._ptr_array([fields[c] for c in range(9)]),
-                                  float(drive_amp), float(drive_k), float(t), int(pusher), int(gather))
+        self.lib.orc_pic_step_full(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
+                                   *[self._ptr(parts[k]) for k in keys],
+                                   self._ptr_array([fields[c] for c in range(9)]),
+                                   float(drive_amp), float(drive_k), float(t), int(pusher), int(gather), int(solver))
 
     # -- moving window (z open) -----------------------------------------
     # Readings of the wakefield run: z is open (fields beyond the ends are
@@ -230,7 +239,7 @@ class Oracle:
         assert g.zopen
         Lz = g.n[2] * g.d[2]
         self.pic_step(g, p, dt, q, m, parts, fields, 0.0, 0.0, win["step"] * dt, pusher=win.get("pusher", 0),
-                      gather=win.get("gather", 0))
+                      gather=win.get("gather", 0), solver=win.get("solver", 0))
         keep = (parts["z"] >= 0.0) & (parts["z"] < Lz)
         parts = {k: np.ascontiguousarray(v[keep]) for k, v in parts.items()}
         win["step"] += 1

@@ -385,6 +385,61 @@ void orc_yee_e(const orc_grid* g, double dt, double* const E[3], const double* c
             }
 }
 
+/* B <- B - h curl E with the Cole-Karkkainen stencil (the CKC solver named
+ * for the plasma-acceleration run, Sec. 4.2), for cubic cells: every forward
+ * difference in curl E is averaged over the two directions transverse to it
+ * with weights (1/4, 1/2, 1/4) x (1/4, 1/2, 1/4), e.g. for d Ez/dy at
+ * (i, j+1/2, k+1/2)
+ *   sum_{a,b in -1..1} w_a w_b (Ez(i+a, j+1, k+b+1/2) - Ez(i+a, j, k+b+1/2)) / dy,
+ * w_0 = 1/2, w_{+-1} = 1/4.  Along-axis variations are untouched (the
+ * weights sum to 1); the scheme is stable up to dt = dx. */
+static double dfwd_ckc(const orc_grid* g, const double* F, int axis, int64_t i, int64_t j, int64_t k) {
+#if ORC_MUTANT == 11
+    static const double w[3] = {1.0 / 3.0, 1.0 / 3.0, 1.0 / 3.0}; /* planted: box average instead of (1/4,1/2,1/4) */
+#else
+    static const double w[3] = {0.25, 0.5, 0.25};
+#endif
+    const int t1 = (axis + 1) % 3, t2 = (axis + 2) % 3;
+    double acc = 0.0;
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) {
+            int64_t p0[3] = {i, j, k};
+            p0[t1] += a;
+            p0[t2] += b;
+            int64_t p1[3] = {p0[0], p0[1], p0[2]};
+            p1[axis] += 1;
+            acc += w[a + 1] * w[b + 1] * (fetch(g, F, p1[0], p1[1], p1[2]) - fetch(g, F, p0[0], p0[1], p0[2]));
+        }
+    return acc / g->d[axis];
+}
+
+void orc_yee_b_ckc(const orc_grid* g, double h, const double* const E[3], double* const B[3]) {
+    const int64_t nx = g->n[0], ny = g->n[1], nz = g->n[2];
+    const int64_t C = nx * ny * nz;
+    double* nb[3];
+    for (int c = 0; c < 3; ++c) nb[c] = (double*)malloc((size_t)C * sizeof(double));
+    for (int64_t i = 0; i < nx; ++i)
+        for (int64_t j = 0; j < ny; ++j)
+            for (int64_t k = 0; k < nz; ++k) {
+                const int64_t c = idx3(g, i, j, k);
+                nb[0][c] = B[0][c] - h * (dfwd_ckc(g, E[2], 1, i, j, k) - dfwd_ckc(g, E[1], 2, i, j, k));
+                nb[1][c] = B[1][c] - h * (dfwd_ckc(g, E[0], 2, i, j, k) - dfwd_ckc(g, E[2], 0, i, j, k));
+                nb[2][c] = B[2][c] - h * (dfwd_ckc(g, E[1], 0, i, j, k) - dfwd_ckc(g, E[0], 1, i, j, k));
+            }
+    for (int c = 0; c < 3; ++c) {
+        memcpy(B[c], nb[c], (size_t)C * sizeof(double));
+        free(nb[c]);
+    }
+}
+
+/* One step with the CKC B update (E update as in Yee). */
+void orc_yee_step_ckc(const orc_grid* g, double dt, double* const E[3], double* const B[3],
+                      const double* const J[3]) {
+    orc_yee_b_ckc(g, 0.5 * dt, (const double* const*)E, B);
+    orc_yee_e(g, dt, E, (const double* const*)B, J);
+    orc_yee_b_ckc(g, 0.5 * dt, (const double* const*)E, B);
+}
+
 /* One Yee step: B half step, E full step with the current, B half step. */
 void orc_yee_step(const orc_grid* g, double dt, double* const E[3], double* const B[3],
                   const double* const J[3]) {
@@ -417,6 +472,14 @@ void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, i
                       double* x, double* y, double* z, double* ux, double* uy, double* uz,
                       const double* w, double* const fields[9],
                       double drive_amp, double drive_k, double t, int pusher, int gather) {
+    orc_pic_step_full(g, p, dt, q, m, np, x, y, z, ux, uy, uz, w, fields, drive_amp, drive_k, t, pusher, gather, 0);
+}
+
+/* The same with a choice of field solver too (0 Yee, 1 CKC). */
+void orc_pic_step_full(const orc_grid* g, int p, double dt, double q, double m, int64_t np,
+                       double* x, double* y, double* z, double* ux, double* uy, double* uz,
+                       const double* w, double* const fields[9],
+                       double drive_amp, double drive_k, double t, int pusher, int gather, int solver) {
     const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
     double* const E[3] = {fields[0], fields[1], fields[2]};
     double* const B[3] = {fields[3], fields[4], fields[5]};
@@ -443,7 +506,8 @@ void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, i
         uy[n] = u[1];
         uz[n] = u[2];
     }
-    orc_yee_step(g, dt, E, B, (const double* const*)J);
+    if (solver) orc_yee_step_ckc(g, dt, E, B, (const double* const*)J);
+    else orc_yee_step(g, dt, E, B, (const double* const*)J);
 }
 
 /* ------------------------------------------------------------------ */

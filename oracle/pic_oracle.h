@@ -29,6 +29,11 @@ void orc_yee_step(const orc_grid* g, double dt, double* const E[3], double* cons
 void orc_pic_step(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
                   double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
                   double drive_amp, double drive_k, double t);
+void orc_yee_b_ckc(const orc_grid* g, double h, const double* const E[3], double* const B[3]);
+void orc_yee_step_ckc(const orc_grid* g, double dt, double* const E[3], double* const B[3], const double* const J[3]);
+void orc_pic_step_full(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                       double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                       double drive_amp, double drive_k, double t, int pusher, int gather, int solver);
 void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
                       double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
                       double drive_amp, double drive_k, double t, int pusher, int gather);

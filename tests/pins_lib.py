@@ -486,3 +486,67 @@ def pin_energy_gather_work(O):
 
 
 ALL_PINS.append(pin_energy_gather_work)
+
+
+def _ckc_mode(O, n, d, m_k, M, dt, solver=1):
+    """Evolve the vacuum mode of wave numbers 2 pi m_k / (n d) with E along a
+    direction orthogonal to the Yee symbol; return (E^M, E^0, predicted cos)."""
+    g = O.grid(n, d)
+    k = np.array([2 * np.pi * m_k[a] / (n[a] * d[a]) for a in range(3)])
+    kap = np.array([2 / d[a] * np.sin(k[a] * d[a] / 2) for a in range(3)])
+    kt = kap.copy()
+    if solver:
+        for a in range(3):
+            for b in range(3):
+                if b != a:
+                    kt[a] *= np.cos(k[b] * d[b] / 2) ** 2
+    e = np.cross(kap, np.array([0.3, -0.7, 0.5]))
+    e /= np.linalg.norm(e)
+    F = np.zeros((9,) + tuple(n))
+    idx = np.meshgrid(*[np.arange(n[a]) for a in range(3)], indexing="ij")
+    for c in range(3):
+        pos = [(idx[a] + (0.5 if a == c else 0.0)) * d[a] for a in range(3)]
+        F[c] = e[c] * np.cos(k[0] * pos[0] + k[1] * pos[1] + k[2] * pos[2])
+    E0 = F[:3].copy()
+    for _ in range(M):
+        O.yee_step(g, dt, F, solver=solver)
+    lam = kap @ kt
+    w = 2 * np.arcsin(0.5 * dt * np.sqrt(lam)) / dt
+    return F[:3], E0, np.cos(M * w * dt)
+
+
+def pin_ckc_oblique_mode(O):
+    """CKC vacuum dispersion: an oblique mode's E evolves as E0 cos(n w dt) with
+    sin^2(w dt/2) = dt^2 sum_a sin^2(k_a d/2)/d^2 prod_{b != a} cos^2(k_b d/2),
+    at dt = 0.95 dx (beyond the Yee limit dx/sqrt 3)."""
+    n, d = (8, 6, 10), (1.0, 1.0, 1.0)
+    for m_k in ((1, 1, 2), (3, 2, 1), (2, 3, 4)):
+        E, E0, c = _ckc_mode(O, n, d, m_k, 23, 0.95)
+        assert np.max(np.abs(E - c * E0)) < 1e-11, m_k
+
+
+ALL_PINS.append(pin_ckc_oblique_mode)
+
+
+def pin_ckc_stable_at_courant_one(O):
+    """At dt = 0.999 dx a random E (B = 0) stays bounded under CKC for 600
+    steps; the Yee update diverges at the same step.  (B is zero at the start:
+    where the transverse factor vanishes, e.g. k_x = k_y = pi, the CKC curl of
+    E is zero, so B there is frozen and a B seeded there would drive E
+    linearly through the Yee curl; runs start from B = 0 or smooth fields.)"""
+    n = (6, 6, 6)
+    g = O.grid(n)
+    rng = np.random.default_rng(5)
+    F = np.zeros((9,) + n)
+    F[:3] = rng.uniform(-1, 1, size=(3,) + n)
+    G = F.copy()
+    m0 = np.max(np.abs(F[:6]))
+    for _ in range(600):
+        O.yee_step(g, 0.999, F, solver=1)
+    assert np.max(np.abs(F[:6])) < 30 * m0
+    for _ in range(60):
+        O.yee_step(g, 0.999, G, solver=0)
+    assert np.max(np.abs(G[:6])) > 1e6 * m0
+
+
+ALL_PINS.append(pin_ckc_stable_at_courant_one)

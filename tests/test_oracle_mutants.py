@@ -24,6 +24,7 @@ MUTANTS = {
     8: "momentum used as velocity",
     9: "energy-conserving gather keeps order p for E_y",
     10: "Vay without the explicit half of v x B",
+    11: "CKC with box-average weights",
 }
 
 
