@@ -81,6 +81,10 @@ typedef struct {
     double window_speed; /* window speed in units of c, in [0, 1] (window_axis = 2) */
     uint64_t seed;       /* reserved for generators that run inside the library */
     int32_t tile[3];     /* cells per tile per axis (powers of two dividing n); 0 = automatic */
+    int32_t solver;      /* field solver: 0 Yee; 1 CKC (Sec. 4.2: the B update takes each
+                            difference of curl E averaged over the two transverse directions
+                            with weights (1/4, 1/2, 1/4) per direction; cubic cells only;
+                            stable up to dt = dx, so the Courant limit is dx) */
 } pic_grid_desc;
 
 /* Create a context: validates the description (PIC_ERR_ARG, PIC_ERR_CFL),

@@ -427,14 +427,19 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
         C *= D.n[a];
     }
     if (C >= (int64_t(1) << 31) - 1) return fail(PIC_ERR_ARG, "too many cells (limit 2^31 - 2)");
-    const double cfl_dt = 1.0 / std::sqrt(1.0 / (D.d[0] * D.d[0]) + 1.0 / (D.d[1] * D.d[1]) + 1.0 / (D.d[2] * D.d[2]));
+    if (D.solver != 0 && D.solver != 1) return fail(PIC_ERR_ARG, "solver must be 0 (Yee) or 1 (CKC)");
+    if (D.solver == 1 && !(D.d[0] == D.d[1] && D.d[1] == D.d[2]))
+        return fail(PIC_ERR_ARG, "the CKC solver needs cubic cells");
+    const double cfl_dt = D.solver == 1 ? D.d[0]
+                                        : 1.0 / std::sqrt(1.0 / (D.d[0] * D.d[0]) + 1.0 / (D.d[1] * D.d[1]) +
+                                                          1.0 / (D.d[2] * D.d[2]));
     double dt = D.dt;
     if (dt == 0.0) {
         if (!(D.cfl > 0.0 && D.cfl <= 1.0)) return fail(PIC_ERR_ARG, "cfl must be in (0, 1] when dt == 0");
         dt = D.cfl * cfl_dt;
     }
     if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PIC_ERR_ARG, "dt must be finite and > 0");
-    if (dt > cfl_dt) return fail(PIC_ERR_CFL, "dt exceeds the Yee Courant limit 1/sqrt(sum 1/d^2)");
+    if (dt > cfl_dt) return fail(PIC_ERR_CFL, "dt exceeds the Courant limit (Yee 1/sqrt(sum 1/d^2), CKC dx)");
 
     pic_ctx* c = new pic_ctx();
     c->dt = dt;
@@ -486,6 +491,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     g.kbase = 0;
     g.zopen = D.window_axis == 2 ? 1 : 0;
     c->window = D.window_axis == 2;
+    c->solver = D.solver;
     c->window_speed = c->window ? D.window_speed : 0.0;
 
     auto bail = [&](cudaError_t e, const char* what) {
@@ -741,8 +747,8 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (pic_status s = check_ctx(c)) return s;
     if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
     if (c->window) return fail(PIC_ERR_STATE, "the adjoint runs periodic grids only");
-    if (c->pusher || c->egather)
-        return fail(PIC_ERR_STATE, "the adjoint differentiates the Boris push and momentum-conserving gather only");
+    if (c->pusher || c->egather || c->solver)
+        return fail(PIC_ERR_STATE, "the adjoint differentiates Boris, momentum-conserving gather and Yee only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (pic_status s = read_error_word(c)) return s;

@@ -193,6 +193,7 @@ template <typename R> void fill_args(const pic_batch* b, std::vector<char>& host
         }
         Y.step = nullptr;
         Y.zopen = 0;
+        Y.ckc = 0;
         Y.h = R(0.5 * P.dt);
         yb[i] = Y;
         Y.h = R(P.dt);

@@ -94,6 +94,7 @@ struct pic_ctx {
     double* dsum = nullptr;        // diagnostics scratch
     int64_t step = 0;
     double drive_amp = 0.0, drive_k = 0.0;
+    int solver = 0;   // 0 Yee, 1 CKC (B update with the transverse-averaged curl)
     int pusher = 0;   // 0 Boris, 1 Vay
     int egather = 0;  // 0 momentum-conserving, 1 energy-conserving gather
 

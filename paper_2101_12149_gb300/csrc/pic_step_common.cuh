@@ -142,6 +142,7 @@ template <typename R> struct YeeArgs {
     R h;
     long long* step;  // advanced by one thread when non-null
     int zopen;        // no field beyond the z ends
+    int ckc;          // B update with the CKC stencil (cubic cells)
 };
 
 // ---------------------------------------------------------------------------

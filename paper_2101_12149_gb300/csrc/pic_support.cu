@@ -41,6 +41,46 @@ template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>&
     Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
 }
 
+// CKC (Cole-Karkkainen, the solver named for the plasma-acceleration run,
+// Sec. 4.2; cubic cells): the forward difference of F along `axis` at cell
+// (i,j,k), averaged over the two transverse axes with weights (1/4, 1/2, 1/4)
+// per axis.  x, y wrap; z wraps or, with z open, reads zero beyond the ends.
+template <typename R>
+__device__ __forceinline__ R ckc_diff(const YeeArgs<R>& Y, const R* __restrict__ F, int axis, int i, int j, int k) {
+    const int t1 = axis == 0 ? 1 : (axis == 1 ? 2 : 0), t2 = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
+    const R w[3] = {R(0.25), R(0.5), R(0.25)};
+    auto val = [&](int q0, int q1, int q2) -> R {
+        if (Y.zopen && unsigned(q2) >= unsigned(Y.n[2])) return R(0);
+        const int64_t a = wrap_any(q0, Y.n[0]), b = wrap_any(q1, Y.n[1]), cz = wrap_any(q2, Y.n[2]);
+        return F[(a * Y.n[1] + b) * Y.n[2] + cz];
+    };
+    R acc = R(0);
+#pragma unroll
+    for (int a = -1; a <= 1; ++a)
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+            int p0[3] = {i, j, k};
+            p0[t1] += a;
+            p0[t2] += b;
+            int p1[3] = {p0[0], p0[1], p0[2]};
+            p1[axis] += 1;
+            acc += w[a + 1] * w[b + 1] * (val(p1[0], p1[1], p1[2]) - val(p0[0], p0[1], p0[2]));
+        }
+    return acc * Y.inv[axis];
+}
+
+template <typename R> __device__ __forceinline__ void yee_b_ckc_at(const YeeArgs<R>& Y, const int64_t c) {
+    const int k = int(c % Y.n[2]);
+    const int j = int((c / Y.n[2]) % Y.n[1]);
+    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+    const R dEz_dy = ckc_diff(Y, Y.E[2], 1, i, j, k), dEy_dz = ckc_diff(Y, Y.E[1], 2, i, j, k);
+    const R dEx_dz = ckc_diff(Y, Y.E[0], 2, i, j, k), dEz_dx = ckc_diff(Y, Y.E[2], 0, i, j, k);
+    const R dEy_dx = ckc_diff(Y, Y.E[1], 0, i, j, k), dEx_dy = ckc_diff(Y, Y.E[0], 1, i, j, k);
+    Y.B[0][c] -= Y.h * (dEz_dy - dEy_dz);
+    Y.B[1][c] -= Y.h * (dEx_dz - dEz_dx);
+    Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
+}
+
 // E <- E + dt (curl B - J) (backward differences), at cell c.
 template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>& Y, const int64_t c) {
     const int k = int(c % Y.n[2]);
@@ -67,7 +107,10 @@ template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<
     const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (Y.step && c == 0) *Y.step += 1;
-    if (c < C) yee_b_at(Y, c);
+    if (c < C) {
+        if (Y.ckc) yee_b_ckc_at(Y, c);
+        else yee_b_at(Y, c);
+    }
 }
 
 template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
@@ -105,6 +148,7 @@ template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
     Y.h = R(h);
     Y.step = nullptr;
     Y.zopen = c->g.zopen;
+    Y.ckc = c->solver;
     return Y;
 }
 

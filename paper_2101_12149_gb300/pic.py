@@ -38,7 +38,7 @@ class GridDesc(ct.Structure):
     _fields_ = [("n", ct.c_int32 * 3), ("d", ct.c_double * 3), ("dt", ct.c_double), ("cfl", ct.c_double),
                 ("precision", ct.c_int32), ("order", ct.c_int32), ("sort_every", ct.c_int32),
                 ("window_axis", ct.c_int32), ("window_speed", ct.c_double), ("seed", ct.c_uint64),
-                ("tile", ct.c_int32 * 3)]
+                ("tile", ct.c_int32 * 3), ("solver", ct.c_int32)]
 
 
 class BatchTuning(ct.Structure):
@@ -133,7 +133,7 @@ class Context:
     """One PIC simulation: grid, fields and one particle species on one GPU."""
 
     def __init__(self, n, d=(1.0, 1.0, 1.0), dt=0.0, cfl=0.99, precision=FP64, order=1, sort_every=1,
-                 tile=(0, 0, 0), stream=None, window_speed=None):
+                 tile=(0, 0, 0), stream=None, window_speed=None, solver=0):
         self.lib = load_library()
         desc = GridDesc()
         for a in range(3):
@@ -148,6 +148,7 @@ class Context:
         desc.window_axis = -1 if window_speed is None else 2
         desc.window_speed = 0.0 if window_speed is None else float(window_speed)
         desc.seed = 0
+        desc.solver = {"yee": 0, "ckc": 1}[solver] if isinstance(solver, str) else int(solver)
         self.n = tuple(int(v) for v in n)
         self.C = self.n[0] * self.n[1] * self.n[2]
         h = ct.c_void_p()

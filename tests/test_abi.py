@@ -33,13 +33,14 @@ def test_header_struct_layout_matches_binding(tmp_path):
     src = tmp_path / "layout.c"
     src.write_text(
         '#include <stddef.h>\n#include <stdio.h>\n#include "pic.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu\\n\", sizeof(pic_grid_desc),"
-        " offsetof(pic_grid_desc, order), offsetof(pic_grid_desc, seed), offsetof(pic_grid_desc, tile));return 0;}\n")
+        "int main(void){printf(\"%zu %zu %zu %zu %zu\\n\", sizeof(pic_grid_desc),"
+        " offsetof(pic_grid_desc, order), offsetof(pic_grid_desc, seed), offsetof(pic_grid_desc, tile),"
+        " offsetof(pic_grid_desc, solver));return 0;}\n")
     exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     G = pic.GridDesc
-    assert vals == [ct.sizeof(G), G.order.offset, G.seed.offset, G.tile.offset]
+    assert vals == [ct.sizeof(G), G.order.offset, G.seed.offset, G.tile.offset, G.solver.offset]
 
 
 def _init(lib, **kw):
@@ -56,6 +57,7 @@ def _init(lib, **kw):
     d.sort_every = kw.get("sort_every", 1)
     d.window_axis = kw.get("window_axis", -1)
     d.window_speed = kw.get("window_speed", 0.0)
+    d.solver = kw.get("solver", 0)
     h = ct.c_void_p()
     st = lib.pic_init_grid(ct.byref(d), None, ct.byref(h))
     return st, h
@@ -76,6 +78,9 @@ def _init(lib, **kw):
     (dict(window_axis=1), pic.PIC_ERR_ARG),              # only z
     (dict(window_axis=2, sort_every=2), pic.PIC_ERR_ARG),
     (dict(window_axis=2, window_speed=1.5), pic.PIC_ERR_ARG),
+    (dict(solver=2), pic.PIC_ERR_ARG),
+    (dict(solver=1, d=(1.0, 0.9, 1.0)), pic.PIC_ERR_ARG),   # CKC needs cubic cells
+    (dict(solver=1, dt=1.01), pic.PIC_ERR_CFL),              # CKC limit dt = dx
 ])
 def test_invalid_descriptions_rejected_without_gpu(lib, kw, status):
     st, h = _init(lib, **kw)
