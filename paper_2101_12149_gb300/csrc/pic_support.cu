@@ -42,40 +42,54 @@ template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>&
 }
 
 // CKC (Cole-Karkkainen, the solver named for the plasma-acceleration run,
-// Sec. 4.2; cubic cells): the forward difference of F along `axis` at cell
-// (i,j,k), averaged over the two transverse axes with weights (1/4, 1/2, 1/4)
-// per axis.  x, y wrap; z wraps or, with z open, reads zero beyond the ends.
+// Sec. 4.2; cubic cells): the forward difference of F along `axis`, averaged
+// over the two transverse axes with weights (1/4, 1/2, 1/4) per axis.  off[a][m]
+// is the element offset of coordinate (cell + m - 1) along axis a, wrapped
+// periodically; ok[m] is false where that z coordinate lies beyond an open z end
+// (the field there is zero).
 template <typename R>
-__device__ __forceinline__ R ckc_diff(const YeeArgs<R>& Y, const R* __restrict__ F, int axis, int i, int j, int k) {
+__device__ __forceinline__ R ckc_diff(const R* __restrict__ F, int axis, const int64_t off[3][4], const bool ok[4],
+                                      R inv) {
     const int t1 = axis == 0 ? 1 : (axis == 1 ? 2 : 0), t2 = axis == 0 ? 2 : (axis == 1 ? 0 : 1);
     const R w[3] = {R(0.25), R(0.5), R(0.25)};
-    auto val = [&](int q0, int q1, int q2) -> R {
-        if (Y.zopen && unsigned(q2) >= unsigned(Y.n[2])) return R(0);
-        const int64_t a = wrap_any(q0, Y.n[0]), b = wrap_any(q1, Y.n[1]), cz = wrap_any(q2, Y.n[2]);
-        return F[(a * Y.n[1] + b) * Y.n[2] + cz];
-    };
     R acc = R(0);
 #pragma unroll
-    for (int a = -1; a <= 1; ++a)
+    for (int a = 0; a < 3; ++a)
 #pragma unroll
-        for (int b = -1; b <= 1; ++b) {
-            int p0[3] = {i, j, k};
-            p0[t1] += a;
-            p0[t2] += b;
-            int p1[3] = {p0[0], p0[1], p0[2]};
-            p1[axis] += 1;
-            acc += w[a + 1] * w[b + 1] * (val(p1[0], p1[1], p1[2]) - val(p0[0], p0[1], p0[2]));
+        for (int b = 0; b < 3; ++b) {
+            int m0[3], m1[3];
+            m0[axis] = 1, m1[axis] = 2;  // the cell and the next one along the difference
+            m0[t1] = m1[t1] = a;
+            m0[t2] = m1[t2] = b;
+            const R v1 = ok[m1[2]] ? F[off[0][m1[0]] + off[1][m1[1]] + off[2][m1[2]]] : R(0);
+            const R v0 = ok[m0[2]] ? F[off[0][m0[0]] + off[1][m0[1]] + off[2][m0[2]]] : R(0);
+            acc += w[a] * w[b] * (v1 - v0);
         }
-    return acc * Y.inv[axis];
+    return acc * inv;
 }
 
 template <typename R> __device__ __forceinline__ void yee_b_ckc_at(const YeeArgs<R>& Y, const int64_t c) {
     const int k = int(c % Y.n[2]);
     const int j = int((c / Y.n[2]) % Y.n[1]);
     const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
-    const R dEz_dy = ckc_diff(Y, Y.E[2], 1, i, j, k), dEy_dz = ckc_diff(Y, Y.E[1], 2, i, j, k);
-    const R dEx_dz = ckc_diff(Y, Y.E[0], 2, i, j, k), dEz_dx = ckc_diff(Y, Y.E[2], 0, i, j, k);
-    const R dEy_dx = ckc_diff(Y, Y.E[1], 0, i, j, k), dEx_dy = ckc_diff(Y, Y.E[0], 1, i, j, k);
+    const int cc[3] = {i, j, k};
+    const int64_t st[3] = {(int64_t)Y.n[1] * Y.n[2], Y.n[2], 1};
+    int64_t off[3][4];
+    bool ok[4];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            int q = cc[a] + m - 1;  // within one period: n >= 3
+            q = q < 0 ? q + Y.n[a] : (q >= Y.n[a] ? q - Y.n[a] : q);
+            if (q >= Y.n[a]) q -= Y.n[a];
+            off[a][m] = q * st[a];
+        }
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ok[m] = !Y.zopen || unsigned(k + m - 1) < unsigned(Y.n[2]);
+    const R dEz_dy = ckc_diff(Y.E[2], 1, off, ok, Y.inv[1]), dEy_dz = ckc_diff(Y.E[1], 2, off, ok, Y.inv[2]);
+    const R dEx_dz = ckc_diff(Y.E[0], 2, off, ok, Y.inv[2]), dEz_dx = ckc_diff(Y.E[2], 0, off, ok, Y.inv[0]);
+    const R dEy_dx = ckc_diff(Y.E[1], 0, off, ok, Y.inv[0]), dEx_dy = ckc_diff(Y.E[0], 1, off, ok, Y.inv[1]);
     Y.B[0][c] -= Y.h * (dEz_dy - dEy_dz);
     Y.B[1][c] -= Y.h * (dEx_dz - dEz_dx);
     Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
@@ -107,10 +121,16 @@ template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<
     const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (Y.step && c == 0) *Y.step += 1;
-    if (c < C) {
-        if (Y.ckc) yee_b_ckc_at(Y, c);
-        else yee_b_at(Y, c);
-    }
+    if (c < C) yee_b_at(Y, c);
+}
+
+// The B half step with the CKC stencil (a kernel of its own: its register
+// needs must not lower the occupancy of the plain Yee update).
+template <typename R> __global__ void __launch_bounds__(kBlock, 3) k_yee_b_ckc(YeeArgs<R> Y) {
+    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (Y.step && c == 0) *Y.step += 1;
+    if (c < C) yee_b_ckc_at(Y, c);
 }
 
 template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
@@ -431,10 +451,12 @@ cudaError_t launch_rekey(int* key, int64_t n, const Geom& from, const Geom& to, 
 cudaError_t launch_yee_b(pic_ctx* c, double h) {
     if (c->prec == PIC_FP64) {
         auto Y = make_yee<double>(c, h);
-        k_yee_b<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        if (c->solver) k_yee_b_ckc<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        else k_yee_b<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
     } else {
         auto Y = make_yee<float>(c, h);
-        k_yee_b<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        if (c->solver) k_yee_b_ckc<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        else k_yee_b<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
     }
     return cudaGetLastError();
 }
