@@ -161,9 +161,16 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
                                                         int* count, int64_t C, unsigned* err) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int k = -1;
+    // the particle's data is loaded first: these loads do not depend on the
+    // slot, so their latency overlaps the atomic that finds it
+    E v[7];
+    int id = 0;
     if (p < np) {
         k = src.key[p];
         if (k < 0 || k >= C) k = -1;
+#pragma unroll
+        for (int i = 0; i < 7; ++i) v[i] = static_cast<const E*>(src.a[i])[p];
+        id = src.id[p];
     }
     const unsigned mask = __match_any_sync(0xffffffffu, k);
     if (k < 0) return;
@@ -181,9 +188,9 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     }
 #endif
 #pragma unroll
-    for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = static_cast<const E*>(src.a[i])[p];
+    for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = v[i];
     dst.key[dest] = k;
-    dst.id[dest] = src.id[p];
+    dst.id[dest] = id;
 }
 
 size_t scan_status_words(int64_t C) { return size_t((C + kScanChunk - 1) / kScanChunk) + 1; }
