@@ -271,13 +271,18 @@ __global__ void k_diag_fields(const R* const* F, int64_t C, double* out) {
 
 template <typename R>
 __global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out) {
-    double ke = 0.0, ch = 0.0;
+    // gamma - 1 = |u|^2 / (gamma + 1) (no cancellation for slow particles), per
+    // particle in the particles' own precision, summed in FP64
+    double ke = 0.0, sw = 0.0;
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.np;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const double u0 = A.pa[3][p], u1 = A.pa[4][p], u2 = A.pa[5][p], w = A.pa[6][p];
-        ke += w * m * (sqrt(1.0 + u0 * u0 + u1 * u1 + u2 * u2) - 1.0);
-        ch += q * w;
+        const R u0 = A.pa[3][p], u1 = A.pa[4][p], u2 = A.pa[5][p], w = A.pa[6][p];
+        const R uu = u0 * u0 + u1 * u1 + u2 * u2;
+        ke += double(w * (uu / (rsqrt_<R>(R(1) + uu) + R(1))));
+        sw += double(w);
     }
+    ke *= m;
+    double ch = q * sw;
     for (int o = 16; o; o >>= 1) {
         ke += __shfl_down_sync(0xffffffffu, ke, o);
         ch += __shfl_down_sync(0xffffffffu, ch, o);
