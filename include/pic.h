@@ -272,7 +272,9 @@ typedef struct pic_batch pic_batch;
 /* Performance knobs (results are unchanged up to the order of floating-point
  * additions): largest tile extent per axis (powers of two <= 8; each box
  * uses the largest power of two not above it that divides its extent),
- * particles per lane run in the tile kernel (0 = about one cell's worth),
+ * particles per lane run in the tile kernel (0 = automatic: each warp
+ * splits its own group of the tile's cells when the particles are spread
+ * evenly over the groups, else runs of about one cell's worth),
  * sort cadence in steps (>= 1; between sorts particles that left their tile
  * take a slower global-memory path).  Default {8,8,8}, 0, 1. */
 typedef struct {

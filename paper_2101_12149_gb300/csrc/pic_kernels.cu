@@ -356,23 +356,54 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     __syncthreads();
 
     // The tile's particles are cell-sorted; consecutive lanes take consecutive
-    // runs of about one cell's worth of particles, so the lanes of a warp work
-    // in neighbouring cells (distinct shared-memory banks).
+    // runs of them, so the lanes of a warp work in neighbouring cells (distinct
+    // shared-memory banks).  When the tile's cells split evenly over the warps
+    // and the particles are spread evenly enough (no warp's share above 1.25x
+    // the mean + 32), warp w owns the w-th group of cells (one z-row of the
+    // FP32-mixed tile) and its lanes split that group's particles: no two
+    // warps then deposit into the same row at the same time.  Otherwise the
+    // whole tile is cut into runs of about one cell's worth (or A.run).
     const int cnt = end - beg;
-    const int run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
-    const int nrun = (cnt + run - 1) / run;
+    const int lane = threadIdx.x & 31;
+    const int nwarp = blockDim.x >> 5;
+    int wbeg = beg, wend = end, run, nrun, rstart, rstride;
+    bool by_warp = false;
+    if (A.run <= 0 && g.cpt % nwarp == 0 && nwarp <= 32) {
+        const int cpw = g.cpt / nwarp;
+        const int64_t c0 = (int64_t)t * g.cpt;
+        const int gsize = lane < nwarp ? A.offsets[c0 + (int64_t)(lane + 1) * cpw] - A.offsets[c0 + (int64_t)lane * cpw] : 0;
+        const int gmax = __reduce_max_sync(0xffffffffu, gsize);
+        by_warp = int64_t(gmax) * nwarp * 4 <= int64_t(cnt) * 5 + int64_t(128) * nwarp;
+        if (by_warp) {
+            const int wid = threadIdx.x >> 5;
+            wbeg = A.offsets[c0 + (int64_t)wid * cpw];
+            wend = A.offsets[c0 + (int64_t)(wid + 1) * cpw];
+            PIC_CHECK_OR(beg <= wbeg && wbeg <= wend && wend <= end, A.err, 1,
+                         ((long long)wbeg << 32) | unsigned(wend), wbeg = wend = beg);
+        }
+    }
+    if (by_warp) {
+        run = max(1, (wend - wbeg + 31) >> 5);
+        nrun = (wend - wbeg + run - 1) / run;  // at most 32: one pass of the warp
+        rstart = 0;
+        rstride = 32;
+    } else {
+        run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
+        nrun = (cnt + run - 1) / run;
+        rstart = threadIdx.x - lane;
+        rstride = blockDim.x;
+    }
     // Warps step their lanes' runs in lockstep.  A move whose old and new
     // shapes start on the same node along every axis (most moves: crossing a
     // cell face is rare) deposits the narrow stencil at once; the others go to
     // a per-warp queue held one slot per lane in registers and are deposited
     // 32 at a time with the full window, so neither kind runs with idle lanes.
-    const int lane = threadIdx.x & 31;
     TileMove<R> qs = TileMove<R>::zero();  // this lane's queue slot
     int qn = 0;                            // queued moves (warp-uniform)
-    for (int rbase = threadIdx.x - lane; rbase < nrun; rbase += blockDim.x) {
+    for (int rbase = rstart; rbase < nrun; rbase += rstride) {
         const int rr = rbase + lane;
-        const int p0 = beg + rr * run;
-        const int len = rr < nrun ? min(run, end - p0) : 0;
+        const int p0 = wbeg + rr * run;
+        const int len = rr < nrun ? min(run, wend - p0) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
         for (int it = 0; it < maxlen; ++it) {
             const int p = p0 + it;

@@ -186,3 +186,32 @@ def test_positions_at_node_boundaries(precision, p):
     e = c.errors()
     tol = 1e-12 if precision == pic.FP64 else 1e-5
     assert max(e.values()) < tol, e
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+def test_uneven_particle_spread(precision):
+    """Tiles whose particles crowd into one z-row or one cell (the tile kernel
+    then cuts the whole tile into runs) beside evenly filled tiles (each warp
+    takes its own group of cells) deposit like the oracle."""
+    n = (16, 16, 32)
+    base = inputs.uniform_plasma(81, n, 2, sigma_u=0.3)
+    r = inputs.uniform(82, 0, 3 * 2500, 0).reshape(3, 2500)
+    row = {"x": 5 + r[0, :2000], "y": 6 + r[1, :2000], "z": 32 * r[2, :2000]}       # one z-row of cells
+    cell = {"x": 9 + r[0, 2000:], "y": 2 + r[1, 2000:], "z": 20 + r[2, 2000:]}      # one cell
+    u = 0.3 * (2 * inputs.uniform(83, 0, 3 * 2500, 0).reshape(3, 2500) - 1)
+    parts = {}
+    for k in ("x", "y", "z"):
+        parts[k] = np.concatenate([base[k], row[k], cell[k]])
+    for a, k in enumerate(("ux", "uy", "uz")):
+        parts[k] = np.concatenate([base[k], u[a]])
+    parts["w"] = np.concatenate([base["w"], np.full(2500, base["w"][0])])
+    parts = {k: np.ascontiguousarray(v, dtype=np.float64) for k, v in parts.items()}
+    c = Case(n, 3, 1, 0.0, 84, precision=precision)
+    c.parts = parts
+    c.ref = {k: v.copy() for k, v in parts.items()}
+    c.ctx.load_particles(c.q, c.m, parts)
+    c.ctx.step(2)
+    c.oracle_steps(2)
+    e = c.errors()
+    tol = 1e-12 if precision == pic.FP64 else 1e-5
+    assert max(e.values()) < tol, e
