@@ -14,6 +14,7 @@ box): value = all ranks' particle-steps / the slowest rank's time.
 """
 import argparse
 import hashlib
+import re
 import json
 import os
 import subprocess
@@ -66,12 +67,16 @@ def measured_peaks():
 
 
 def kernel_source_hash():
-    """Hash of the sources the tile kernel is built from (its DRAM counters in
-    profiles/ hold only while this matches)."""
+    """Hash of the code (comments and layout stripped) of the sources the tile
+    kernel is built from: its DRAM counters in profiles/ hold only while
+    this matches."""
     h = hashlib.sha256()
     for f in ("pic_kernels.cu", "pic_device.cuh", "pic_step_common.cuh"):
-        with open(os.path.join(ROOT, "paper_2101_12149_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2101_12149_gb300", "csrc", f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
@@ -396,6 +401,77 @@ def wakefield_statement(torch, steps_cmp=50, steps_fp32=150):
     return res
 
 
+def sort_study_statement(torch, stream, parts, n, steps32=8, steps64=4):
+    """The sort-interval x bin-size study and the shared-vs-global deposit
+    ablation (Sec. 3.4.2, 4.1.1) on the uniform-plasma workload (fields and
+    particles far larger than L2): ms per step of (a) the fused tile kernel
+    sorting by cell every k steps (between sorts the particles that left
+    their tile take the global-atomic outsider path), (b) the split path of
+    the paper's GPU design (gather+push kernel, then a deposit kernel with
+    global atomics) from a random particle order, never re-sorted or
+    re-sorted every k steps by bins of 2^s consecutive tile-major cells, and
+    from cell order never re-sorted.  Each configuration: 2 untimed steps,
+    then the timed steps with CUDA events on the launching stream (sorts
+    included)."""
+    from paper_2101_12149_gb300 import inputs, pic
+    w = inputs.WORKLOADS[WORKLOAD]
+    dev = {k: torch.from_numpy(v).to(torch.cuda.current_device()) for k, v in parts.items()}
+    N = parts["x"].size
+    res = {"grid": "x".join(str(v) for v in n), "particles": N, "order": w["order"], "ppc": w["ppc"]}
+
+    def timed(body, steps):
+        for s_ in range(2):
+            body(s_)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for s_ in range(steps):
+            body(s_ + 2)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    def split_body(ctx, every, shift):
+        def body(s_):
+            if every and s_ % every == 0:
+                ctx.sort_particles(shift)
+            ctx.gather_push()
+            ctx.deposit()
+            ctx.yee_step()
+        return body
+
+    for prec, name, steps in ((pic.FP32_MIXED, "fp32_mixed", steps32), (pic.FP64, "fp64", steps64)):
+        r = {}
+        everies = (1, 2, 4, 8, 16) if prec == pic.FP32_MIXED else (1, 4)
+        for k in everies:
+            with pic.Context(n, cfl=w["cfl"], order=w["order"], precision=prec, sort_every=k, stream=stream) as ctx:
+                ctx.load_particles(-1.0, 1.0, dev)
+                r[f"fused, cell sort every {k}"] = timed(lambda s_: ctx.step(1), steps)
+        split = [(0, None)] + ([(k, sh) for k in (1, 4, 16) for sh in (0, 5, 9, 12)] if prec == pic.FP32_MIXED
+                                 else [(1, 0), (1, 5)])
+        for start in ("random", "cell"):
+            for every, shift in split:
+                if start == "cell" and every:
+                    continue
+                with pic.Context(n, cfl=w["cfl"], order=w["order"], precision=prec, stream=stream) as ctx:
+                    ctx.load_particles(-1.0, 1.0, dev)
+                    if start == "random":
+                        ctx.sort_particles(pic.ORDER_RANDOM)
+                    key = (f"split, {start} start, " +
+                           (f"bins of 2^{shift} cells every {every}" if every else "never re-sorted"))
+                    r[key] = timed(split_body(ctx, every, shift), steps)
+        r = {k: round(v, 3) for k, v in r.items()}
+        best_split = min(v for k, v in r.items() if k.startswith("split"))
+        res[name] = {"steps": steps, "ms_per_step": r,
+                     "split_random_never_over_best_split": r["split, random start, never re-sorted"] / best_split,
+                     "global_over_shared_deposit_sorted_every_step":
+                         r["split, random start, bins of 2^0 cells every 1"] / r["fused, cell sort every 1"]}
+    del dev
+    torch.cuda.empty_cache()
+    return res
+
+
 def adjoint_statement(torch):
     """The differentiation workload: 64^3, 4 ppc, order 2, drive A from seed 4,
     200 steps with checkpoints every 20; forward + checkpointed reverse timed
@@ -583,6 +659,7 @@ def main():
         if rank == 0:
             line["ensemble"] = ensemble_statement(torch, stream)
             line["adjoint"] = adjoint_statement(torch)
+            line["sort_study"] = sort_study_statement(torch, stream, host, n)
             line["wakefield"] = wakefield_statement(torch)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline()

@@ -119,6 +119,23 @@ pic_status pic_deposit(pic_ctx* ctx);
 /* Yee update with the current J: B half step, E full step, B half step. */
 pic_status pic_yee_step(pic_ctx* ctx);
 
+/* Reorder the particles now with the counting sort (Sec. 3.4.2 bins the
+ * particles by cell and reorders their data; the paper sweeps the bin size
+ * and the sort interval).  bin_shift = 0: by cell, in tile-major cell order
+ * (the order pic_step keeps); bin_shift in 1..30: by bins of 2^bin_shift
+ * consecutive tile-major cells, in no set order within a bin;
+ * PIC_ORDER_RANDOM (-1): a pseudo-random order (bins drawn from the particle
+ * id, pic_grid_desc.seed and a per-context call counter; the paper has no
+ * such call: it stands for the state of a long run without sorting).  With
+ * the split API the caller chooses the bins and the cadence.  After anything
+ * but a cell sort, the next pic_step or pic_step_adjoint first sorts by cell.
+ * Physics is unchanged (results up to the order of floating-point additions);
+ * a pic_gather_push not yet followed by pic_deposit is dropped.
+ * PIC_ERR_ARG if bin_shift is outside [-1, 30]; PIC_ERR_STATE for a
+ * moving-window context. */
+enum { PIC_ORDER_RANDOM = -1 };
+pic_status pic_sort_particles(pic_ctx* ctx, int32_t bin_shift);
+
 /* nsteps full PIC steps: counting sort (at the sort cadence), fused tile
  * kernel (gather + push + advance + Esirkepov into shared memory, one flush
  * per tile), Yee update.  Checks the device error word at the end.

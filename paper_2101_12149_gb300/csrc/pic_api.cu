@@ -51,6 +51,7 @@ void free_particles(pic_ctx* c) {
     cudaFree(c->old[0]);
     for (auto& o : c->old) o = nullptr;
     c->oldkey = nullptr;
+    c->sortbin = nullptr;
     c->outl = nullptr;
     c->np = c->cap = 0;
     c->have_old = false;
@@ -76,6 +77,7 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
     if (e != cudaSuccess) return e;
     for (int i = 0; i < 6; ++i) c->old[i] = ob + i * per;
     c->oldkey = reinterpret_cast<int*>(ob + 6 * per);
+    c->sortbin = c->oldkey;  // pic_sort_particles ends any split-API step, so the two never overlap
     c->outl = reinterpret_cast<int*>(ob + 6 * per + ints);
     c->cap = int64_t(cap);
     return cudaSuccess;
@@ -169,6 +171,17 @@ cudaError_t run_sort(pic_ctx* c) {
     if ((e = counted(c, "k_scan", 1, pic::launch_scan)) != cudaSuccess) return e;
     if ((e = counted(c, "k_scatter", 1, pic::launch_scatter)) != cudaSuccess) return e;
     c->cur = 1 - c->cur;
+    return cudaSuccess;
+}
+
+// The tile kernel needs the particles in tile order of the current offsets;
+// after pic_sort_particles with coarse or random bins they are not.
+cudaError_t ensure_tile_order(pic_ctx* c) {
+    if (c->sorted || c->np == 0) return cudaSuccess;
+    cudaError_t e = run_sort(c);
+    if (e != cudaSuccess) return e;
+    c->sorted = true;
+    c->since_sort = 0;
     return cudaSuccess;
 }
 
@@ -446,6 +459,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     c->prec = D.precision;
     c->order = D.order;
     c->sort_every = D.sort_every;
+    c->seed = D.seed;
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->rsize = D.precision == PIC_FP64 ? 8 : 4;
     cudaGetDevice(&c->device);
@@ -679,6 +693,28 @@ pic_status pic_deposit(pic_ctx* c) {
     return PIC_OK;
 }
 
+pic_status pic_sort_particles(pic_ctx* c, int32_t bin_shift) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (bin_shift < -1 || bin_shift > 30) return fail(PIC_ERR_ARG, "bin_shift must be in [-1, 30]");
+    if (c->window) return fail(PIC_ERR_STATE, "a moving-window context keeps its own sort");
+    c->have_old = false;
+    if (c->np == 0) return PIC_OK;
+    if (bin_shift == 0) {
+        PIC_CUDA(run_sort(c));
+        c->sorted = true;
+        c->since_sort = 0;
+        return PIC_OK;
+    }
+    c->sort_shift = bin_shift;
+    cudaError_t e = counted(c, "k_bin_keys", 1, pic::launch_bin_keys);
+    if (e == cudaSuccess) e = run_sort(c);
+    c->sort_shift = 0;
+    if (bin_shift < 0) c->reorders += 1;
+    PIC_CUDA(e);
+    c->sorted = false;
+    return PIC_OK;
+}
+
 pic_status pic_yee_step(pic_ctx* c) {
     if (pic_status s = check_ctx(c)) return s;
     PIC_CUDA(run_yee(c));
@@ -692,6 +728,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (nsteps < 0) return fail(PIC_ERR_ARG, "nsteps < 0");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     int32_t left = nsteps;
+    if (nsteps > 0) PIC_CUDA(ensure_tile_order(c));
     if (c->window) {
         for (; left > 0; --left)
             if (pic_status s = run_window_step(c)) return s;
@@ -750,6 +787,7 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (c->pusher || c->egather || c->solver)
         return fail(PIC_ERR_STATE, "the adjoint differentiates Boris, momentum-conserving gather and Yee only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
+    PIC_CUDA(ensure_tile_order(c));
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (pic_status s = read_error_word(c)) return s;
     const int k = ckpt_every;

@@ -88,6 +88,12 @@ struct pic_ctx {
     int scan_chunks = 0;
     bool sorted = false;       // particles are in tile order of the current offsets
     int since_sort = 0;
+    // sort bins: 0 = cells (the step's sort); > 0 = runs of 2^sort_shift
+    // consecutive tile-major cells; -1 = pseudo-random bins (pic_sort_particles)
+    int sort_shift = 0;
+    int* sortbin = nullptr;    // bin of each particle when sort_shift != 0 [cap]
+    uint64_t seed = 0;
+    int64_t reorders = 0;      // pic_sort_particles calls with random bins so far
 
     unsigned* err = nullptr;       // device error word [4] + outsider count [1] (8 words allocated)
     long long* d_step = nullptr;   // device copy of the step counter (drive time)
@@ -138,6 +144,8 @@ cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
 // below z = 0 die), then fill the front slab with plasma at slots [np, np + nx*ny*ppc)
 cudaError_t launch_window_shift(pic_ctx* c);
 cudaError_t launch_inject(pic_ctx* c);
+// bins of pic_sort_particles (sort_shift != 0) into sortbin (pic_sort.cu)
+cudaError_t launch_bin_keys(pic_ctx* c);
 
 // adjoint (pic_adjoint.cu)
 // Work buffers of the reverse sweep: adjoints of positions (cell units) and

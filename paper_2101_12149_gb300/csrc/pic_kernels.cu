@@ -36,11 +36,10 @@ namespace pic {
 //   J box:   x, y [-2, T+3), z [-4, T+4), z rows of pitch JP (z padded so the
 //            flush moves aligned float4s)
 // Two layouts.  4 x 4 x 32 when nz is a multiple of 32: the lanes of a warp
-// take 32 consecutive cells in tile order (one z-row, or the end of one and
-// the start of the next), and with row and plane pitches that are multiples
-// of 32 words the bank of every access is its z index, so gathers and
-// deposits hit 32 distinct banks whatever the per-lane staggering offsets.
-// Otherwise up to 8 x 8 x 8 cells.
+// take the particles of one z-row of 32 cells (tile_body), and with row and
+// plane pitches that are multiples of 32 words the bank of every access is
+// its z index, so lanes in distinct cells hit distinct banks whatever their
+// staggering offsets along x and y.  Otherwise up to 8 x 8 x 8 cells.
 template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
     static constexpr int EX = MX + 4, EY = MY + 4, EZ = MZ + 4;
     static constexpr int eY = EP, eX = EY * EP, eVol = EX * EY * EP;

@@ -11,6 +11,8 @@
 //  k_scatter  each particle takes a slot in its cell's range by decrementing
 //             count (warp-aggregated), then all its arrays move to the other
 //             buffer.  count returns to zero, ready for the next histogram.
+//  k_bin_keys pic_sort_particles only: coarse (runs of cells) or random bins
+//             for the same three kernels; the cell key moves as data.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -156,17 +158,22 @@ __global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ cou
     }
 }
 
+// `bin` is the array of sort bins: the cell keys themselves (the step's
+// sort) or the bins of pic_sort_particles; the cell key always moves with
+// the particle.
 template <typename E>
-__global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst, int64_t np, const int* offsets,
-                                                        int* count, int64_t C, unsigned* err) {
+__global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst, const int* __restrict__ bin,
+                                                        int64_t np, const int* offsets, int* count, int64_t C,
+                                                        unsigned* err) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int k = -1;
+    int k = -1, key = 0;
     // the particle's data is loaded first: these loads do not depend on the
     // slot, so their latency overlaps the atomic that finds it
     E v[7];
     int id = 0;
     if (p < np) {
-        k = src.key[p];
+        k = bin[p];
+        key = bin == src.key ? k : src.key[p];
         if (k < 0 || k >= C) k = -1;
 #pragma unroll
         for (int i = 0; i < 7; ++i) v[i] = static_cast<const E*>(src.a[i])[p];
@@ -189,19 +196,57 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
 #endif
 #pragma unroll
     for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = v[i];
-    dst.key[dest] = k;
+    dst.key[dest] = key;
     dst.id[dest] = id;
+}
+
+// SplitMix64 output function (Steele, Lea & Flood 2014): a bijective 64-bit mixer.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Bins of pic_sort_particles: shift > 0, the cell key's run of 2^shift
+// consecutive tile-major cells; shift < 0, a pseudo-random bin in [0, nb)
+// from the particle id, the seed and the call counter.
+__global__ void __launch_bounds__(kSortBlock) k_bin_keys(const int* __restrict__ key, const int* __restrict__ id,
+                                                         int64_t np, int shift, uint64_t seed, uint64_t ctr,
+                                                         int64_t nb, int* bin) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= np) return;
+    if (shift > 0) {
+        bin[p] = key[p] >> shift;
+    } else {
+        const uint64_t h = splitmix64(seed ^ splitmix64(uint64_t(uint32_t(id[p])) | (ctr << 32)));
+        bin[p] = int(((h >> 32) * uint64_t(nb)) >> 32);
+    }
 }
 
 size_t scan_status_words(int64_t C) { return size_t((C + kScanChunk - 1) / kScanChunk) + 1; }
 
-// Bins of the sort: one per cell, plus one for removed particles when z is open.
-static int64_t nbins(const pic_ctx* c) { return c->g.C + (c->g.zopen ? 1 : 0); }
+// Bins of the sort: one per cell, plus one for removed particles when z is
+// open; with pic_sort_particles' coarse bins one per run of 2^sort_shift
+// cells, with its random bins one per cell.
+static int64_t nbins(const pic_ctx* c) {
+    if (c->sort_shift > 0) return ((c->g.C - 1) >> c->sort_shift) + 1;
+    return c->g.C + (c->g.zopen ? 1 : 0);
+}
+static const int* bins(const pic_ctx* c) { return c->sort_shift == 0 ? c->P[c->cur].key : c->sortbin; }
+
+cudaError_t launch_bin_keys(pic_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
+    k_bin_keys<<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur].key, c->P[c->cur].id, c->np, c->sort_shift, c->seed,
+                                                 uint64_t(c->reorders), nbins(c), c->sortbin);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_hist(pic_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
-    k_hist<<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur].key, c->np, c->count, nbins(c), c->err);
+    k_hist<<<nb, kSortBlock, 0, c->stream>>>(bins(c), c->np, c->count, nbins(c), c->err);
     return cudaGetLastError();
 }
 
@@ -218,11 +263,11 @@ cudaError_t launch_scatter(pic_ctx* c) {
     if (c->np == 0) return cudaSuccess;
     const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
     if (c->prec == PIC_FP64)
-        k_scatter<double><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                            c->count, nbins(c), c->err);
+        k_scatter<double><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], bins(c), c->np,
+                                                            c->offsets, c->count, nbins(c), c->err);
     else
-        k_scatter<float><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], c->np, c->offsets,
-                                                           c->count, nbins(c), c->err);
+        k_scatter<float><<<nb, kSortBlock, 0, c->stream>>>(c->P[c->cur], c->P[1 - c->cur], bins(c), c->np,
+                                                           c->offsets, c->count, nbins(c), c->err);
     return cudaGetLastError();
 }
 

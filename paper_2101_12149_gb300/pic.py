@@ -21,6 +21,7 @@ PIC_OK, PIC_ERR_ARG, PIC_ERR_CFL, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_STATE, PIC_
 STATUS_NAMES = {0: "PIC_OK", 1: "PIC_ERR_ARG", 2: "PIC_ERR_CFL", 3: "PIC_ERR_OOM", 4: "PIC_ERR_CUDA",
                 5: "PIC_ERR_STATE", 6: "PIC_ERR_PARTICLE", 7: "PIC_ERR_TIMEOUT"}
 FP64, FP32_MIXED = 0, 1
+ORDER_RANDOM = -1
 FIELDS = ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Jx", "Jy", "Jz")
 PARTICLE_KEYS = ("x", "y", "z", "ux", "uy", "uz", "w")
 
@@ -61,6 +62,7 @@ def load_library(path: str = LIB_PATH):
             "pic_gather_push": [P],
             "pic_deposit": [P],
             "pic_yee_step": [P],
+            "pic_sort_particles": [P, I32],
             "pic_step": [P, I32],
             "pic_step_adjoint": [P, I32, I32, P, P, P, ct.c_int],
             "pic_set_window_plasma": [P, I32, D, D, D],
@@ -133,7 +135,7 @@ class Context:
     """One PIC simulation: grid, fields and one particle species on one GPU."""
 
     def __init__(self, n, d=(1.0, 1.0, 1.0), dt=0.0, cfl=0.99, precision=FP64, order=1, sort_every=1,
-                 tile=(0, 0, 0), stream=None, window_speed=None, solver=0):
+                 tile=(0, 0, 0), stream=None, window_speed=None, solver=0, seed=0):
         self.lib = load_library()
         desc = GridDesc()
         for a in range(3):
@@ -147,7 +149,7 @@ class Context:
         desc.sort_every = int(sort_every)
         desc.window_axis = -1 if window_speed is None else 2
         desc.window_speed = 0.0 if window_speed is None else float(window_speed)
-        desc.seed = 0
+        desc.seed = int(seed)
         desc.solver = {"yee": 0, "ckc": 1}[solver] if isinstance(solver, str) else int(solver)
         self.n = tuple(int(v) for v in n)
         self.C = self.n[0] * self.n[1] * self.n[2]
@@ -210,6 +212,11 @@ class Context:
 
     def yee_step(self):
         _check(self.lib.pic_yee_step(self.h))
+
+    def sort_particles(self, bin_shift=0):
+        """Reorder the particles: by cell (0), by runs of 2**bin_shift cells,
+        or in a pseudo-random order (ORDER_RANDOM)."""
+        _check(self.lib.pic_sort_particles(self.h, int(bin_shift)))
 
     def step(self, nsteps=1):
         _check(self.lib.pic_step(self.h, int(nsteps)))
