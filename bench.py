@@ -554,15 +554,20 @@ def main():
     head_prec = pic.FP32_MIXED if args.precision == "fp32" else pic.FP64
     ctx = make_ctx(head_prec)
     ctx.step(args.warmup)
-    ctx.set_timing(True)
     l0 = ctx.launch_count()
     uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid) if hasattr(
         torch.cuda.get_device_properties(local), "uuid") else str(local)
     if dist:
         dist.barrier()
+    # the timed steps run as the library runs them (pairs of steps replayed as
+    # one CUDA graph, no per-kernel events)
     with ClockSampler(uuid) as clk:
         t = timed_run(ctx, args.steps, stream, torch)
     launches = ctx.launch_count() - l0
+    # per-kernel times: the same number of steps again, with CUDA events around
+    # every kernel on the launching stream
+    ctx.set_timing(True)
+    t_evented = timed_run(ctx, args.steps, stream, torch)
     timings = ctx.get_timing()
     ctx.set_timing(False)
     t = max_over_ranks(t, dist, f"cuda:{local}")
@@ -602,6 +607,7 @@ def main():
         "roofline": roof_alu if (alu_frac or 0) >= (hbm_frac or 0) else roof_hbm,
         "roofline_alt": roof_hbm if (alu_frac or 0) >= (hbm_frac or 0) else roof_alu,
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
+        "ms_per_step_with_kernel_events": 1e3 * t_evented / args.steps,
         "kernel_share": {k: v[0] / max(sum(x[0] for x in timings.values()), 1e-30) for k, v in timings.items()},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
@@ -613,12 +619,17 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ctx2 = pic.Context(n, cfl=w["cfl"], order=order, precision=pic.FP32_MIXED, stream=stream)
+        t1 = time.perf_counter()
         ctx2.load_particles(-1.0, 1.0, host)
+        t2 = time.perf_counter()
         for _ in range(e2e_steps):
             ctx2.step(1)
             ctx2.diagnostics()
+        t3 = time.perf_counter()
         ex = ctx2.get_field("Ex")
         t_e2e = time.perf_counter() - t0
+        phases = {"create": t1 - t0, "load": t2 - t1, "steps_with_diagnostics": t3 - t2,
+                  "field_readback": t0 + t_e2e - t3}
         ctx2.close()
         h2d = 7 * 8 * N
         d2h = e2e_steps * 4 * 8 + ex.nbytes
@@ -626,7 +637,8 @@ def main():
         line["e2e"] = {"value": job_throughput(world, N, e2e_steps, t_e2e), "unit": UNIT,
                        "h2d_bytes_per_step": h2d // e2e_steps, "d2h_bytes_per_step": d2h // e2e_steps,
                        "what": "context creation + pic_load_particles from pinned host FP64 arrays + "
-                               f"{e2e_steps} x (pic_step + pic_diagnostics read-back) + E_x field read-back"}
+                               f"{e2e_steps} x (pic_step + pic_diagnostics read-back) + E_x field read-back",
+                       "phases_s": {k: round(v, 4) for k, v in phases.items()}}
         # ---- FP64 on the same workload -----------------------------------
         ctx64 = make_ctx(pic.FP64)
         ctx64.step(1)

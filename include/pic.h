@@ -98,6 +98,10 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
  * momenta ux,uy,uz = gamma v at t = -dt/2, weights w (FP64 arrays of n).
  * Replaces any previous particles, allocates the particle buffers for n,
  * assigns ids 0..n-1 in input order and sorts the particles by cell.
+ * on_device = 0: host arrays; when all seven are in pinned (page-locked,
+ * device-mapped) memory the load kernel reads them directly over the host
+ * link, otherwise they pass through a device staging buffer of at most
+ * 2^23 particles at a time.  Returns when the load is complete.
  * PIC_ERR_ARG if n < 0 or n >= 2^31, a pointer is NULL with n > 0, or a
  * value is non-finite. */
 pic_status pic_load_particles(pic_ctx* ctx, double q, double m, int64_t n,

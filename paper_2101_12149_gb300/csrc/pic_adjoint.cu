@@ -45,7 +45,7 @@ __device__ __forceinline__ void boris_adj(R k, const R E[3], const R B[3], const
     R um[3], t[3], s[3], up[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) um[a] = u_old[a] + k * E[a];
-    const R gm = rsqrt_<R>(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
+    const R gm = sqrt_<R>(R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2]);
 #pragma unroll
     for (int a = 0; a < 3; ++a) t[a] = k * B[a] / gm;
     const R tt = t[0] * t[0] + t[1] * t[1] + t[2] * t[2];
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(kAdjBlock) k_adj_particles(StepArgs<R> A, AdjA
         }
         // ---- advance: f1 = f0 + (dt/d) u / gamma ------------------------
         {
-            const R gam = rsqrt_<R>(R(1) + mv.u[0] * mv.u[0] + mv.u[1] * mv.u[1] + mv.u[2] * mv.u[2]);
+            const R gam = sqrt_<R>(R(1) + mv.u[0] * mv.u[0] + mv.u[1] * mv.u[1] + mv.u[2] * mv.u[2]);
             R sdot = R(0);
 #pragma unroll
             for (int a = 0; a < 3; ++a) {

@@ -588,26 +588,50 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
     c->np = n;
     c->cur = 0;
     c->have_old = false;
-    double* staged = nullptr;
-    const double* dsrc[7];
-    if (n > 0 && !on_device) {
-        PIC_CUDA(cudaMalloc(&staged, 7 * size_t(n) * sizeof(double)));
-        for (int i = 0; i < 7; ++i) {
-            cudaError_t e = cudaMemcpyAsync(staged + i * n, src[i], n * sizeof(double), cudaMemcpyHostToDevice,
-                                            c->stream);
-            if (e != cudaSuccess) {
-                cudaFree(staged);
-                return cuda_fail(e, "particle upload");
-            }
-            dsrc[i] = staged + i * n;
-        }
-    } else {
-        for (int i = 0; i < 7; ++i) dsrc[i] = src[i];
-    }
     PIC_CUDA(cudaMemsetAsync(c->err, 0, 8 * sizeof(unsigned), c->stream));
     clear_stale("k_load");
-    cudaError_t e = pic::launch_load_particles(c, dsrc, n);
-    if (e == cudaSuccess) c->launches += n > 0 ? 1 : 0;
+    // Host arrays in pinned (page-locked, mapped) memory are read by the load
+    // kernel itself over the host link; other host memory goes through a
+    // device staging buffer of at most 2^23 particles, one chunk at a time.
+    double* staged = nullptr;
+    cudaError_t e = cudaSuccess;
+    int64_t loads = 0;
+    if (n > 0 && !on_device) {
+        const double* mapped[7];
+        bool all_mapped = true;
+        for (int i = 0; i < 7 && all_mapped; ++i) {
+            cudaPointerAttributes at;
+            if (cudaPointerGetAttributes(&at, src[i]) != cudaSuccess) {
+                cudaGetLastError();
+                all_mapped = false;
+            } else {
+                all_mapped = at.type == cudaMemoryTypeHost && at.devicePointer != nullptr;
+                mapped[i] = static_cast<const double*>(at.devicePointer);
+            }
+        }
+        if (all_mapped) {
+            e = pic::launch_load_particles(c, mapped, n, 0);
+            loads = 1;
+        } else {
+            const int64_t chunk = std::min<int64_t>(n, int64_t(1) << 23);
+            e = cudaMalloc(&staged, 7 * size_t(chunk) * sizeof(double));
+            for (int64_t b0 = 0; e == cudaSuccess && b0 < n; b0 += chunk) {
+                const int64_t cnt = std::min(chunk, n - b0);
+                const double* part[7];
+                for (int i = 0; i < 7 && e == cudaSuccess; ++i) {
+                    e = cudaMemcpyAsync(staged + i * chunk, src[i] + b0, size_t(cnt) * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream);
+                    part[i] = staged + i * chunk;
+                }
+                if (e == cudaSuccess) e = pic::launch_load_particles(c, part, cnt, b0);
+                loads += 1;
+            }
+        }
+    } else {
+        e = pic::launch_load_particles(c, src, n, 0);
+        loads = n > 0 ? 1 : 0;
+    }
+    if (e == cudaSuccess) c->launches += loads;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (staged) cudaFree(staged);
     if (e != cudaSuccess) return cuda_fail(e, n > 0 ? "particle load kernel" : "particle load");

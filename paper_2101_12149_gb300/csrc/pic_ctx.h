@@ -135,7 +135,8 @@ cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);
 cudaError_t launch_yee_e(pic_ctx* c);
 cudaError_t launch_step_counter(pic_ctx* c);
-cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n);
+// particles [base, base + n) from arrays that start at particle base
+cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n, int64_t base = 0);
 cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id);
 cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst);
 cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src);

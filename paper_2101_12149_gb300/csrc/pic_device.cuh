@@ -52,9 +52,9 @@ template <typename R> __device__ __forceinline__ R rfloor(R v);
 template <> __device__ __forceinline__ double rfloor<double>(double v) { return floor(v); }
 template <> __device__ __forceinline__ float rfloor<float>(float v) { return floorf(v); }
 
-template <typename R> __device__ __forceinline__ R rsqrt_(R v);
-template <> __device__ __forceinline__ double rsqrt_<double>(double v) { return sqrt(v); }
-template <> __device__ __forceinline__ float rsqrt_<float>(float v) { return sqrtf(v); }
+template <typename R> __device__ __forceinline__ R sqrt_(R v);
+template <> __device__ __forceinline__ double sqrt_<double>(double v) { return sqrt(v); }
+template <> __device__ __forceinline__ float sqrt_<float>(float v) { return sqrtf(v); }
 
 // ---------------------------------------------------------------------------
 // Order-P cardinal B-spline weights.
@@ -201,7 +201,7 @@ __device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
         um[1] = R(umd[1]);
         um[2] = R(umd[2]);
     } else {
-        boris_rotate<R>(k, B, um, rsqrt_<R>(g2));
+        boris_rotate<R>(k, B, um, sqrt_<R>(g2));
     }
     u[0] = um[0] + k * E[0];
     u[1] = um[1] + k * E[1];
@@ -223,7 +223,7 @@ __device__ __forceinline__ void vay_core(T kq, const T B[3], const T up[3], T u[
     const T tau2 = tau[0] * tau[0] + tau[1] * tau[1] + tau[2] * tau[2];
     const T ustar = up[0] * tau[0] + up[1] * tau[1] + up[2] * tau[2];
     const T sigma = T(1) + up[0] * up[0] + up[1] * up[1] + up[2] * up[2] - tau2;
-    const T gnew = rsqrt_<T>(T(0.5) * (sigma + rsqrt_<T>(sigma * sigma + T(4) * (tau2 + ustar * ustar))));
+    const T gnew = sqrt_<T>(T(0.5) * (sigma + sqrt_<T>(sigma * sigma + T(4) * (tau2 + ustar * ustar))));
     const T t[3] = {tau[0] / gnew, tau[1] / gnew, tau[2] / gnew};
     const T s = T(1) / (T(1) + t[0] * t[0] + t[1] * t[1] + t[2] * t[2]);
     const T ut = up[0] * t[0] + up[1] * t[1] + up[2] * t[2];
@@ -234,7 +234,7 @@ __device__ __forceinline__ void vay_core(T kq, const T B[3], const T up[3], T u[
 
 template <typename R>
 __device__ __forceinline__ void vay(R kq, const R E[3], const R B[3], R u[3]) {
-    const R g0 = rsqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const R g0 = sqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const R v[3] = {u[0] / g0, u[1] / g0, u[2] / g0};
     R up[3];
     up[0] = u[0] + R(2) * kq * E[0] + kq * (v[1] * B[2] - v[2] * B[1]);

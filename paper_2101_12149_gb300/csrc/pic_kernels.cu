@@ -301,6 +301,16 @@ template <typename R> struct TileMove {
     }
 };
 
+// A fixed-point node sum hi 2^15 + lo (|hi| < 2^31, 0 <= lo < 2^31, as the
+// deposit accumulates them) rounded once to float, in FP32 arithmetic: with
+// the carry of lo moved into hi both parts are exact floats, and one fused
+// multiply-add rounds the exact sum.  Sums of 2^38 and more take the 64-bit
+// conversion.
+__device__ __forceinline__ float fixed_to_float(int hi, int lo) {
+    if (hi > -(1 << 23) && hi < (1 << 23)) return fmaf(float(hi + (lo >> 15)), 32768.0f, float(lo & 0x7fff));
+    return __ll2float_rn((long long)hi * 32768 + lo);
+}
+
 // Block size of the tile kernel: FP32-mixed 512 threads (one CTA per SM, its
 // shared memory holding the fixed-point J box), FP64 256.
 template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
@@ -404,15 +414,20 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
         const int p0 = wbeg + rr * run;
         const int len = rr < nrun ? min(run, wend - p0) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
+        // the next particle's loads are issued before the current one's work
+        RawParticle<R> next;
+        if (len > 0) load_raw<R>(A, p0, next);
         for (int it = 0; it < maxlen; ++it) {
             const int p = p0 + it;
             bool wide = false;
             TileMove<R> mine = TileMove<R>::zero();
+            const RawParticle<R> raw = next;
+            if (it + 1 < len) load_raw<R>(A, p + 1, next);
             if (it < len) {
                 int cell[3];
                 R f0[3], u[3], wq;
                 double xg0[3];
-                load_particle<R>(A, p, cell, f0, xg0, u, wq);
+                decode_particle<R>(A, raw, cell, f0, xg0, u, wq);
                 const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
                 // the fixed-point sums are exact for up to 65535 particles per tile
                 const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
@@ -496,10 +511,10 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             const int4 lo = *reinterpret_cast<const int4*>(sJi + o);
             const int4 hi = *reinterpret_cast<const int4*>(sJi + o + LY::jVol);
             if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
-            const float4 v = make_float4(float(double((long long)hi.x * 32768 + lo.x) * A.inv_vscale),
-                                         float(double((long long)hi.y * 32768 + lo.y) * A.inv_vscale),
-                                         float(double((long long)hi.z * 32768 + lo.z) * A.inv_vscale),
-                                         float(double((long long)hi.w * 32768 + lo.w) * A.inv_vscale));
+            const float4 v = make_float4(fixed_to_float(hi.x, lo.x) * A.inv_vscale,
+                                         fixed_to_float(hi.y, lo.y) * A.inv_vscale,
+                                         fixed_to_float(hi.z, lo.z) * A.inv_vscale,
+                                         fixed_to_float(hi.w, lo.w) * A.inv_vscale);
             const int gi = wrap_any(oi - 2 + a, g.n[0]);
             const int gj = wrap_any(oj - 2 + b, g.n[1]);
             // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
@@ -521,7 +536,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             const int o = a * LY::jX + b * LY::jY + kk;
             R v;
             if (kFixed)
-                v = R(double((long long)sJi[2 * c * LY::jVol + LY::jVol + o] * 32768 + sJi[2 * c * LY::jVol + o]) *
+                v = R(fixed_to_float(sJi[2 * c * LY::jVol + LY::jVol + o], sJi[2 * c * LY::jVol + o]) *
                       A.inv_vscale);
             else
                 v = sJ[c * LY::jVol + o];

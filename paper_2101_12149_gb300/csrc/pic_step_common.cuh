@@ -83,7 +83,7 @@ template <typename R> struct StepArgs {
     int pusher;         // 0 Boris, 1 Vay
     int egather;        // 0 momentum-conserving gather, 1 energy-conserving
     float vscale;       // FP32-mixed fixed-point scale of the deposit (largest power of two <= 2^30 / max|coef|)
-    double inv_vscale;
+    float inv_vscale;   // 1 / vscale (a power of two: exact)
     int64_t np;
 };
 
@@ -125,7 +125,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
         int e = 0;
         std::frexp(1073741824.0 / cmax, &e);  // 2^30 / cmax = m 2^e, m in [0.5, 1)
         a.vscale = float(std::ldexp(1.0, e - 1));
-        a.inv_vscale = 1.0 / double(a.vscale);
+        a.inv_vscale = float(std::ldexp(1.0, 1 - e));
     }
     a.np = c->np;
     return a;
@@ -329,8 +329,17 @@ __device__ __forceinline__ void jtarget_global(JTarget<P, R>& t, const Geom& g, 
 // particle state access (FP64 and FP32-mixed)
 // ---------------------------------------------------------------------------
 // FP64: positions are global coordinates; cell = floor(x/d), fraction exact.
+// x / d, correctly rounded; when d is a normal power of two (unit cells among
+// them) by the exact reciprocal, which avoids the FP64 division.
+__device__ __forceinline__ double div_by_cell(double x, double d) {
+    const long long b = __double_as_longlong(d);
+    if ((b & 0x000FFFFFFFFFFFFFll) == 0 && b > 0x0010000000000000ll && b < 0x7FE0000000000000ll)
+        return x * __longlong_as_double(0x7FE0000000000000ll - b);
+    return x / d;
+}
+
 __device__ __forceinline__ void split_pos(double x, double d, int n, int& cell, double& f) {
-    const double p = x / d;
+    const double p = div_by_cell(x, d);
     double fl = floor(p);
     int c = int(fl);
     if (c >= n) c = n - 1, fl = double(n - 1);
@@ -369,13 +378,13 @@ __device__ __forceinline__ void push_particle(const StepArgs<R>& A, R EB[6], con
         for (int a = 0; a < 3; ++a) {
             const double dx = __dmul_rn(__dmul_rn(A.dt, double(u[a])), gi);
             mv.xg1[a] = __dadd_rn(xg0[a], dx);
-            const double p1 = mv.xg1[a] / A.g.d[a];
+            const double p1 = div_by_cell(mv.xg1[a], A.g.d[a]);
             mv.f1[a] = R(p1 - double(cell[a]));
             mv.f0[a] = f0[a];
             if (!(fabs(double(mv.f1[a] - f0[a])) < 1.0)) mv.ok = false;
         }
     } else {
-        const R gi = R(1) / rsqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        const R gi = R(1) / sqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
             mv.f0[a] = f0[a];
@@ -424,6 +433,46 @@ __device__ __forceinline__ void load_particle(const StepArgs<R>& A, int p, int c
     u[1] = A.pa[4][p];
     u[2] = A.pa[5][p];
     wq = A.pa[6][p];
+}
+
+// A particle's stored data as loaded (key and the 7 reals), so that the tile
+// kernel can issue the next particle's loads before it works on the current one.
+template <typename R> struct RawParticle {
+    int key;
+    R a[7];
+};
+
+template <typename R> __device__ __forceinline__ void load_raw(const StepArgs<R>& A, int p, RawParticle<R>& r) {
+    r.key = sizeof(R) == 8 ? 0 : A.key[p];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) r.a[i] = A.pa[i][p];
+}
+
+// load_particle on data already loaded.
+template <typename R>
+__device__ __forceinline__ void decode_particle(const StepArgs<R>& A, const RawParticle<R>& r, int cell[3], R f0[3],
+                                                double xg0[3], R u[3], R& wq) {
+    const Geom& g = A.g;
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            xg0[a] = double(r.a[a]);
+            double f;
+            split_pos(xg0[a], g.d[a], g.n[a], cell[a], f);
+            f0[a] = R(f);
+        }
+    } else {
+        cell_of(g, r.key, cell[0], cell[1], cell[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            f0[a] = r.a[a];
+            xg0[a] = 0.0;
+        }
+    }
+    u[0] = r.a[3];
+    u[1] = r.a[4];
+    u[2] = r.a[5];
+    wq = r.a[6];
 }
 
 // Store the moved particle in place: momentum, wrapped position, new cell key.

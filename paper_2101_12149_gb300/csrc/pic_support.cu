@@ -176,31 +176,36 @@ template <typename R> YeeArgs<R> make_yee(pic_ctx* c, double h) {
 // particle load / store, field conversion, diagnostics
 // ---------------------------------------------------------------------------
 template <typename R>
+// Particles [base, base + count) from source arrays that start at particle
+// `base` (device memory, or pinned host memory the kernel reads directly).
 __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const double* z, const double* ux,
-                       const double* uy, const double* uz, const double* w, int* id, unsigned long long* wmax) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                       const double* uy, const double* uz, const double* w, int64_t base, int64_t count, int* id,
+                       unsigned long long* wmax) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double wi = i < count ? w[i] : 0.0;
     // largest |w| of the warp (non-negative doubles order like their bit
     // patterns), then one atomic per warp
     unsigned long long wb = 0ull;
-    if (p < A.np && isfinite(w[p])) wb = (unsigned long long)__double_as_longlong(fabs(double(R(w[p]))));
+    if (i < count && isfinite(wi)) wb = (unsigned long long)__double_as_longlong(fabs(double(R(wi))));
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         const unsigned long long other = __shfl_down_sync(0xffffffffu, wb, o);
         wb = other > wb ? other : wb;
     }
     if ((threadIdx.x & 31) == 0 && wb) atomicMax(wmax, wb);
-    if (p >= A.np) return;
+    if (i >= count) return;
+    const int64_t p = base + i;
     const Geom& g = A.g;
-    const double xs[3] = {x[p], y[p], z[p]};
-    const double us[3] = {ux[p], uy[p], uz[p]};
-    bool ok = isfinite(w[p]);
+    const double xs[3] = {x[i], y[i], z[i]};
+    const double us[3] = {ux[i], uy[i], uz[i]};
+    bool ok = isfinite(wi);
     int cell[3];
     bool gone = false;  // z open: a particle loaded outside [0, Lz) is dropped by the first sort
     for (int a = 0; a < 3; ++a) {
         ok = ok && isfinite(xs[a]) && isfinite(us[a]);
         double xv = isfinite(xs[a]) ? xs[a] : 0.0;
         if (a == 2 && g.zopen && !(xv >= 0.0 && xv < g.L[2])) gone = true, xv = 0.0;
-        xv = fmod(xv, g.L[a]);
+        if (!(xv >= 0.0 && xv < g.L[a])) xv = fmod(xv, g.L[a]);  // fmod is the identity inside [0, L)
         xv = wrap_pos(xv, g.L[a]);
         double f;
         split_pos(xv, g.d[a], g.n[a], cell[a], f);
@@ -216,7 +221,7 @@ __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const do
         }
         A.pa[3 + a][p] = R(us[a]);
     }
-    A.pa[6][p] = R(w[p]);
+    A.pa[6][p] = R(wi);
     A.key[p] = gone ? dead_key(g) : key_of(g, cell[0], cell[1], cell[2]);
     id[p] = int(p);
     if (!ok) raise_error(A.err, ERRBIT_PARTICLE);
@@ -273,14 +278,27 @@ template <typename R>
 __global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out) {
     // gamma - 1 = |u|^2 / (gamma + 1) (no cancellation for slow particles), per
     // particle in the particles' own precision, summed in FP64
-    double ke = 0.0, sw = 0.0;
+    // FP32: each thread's terms summed in FP32 with Kahan compensation (its
+    // few hundred terms then carry about one FP32 rounding), then in FP64.
+    R ks = R(0), kc = R(0), ws = R(0), wc = R(0);
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < A.np;
          p += (int64_t)gridDim.x * blockDim.x) {
         const R u0 = A.pa[3][p], u1 = A.pa[4][p], u2 = A.pa[5][p], w = A.pa[6][p];
         const R uu = u0 * u0 + u1 * u1 + u2 * u2;
-        ke += double(w * (uu / (rsqrt_<R>(R(1) + uu) + R(1))));
-        sw += double(w);
+        const R term = w * (uu / (sqrt_<R>(R(1) + uu) + R(1)));
+        if (sizeof(R) == 8) {
+            ks += term;
+            ws += w;
+        } else {
+            const R y = term - kc, t = ks + y;
+            kc = (t - ks) - y;
+            ks = t;
+            const R y2 = w - wc, t2 = ws + y2;
+            wc = (t2 - ws) - y2;
+            ws = t2;
+        }
     }
+    double ke = double(ks) - double(kc), sw = double(ws) - double(wc);
     ke *= m;
     double ch = q * sw;
     for (int o = 16; o; o >>= 1) {
@@ -301,20 +319,27 @@ __global__ void k_diag_particles(StepArgs<R> A, double m, double q, double* out)
     }
 }
 
+// One warp per z-row (i, j) at a time, its lanes along z.
 template <typename R>
 __global__ void k_diag_divb(const R* Bx, const R* By, const R* Bz, int nx, int ny, int nz, double dx, double dy,
                             double dz, int zopen, unsigned long long* out) {
-    const int64_t C = (int64_t)nx * ny * nz;
+    const double ix = 1.0 / dx, iy = 1.0 / dy, iz = 1.0 / dz;
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = (int64_t)nx * ny;
     double mx = 0.0;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < C; c += (int64_t)gridDim.x * blockDim.x) {
-        const int k = int(c % nz), j = int((c / nz) % ny), i = int(c / ((int64_t)ny * nz));
-        const int64_t ip = ((int64_t)wrap_once(i + 1, nx) * ny + j) * nz + k;
-        const int64_t jp = ((int64_t)i * ny + wrap_once(j + 1, ny)) * nz + k;
-        const int64_t kp = ((int64_t)i * ny + j) * nz + wrap_once(k + 1, nz);
-        const double bz_up = zopen && k + 1 == nz ? 0.0 : double(Bz[kp]);  // z open: zero beyond the end
-        const double v = (double(Bx[ip]) - double(Bx[c])) / dx + (double(By[jp]) - double(By[c])) / dy +
-                         (bz_up - double(Bz[c])) / dz;
-        mx = fmax(mx, fabs(v));
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int i = int(r / ny), j = int(r - (int64_t)i * ny);
+        const int64_t c0 = r * nz;
+        const int64_t ip0 = ((int64_t)wrap_once(i + 1, nx) * ny + j) * nz;
+        const int64_t jp0 = ((int64_t)i * ny + wrap_once(j + 1, ny)) * nz;
+        for (int k = lane; k < nz; k += 32) {
+            const int64_t c = c0 + k;
+            const double bz_up = zopen && k + 1 == nz ? 0.0 : double(Bz[c0 + wrap_once(k + 1, nz)]);  // z open: zero beyond the end
+            const double v = (double(Bx[ip0 + k]) - double(Bx[c])) * ix + (double(By[jp0 + k]) - double(By[c])) * iy +
+                             (bz_up - double(Bz[c])) * iz;
+            mx = fmax(mx, fabs(v));
+        }
     }
     for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(mx));
@@ -484,17 +509,17 @@ cudaError_t launch_step_counter(pic_ctx* c) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n) {
+cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n, int64_t base) {
     if (n == 0) return cudaSuccess;
     if (c->prec == PIC_FP64) {
         auto A = make_args<double>(c);
         k_load<double><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                               src[6], c->P[c->cur].id,
+                                                               src[6], base, n, c->P[c->cur].id,
                                                                reinterpret_cast<unsigned long long*>(c->err + 6));
     } else {
         auto A = make_args<float>(c);
         k_load<float><<<blocks_for(n), kBlock, 0, c->stream>>>(A, src[0], src[1], src[2], src[3], src[4], src[5],
-                                                              src[6], c->P[c->cur].id,
+                                                              src[6], base, n, c->P[c->cur].id,
                                                               reinterpret_cast<unsigned long long*>(c->err + 6));
     }
     return cudaGetLastError();
