@@ -528,6 +528,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     if ((e = cudaMalloc(&c->err, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word allocation");
     if ((e = cudaMemset(c->err, 0, 8 * sizeof(unsigned))) != cudaSuccess) return bail(e, "error word");
     if ((e = pic::configure_tile_kernels(c)) != cudaSuccess) return bail(e, "tile kernel configuration");
+    pic::setup_tile_tma(c);
     if ((e = cudaMalloc(&c->d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter allocation");
     if ((e = cudaMemset(c->d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMalloc(&c->dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");

@@ -1,6 +1,7 @@
 // Host-side context of libpic and the launchers shared between its
 // translation units.  Not part of the public C-ABI (see include/pic.h).
 #pragma once
+#include <cuda.h>  // CUtensorMap (the type only: the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -81,6 +82,10 @@ struct pic_ctx {
 
     int* outl = nullptr;     // outsider list of the tile kernel [cap]
     int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32
+    // FP32-mixed, 4x4x32 layout: TMA descriptor of E and B (four dimensions z, y, x,
+    // component) whose box is one tile's staged E/B block
+    CUtensorMap tmap_eb;
+    bool tma = false;
 
     int* count = nullptr;    // per-cell particle counts [C]
     int* offsets = nullptr;  // exclusive scan of count [C+1]; tile t owns [offsets[t*cpt], offsets[(t+1)*cpt])
@@ -130,6 +135,8 @@ namespace pic {
 cudaError_t launch_zero_fields(pic_ctx* c, int first, int count);
 cudaError_t launch_tile_step(pic_ctx* c);        // fused gather+push+deposit, tile kernel
 cudaError_t configure_tile_kernels(pic_ctx* c);
+// encodes c->tmap_eb where the tile kernel can stage by TMA (sets c->tma)
+void setup_tile_tma(pic_ctx* c);
 cudaError_t launch_gather_push_global(pic_ctx* c);
 cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);

@@ -14,10 +14,13 @@
 //                     (the paper's GPU deposit, Sec. 3.4.1).
 // The Yee update, load/store, diagnostics and the moving window are in
 // pic_support.cu.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <type_traits>
 
 #include "pic_ctx.h"
@@ -315,14 +318,93 @@ __device__ __forceinline__ float fixed_to_float(int hi, int lo) {
 // shared memory holding the fixed-point J box), FP64 256.
 template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
 
+// Stage the sub-box [a0,a1) x [b0,b1) x [k0,k1) of the tile's E/B block (cells
+// [-2, T+2) per axis around the tile origin oi, oj, ok), periodic wrap in x, y
+// and in z unless z is open, where nothing lies beyond the ends.
+template <typename R, class LY>
+__device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, int oj, int ok, int a0, int a1, int b0,
+                                          int b1, int k0, int k1) {
+    const Geom& g = A.g;
+    const int eb = b1 - b0, ek = k1 - k0;
+    const int vol = (a1 - a0) * eb * ek;
+    for (int e = threadIdx.x; e < 6 * vol; e += blockDim.x) {
+        const int c = e / vol;
+        int r = e - c * vol;
+        const int a = a0 + r / (eb * ek);
+        r -= (a - a0) * eb * ek;
+        const int b = b0 + r / ek;
+        const int kk = k0 + r - (b - b0) * ek;
+        const int gi = wrap_any(oi - 2 + a, g.n[0]);
+        const int gj = wrap_any(oj - 2 + b, g.n[1]);
+        const int kz = ok - 2 + kk;
+        R v = R(0);
+        if (!g.zopen || unsigned(kz) < unsigned(g.n[2])) {
+            const int gk = wrap_any(kz, g.n[2]);
+            const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+            PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx,
+                         continue);
+            v = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+        }
+        sEB[c * LY::eVol + a * LY::eX + b * LY::eY + kk] = v;
+    }
+}
+
+// TMA staging of the FP32-mixed 4x4x32 layout: one 4-D box (z, y, x,
+// component) of 64 x 8 x 8 x 6 floats lands in the E/B block exactly (its
+// row pitch is 64).  The box starts at z = ok - 4 (a multiple of 4, as TMA
+// requires of the innermost coordinate), so the block is addressed 2 floats
+// in; coordinates outside the grid read as zero and the wrapped halo planes
+// are restaged by stage_box after the copy has landed.
+constexpr int kTmaBoxZ = 64, kTmaBoxXY = 8;
+constexpr unsigned kTmaBytes = 6u * kTmaBoxXY * kTmaBoxXY * kTmaBoxZ * 4u;
+constexpr int kTmaSpinLimit = 1 << 20;
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
+    const unsigned b = unsigned(__cvta_generic_to_shared(bar));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_eb(const CUtensorMap* map, void* dst, unsigned long long* bar, int z, int y,
+                                            int x) {
+    const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+    const unsigned b = unsigned(__cvta_generic_to_shared(bar));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kTmaBytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];" ::"r"(d),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(z), "r"(y), "r"(x), "r"(0), "r"(b)
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of the barrier; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int limit) {
+    const unsigned b = unsigned(__cvta_generic_to_shared(bar));
+    for (int i = 0; i < limit; ++i) {
+        unsigned done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // One tile t of the box described by A, by the whole CTA; `smem_raw` is the
-// CTA's dynamic shared memory.  Returns with the block converged.
+// CTA's dynamic shared memory; `tmap` the TMA descriptor of E/B for the
+// FP32-mixed 4x4x32 layout (null: staged by loads).  Returns with the block
+// converged.
 template <int P, typename R, class LY>
-__device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw) {
+__device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw,
+                                          const CUtensorMap* tmap = nullptr) {
     R* sm = reinterpret_cast<R*>(smem_raw);
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
-    R* sEB = sm;                  // 6 * eVol
+    constexpr bool kTmaLayout = kFixed && LY::eY == kTmaBoxZ && LY::EX == kTmaBoxXY && LY::EY == kTmaBoxXY;
+    constexpr int kZShift = kTmaLayout ? 2 : 0;
+    R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
     R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
     int* sJi = reinterpret_cast<int*>(sJ);
 
@@ -333,34 +415,47 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     int oi, oj, ok;
     tile_origin(g, t, oi, oj, ok);
 
-    // stage E, B of the tile and a halo of 2 (wrapped)
+    // stage E, B of the tile and a halo of 2 (wrapped), zero the tile's J
     {
         const int ex = g.T[0] + 4, ey = g.T[1] + 4, ez = g.T[2] + 4;
-        const int vol = ex * ey * ez;
-        for (int e = threadIdx.x; e < 6 * vol; e += blockDim.x) {
-            const int c = e / vol;
-            int r = e - c * vol;
-            const int a = r / (ey * ez);
-            r -= a * ey * ez;
-            const int b = r / ez;
-            const int kk = r - b * ez;
-            const int gi = wrap_any(oi - 2 + a, g.n[0]);
-            const int gj = wrap_any(oj - 2 + b, g.n[1]);
-            const int kz = ok - 2 + kk;
-            R v = R(0);
-            if (!g.zopen || unsigned(kz) < unsigned(g.n[2])) {  // z open: nothing beyond the ends
-                const int gk = wrap_any(kz, g.n[2]);
-                const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
-                PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx,
-                             continue);
-                v = c < 3 ? A.E[c][gidx] : A.B[c - 3][gidx];
+        bool by_tma = false;
+        if constexpr (kTmaLayout) {
+            __shared__ __align__(8) unsigned long long s_bar;
+            by_tma = tmap != nullptr && (unsigned(__cvta_generic_to_shared(sm)) & 127u) == 0u &&
+                     ((ok - 2 - kZShift) & 3) == 0;
+            if (by_tma) {
+                if (threadIdx.x == 0) mbar_init(&s_bar);
+                __syncthreads();
+                if (threadIdx.x == 0) tma_load_eb(tmap, sm, &s_bar, ok - 2 - kZShift, oj - 2, oi - 2);
+                for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
+                // every thread waits for the copy; if it did not land in time,
+                // all wait once more (it is still writing into this CTA's
+                // shared memory) and the tile is skipped with the error set
+                const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0u, kTmaSpinLimit));
+                if (late) {
+                    if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
+                    mbar_wait(&s_bar, 0u, kTmaSpinLimit);
+                    __syncthreads();
+                    return;
+                }
+                // halo planes that wrap around the grid came in as zeros
+                if (oi < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, 2 - oi, 0, ey, 0, ez);
+                if (oi + ex - 2 > g.n[0]) stage_box<R, LY>(A, sEB, oi, oj, ok, g.n[0] - oi + 2, ex, 0, ey, 0, ez);
+                if (oj < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, 2 - oj, 0, ez);
+                if (oj + ey - 2 > g.n[1]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, g.n[1] - oj + 2, ey, 0, ez);
+                if (!g.zopen) {
+                    if (ok < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, 2 - ok);
+                    if (ok + ez - 2 > g.n[2]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, g.n[2] - ok + 2, ez);
+                }
             }
-            sEB[c * LY::eVol + a * LY::eX + b * LY::eY + kk] = v;
         }
-        if (kFixed)
-            for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
-        else
-            for (int e = threadIdx.x; e < 3 * LY::jVol; e += blockDim.x) sJ[e] = R(0);
+        if (!by_tma) {
+            stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
+            if (kFixed)
+                for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
+            else
+                for (int e = threadIdx.x; e < 3 * LY::jVol; e += blockDim.x) sJ[e] = R(0);
+        }
     }
     __syncthreads();
 
@@ -551,9 +646,10 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
 }
 
 template <int P, typename R, class LY>
-__global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    tile_body<P, R, LY>(A, int(blockIdx.x), smem_raw);
+__global__ void __launch_bounds__(tile_block<R>(), 1)
+    k_tile_step(StepArgs<R> A, const __grid_constant__ CUtensorMap tmap, int use_tma) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    tile_body<P, R, LY>(A, int(blockIdx.x), smem_raw, use_tma ? &tmap : nullptr);
 }
 
 // Batch of boxes: a persistent grid pulls (box, tile) items from a queue
@@ -562,7 +658,7 @@ __global__ void __launch_bounds__(tile_block<R>(), 1) k_tile_step(StepArgs<R> A)
 template <int P, typename R, class LY>
 __global__ void __launch_bounds__(tile_block<R>(), 1)
     k_tile_step_batch(const StepArgs<R>* __restrict__ boxes, const int2* __restrict__ items, int nitems, int* queue) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(16) StepArgs<R> sA;
     __shared__ int s_item;
     for (;;) {
@@ -751,7 +847,7 @@ template <typename R, int P, class LY> cudaError_t tile_step_impl(pic_ctx* c) {
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    k_tile_step<P, R, LY><<<unsigned(c->g.ntiles), tile_block<R>(), smem, c->stream>>>(A);
+    k_tile_step<P, R, LY><<<unsigned(c->g.ntiles), tile_block<R>(), smem, c->stream>>>(A, c->tmap_eb, c->tma ? 1 : 0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_outsiders<P, R><<<152 * 4, kBlock, 0, c->stream>>>(A);
@@ -777,6 +873,29 @@ cudaError_t launch_tile_step(pic_ctx* c) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err + 4, 0, sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
+}
+
+void setup_tile_tma(pic_ctx* c) {
+    c->tma = false;
+    std::memset(&c->tmap_eb, 0, sizeof(c->tmap_eb));
+    if (c->prec != PIC_FP32_MIXED || c->layout != 1 || c->g.n[2] % 4 != 0) return;
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return;
+    }
+    const cuuint64_t nz = cuuint64_t(c->g.n[2]), ny = cuuint64_t(c->g.n[1]), nx = cuuint64_t(c->g.n[0]);
+    const cuuint64_t dims[4] = {nz, ny, nx, 6};
+    const cuuint64_t strides[3] = {nz * 4, ny * nz * 4, cuuint64_t(c->g.C) * 4};  // bytes, dimensions 1..3
+    const cuuint32_t box[4] = {kTmaBoxZ, kTmaBoxXY, kTmaBoxXY, 6};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
+        &c->tmap_eb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->F[0], dims, strides, box, estride,
+        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    c->tma = r == CUDA_SUCCESS;
 }
 
 // The tile kernels need more than 48 KB of dynamic shared memory: raise the

@@ -215,3 +215,15 @@ def test_uneven_particle_spread(precision):
     e = c.errors()
     tol = 1e-12 if precision == pic.FP64 else 1e-5
     assert max(e.values()) < tol, e
+
+
+@pytest.mark.parametrize("n", [(8, 8, 32), (8, 12, 64), (16, 8, 96)])
+def test_fp32_mixed_row_layout_halos(n):
+    """FP32-mixed grids whose z extent is a multiple of 32 (4x4x32 tiles, E/B
+    staged by TMA): tiles touching the grid's faces restage their wrapped
+    halo planes; with random fields any wrong halo value shows at O(1)."""
+    c = Case(n, 3, 2, 0.3, 95, precision=pic.FP32_MIXED, field_scale=0.5)
+    c.ctx.step(2)
+    c.oracle_steps(2)
+    e = c.errors()
+    assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
