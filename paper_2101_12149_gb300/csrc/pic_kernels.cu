@@ -318,15 +318,26 @@ __device__ __forceinline__ float fixed_to_float(int hi, int lo) {
 // shared memory holding the fixed-point J box), FP64 256.
 template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
 
+// Periodic index of a cell at most one period outside [0, n) (any i, n > 0,
+// without a division in that common case).
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    return unsigned(i) < unsigned(n) ? i : wrap_any(i, n);
+}
+
 // Stage the sub-box [a0,a1) x [b0,b1) x [k0,k1) of the tile's E/B block (cells
 // [-2, T+2) per axis around the tile origin oi, oj, ok), periodic wrap in x, y
 // and in z unless z is open, where nothing lies beyond the ends.
-template <typename R, class LY>
+// kFull: the whole block of the layout's own tile shape (compile-time
+// divisors; the sub-box arguments are ignored).
+template <typename R, class LY, bool kFull = false>
 __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, int oj, int ok, int a0, int a1, int b0,
                                           int b1, int k0, int k1) {
     const Geom& g = A.g;
-    const int eb = b1 - b0, ek = k1 - k0;
-    const int vol = (a1 - a0) * eb * ek;
+    if (kFull) a0 = 0, b0 = 0, k0 = 0;
+    const int eb = kFull ? LY::EY : b1 - b0, ek = kFull ? LY::EZ : k1 - k0;
+    const int vol = kFull ? LY::EX * LY::EY * LY::EZ : (a1 - a0) * eb * ek;
     for (int e = threadIdx.x; e < 6 * vol; e += blockDim.x) {
         const int c = e / vol;
         int r = e - c * vol;
@@ -334,12 +345,12 @@ __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, 
         r -= (a - a0) * eb * ek;
         const int b = b0 + r / ek;
         const int kk = k0 + r - (b - b0) * ek;
-        const int gi = wrap_any(oi - 2 + a, g.n[0]);
-        const int gj = wrap_any(oj - 2 + b, g.n[1]);
+        const int gi = wrap_near(oi - 2 + a, g.n[0]);
+        const int gj = wrap_near(oj - 2 + b, g.n[1]);
         const int kz = ok - 2 + kk;
         R v = R(0);
         if (!g.zopen || unsigned(kz) < unsigned(g.n[2])) {
-            const int gk = wrap_any(kz, g.n[2]);
+            const int gk = wrap_near(kz, g.n[2]);
             const int64_t gidx = ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
             PIC_CHECK_OR(gidx >= 0 && gidx < g.C && a < LY::EX && b < LY::EY && kk < LY::EZ, A.err, 2, gidx,
                          continue);
@@ -392,6 +403,42 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
     return false;
 }
 
+// Flush of the fixed-point J box in groups of 4 consecutive z nodes (aligned
+// float4 reductions into HBM).  JYc, Q4c > 0: the box extents are the
+// layout's (compile-time divisors); 0: the runtime jy, q4.
+template <typename R, class LY, int JYc, int Q4c>
+__device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJi, int oi, int oj, int ok, int jx,
+                                             int jy_rt, int q4_rt) {
+    const Geom& g = A.g;
+    const int jy = JYc > 0 ? JYc : jy_rt;
+    const int q4 = Q4c > 0 ? Q4c : q4_rt;
+    const int per_c = jx * jy * q4;
+    for (int e = threadIdx.x; e < 3 * per_c; e += blockDim.x) {
+        const int c = e / per_c;
+        int r = e - c * per_c;
+        const int row = r / q4;
+        const int q = r - row * q4;
+        const int a = row / jy;
+        const int b = row - a * jy;
+        const int o = 2 * c * LY::jVol + a * LY::jX + b * LY::jY + 4 * q;
+        const int4 lo = *reinterpret_cast<const int4*>(sJi + o);
+        const int4 hi = *reinterpret_cast<const int4*>(sJi + o + LY::jVol);
+        if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
+        // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
+        if (g.zopen && unsigned(ok - 4 + 4 * q) >= unsigned(g.n[2])) continue;
+        const float4 v = make_float4(fixed_to_float(hi.x, lo.x) * A.inv_vscale,
+                                     fixed_to_float(hi.y, lo.y) * A.inv_vscale,
+                                     fixed_to_float(hi.z, lo.z) * A.inv_vscale,
+                                     fixed_to_float(hi.w, lo.w) * A.inv_vscale);
+        const int gi = wrap_near(oi - 2 + a, g.n[0]);
+        const int gj = wrap_near(oj - 2 + b, g.n[1]);
+        const int gk = wrap_near(ok - 4 + 4 * q, g.n[2]);
+        PIC_CHECK_OR(gk + 3 < g.n[2] && ((gk & 3) == 0), A.err, 6, gk, continue);
+        float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
+        atomicAdd(reinterpret_cast<float4*>(dst), v);
+    }
+}
+
 // One tile t of the box described by A, by the whole CTA; `smem_raw` is the
 // CTA's dynamic shared memory; `tmap` the TMA descriptor of E/B for the
 // FP32-mixed 4x4x32 layout (null: staged by loads).  Returns with the block
@@ -427,7 +474,8 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                 if (threadIdx.x == 0) mbar_init(&s_bar);
                 __syncthreads();
                 if (threadIdx.x == 0) tma_load_eb(tmap, sm, &s_bar, ok - 2 - kZShift, oj - 2, oi - 2);
-                for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
+                for (int e = threadIdx.x; e < 6 * LY::jVol / 4; e += blockDim.x)
+                    reinterpret_cast<int4*>(sJi)[e] = make_int4(0, 0, 0, 0);
                 // every thread waits for the copy; if it did not land in time,
                 // all wait once more (it is still writing into this CTA's
                 // shared memory) and the tile is skipped with the error set
@@ -450,11 +498,13 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             }
         }
         if (!by_tma) {
-            stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
-            if (kFixed)
-                for (int e = threadIdx.x; e < 6 * LY::jVol; e += blockDim.x) sJi[e] = 0;
+            if (ex == LY::EX && ey == LY::EY && ez == LY::EZ)
+                stage_box<R, LY, true>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
             else
-                for (int e = threadIdx.x; e < 3 * LY::jVol; e += blockDim.x) sJ[e] = R(0);
+                stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
+            // J box zeroed 16 bytes at a time (jVol is a multiple of 4; the box starts 16-byte aligned)
+            const int n16 = kFixed ? 6 * LY::jVol / 4 : 3 * LY::jVol / 2;
+            for (int e = threadIdx.x; e < n16; e += blockDim.x) reinterpret_cast<int4*>(sJ)[e] = make_int4(0, 0, 0, 0);
         }
     }
     __syncthreads();
@@ -593,32 +643,11 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     // flush the tile's current into the global arrays (periodic fold)
     const int jx = g.T[0] + 5, jy = g.T[1] + 5, jz = g.T[2] + 8;
     if (kFixed && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
-        const int q4 = jz / 4;
-        const int rows = jx * jy;
-        for (int e = threadIdx.x; e < 3 * rows * q4; e += blockDim.x) {
-            const int c = e / (rows * q4);
-            int r = e - c * rows * q4;
-            const int row = r / q4;
-            const int q = r - row * q4;
-            const int a = row / jy;
-            const int b = row - a * jy;
-            const int o = 2 * c * LY::jVol + a * LY::jX + b * LY::jY + 4 * q;
-            const int4 lo = *reinterpret_cast<const int4*>(sJi + o);
-            const int4 hi = *reinterpret_cast<const int4*>(sJi + o + LY::jVol);
-            if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
-            const float4 v = make_float4(fixed_to_float(hi.x, lo.x) * A.inv_vscale,
-                                         fixed_to_float(hi.y, lo.y) * A.inv_vscale,
-                                         fixed_to_float(hi.z, lo.z) * A.inv_vscale,
-                                         fixed_to_float(hi.w, lo.w) * A.inv_vscale);
-            const int gi = wrap_any(oi - 2 + a, g.n[0]);
-            const int gj = wrap_any(oj - 2 + b, g.n[1]);
-            // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
-            if (g.zopen && unsigned(ok - 4 + 4 * q) >= unsigned(g.n[2])) continue;
-            const int gk = wrap_any(ok - 4 + 4 * q, g.n[2]);
-            PIC_CHECK_OR(gk + 3 < g.n[2] && ((gk & 3) == 0), A.err, 6, gk, continue);
-            float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
-            atomicAdd(reinterpret_cast<float4*>(dst), v);
-        }
+        // the layout's own tile shape indexes the J box with constants
+        if (jx == LY::JX && jy == LY::JY && jz == LY::JZ)
+            flush_fixed4<R, LY, LY::JY, LY::JZ / 4>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
+        else
+            flush_fixed4<R, LY, 0, 0>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
     } else {
         const int vol = jx * jy * jz;
         for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) {
@@ -637,9 +666,9 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                 v = sJ[c * LY::jVol + o];
             if (v == R(0)) continue;
             if (g.zopen && unsigned(ok - 4 + kk) >= unsigned(g.n[2])) continue;
-            const int gi = wrap_any(oi - 2 + a, g.n[0]);
-            const int gj = wrap_any(oj - 2 + b, g.n[1]);
-            const int gk = wrap_any(ok - 4 + kk, g.n[2]);
+            const int gi = wrap_near(oi - 2 + a, g.n[0]);
+            const int gj = wrap_near(oj - 2 + b, g.n[1]);
+            const int gk = wrap_near(ok - 4 + kk, g.n[2]);
             atomicAdd(A.J[c] + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk, v);
         }
     }
