@@ -48,6 +48,21 @@ def flops_per_particle(p: int) -> int:
     return gather + weights + boris + advance + esirk
 
 
+# shared-memory roof: 32 banks x 4 B per clock per SM
+SMEM_PEAK_GBS = 152 * 128 * 2.07e9 / 1e9
+
+
+def smem_bytes_per_particle(p: int, prec: str) -> int:
+    """Algorithmic shared-memory bytes of one particle in the tile kernel:
+    the gather reads 6 (p+1)^3 staged field values, the narrow Esirkepov
+    deposit adds 3 p (p+1)^2 current values (FP32-mixed: two int32 words
+    each, the fixed-point hi and lo; FP64: one double)."""
+    rs = 4 if prec == "fp32" else 8
+    gather = 6 * (p + 1) ** 3 * rs
+    deposit = 3 * p * (p + 1) ** 2 * 8
+    return gather + deposit
+
+
 def bytes_per_launch(np_, C, prec):
     """Algorithmic HBM bytes of one fused tile-kernel launch: each particle's
     state read once and written once (FP32-mixed: key + 3 offsets + 3 u + w
@@ -594,6 +609,13 @@ def main():
                         f"; algorithmic flops {flops_per_particle(order)} per particle"}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
                 "traffic": traffic, "kernel": "k_tile_step", "peak_source": f"{peak_kind} hbm_gbs"}
+    smem = N * smem_bytes_per_particle(order, args.precision) / avg_tile_s / 1e9 if avg_tile_s > 0 else None
+    roof_smem = {"bound": "smem", "achieved": smem, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
+                 "frac": smem / SMEM_PEAK_GBS if smem else None, "kernel": "k_tile_step",
+                 "note": "shared-memory roof derived from 152 SMs x 128 B/clock x 2.07 GHz; algorithmic bytes "
+                         f"{smem_bytes_per_particle(order, args.precision)} per particle (gather loads + narrow "
+                         "deposit reductions); the ncu profile gives the pipe's busy fraction including bank "
+                         "conflicts and the two cycles of each reduction"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -606,6 +628,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": roof_alu if (alu_frac or 0) >= (hbm_frac or 0) else roof_hbm,
         "roofline_alt": roof_hbm if (alu_frac or 0) >= (hbm_frac or 0) else roof_alu,
+        "roofline_smem": roof_smem,
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
         "ms_per_step_with_kernel_events": 1e3 * t_evented / args.steps,
         "kernel_share": {k: v[0] / max(sum(x[0] for x in timings.values()), 1e-30) for k, v in timings.items()},
