@@ -90,6 +90,8 @@ struct pic_batch {
     char* tab = nullptr;
     size_t tab_bytes = 0;
     size_t off_args[2] = {0, 0}, off_yb = 0, off_ye = 0, off_blocks = 0, off_pbase = 0, off_counters = 0;
+    size_t off_maps = 0;          // FP32-mixed: one E/B TMA descriptor per box
+    std::vector<char> map_ok;     // per box: its descriptor is valid
     int nblocks = 0;
     // captured step loop
     cudaGraphExec_t graph = nullptr;
@@ -176,6 +178,9 @@ template <typename R> void fill_args(const pic_batch* b, std::vector<char>& host
             int* counters = reinterpret_cast<int*>(b->tab + b->off_counters);
             A.outn = counters + 4 + k;
             A.outl = P.outl + b->cls[size_t(k)].outl_off;
+            A.tmap = b->map_ok.size() > i && b->map_ok[i]
+                         ? reinterpret_cast<const CUtensorMap*>(b->tab + b->off_maps) + i
+                         : nullptr;
             args[i] = A;
         }
     }
@@ -258,6 +263,8 @@ pic_status build_tables(pic_batch* b) {
     off = align(off + (nb + 1) * sizeof(int64_t));
     b->off_counters = off;
     off = align(off + 8 * sizeof(int));
+    b->off_maps = off;
+    off = align(off + (rs == 4 ? nb : 0) * sizeof(CUtensorMap));
     if (off > b->tab_bytes) {
         if (b->tab) cudaFree(b->tab);
         b->tab = nullptr;
@@ -267,6 +274,16 @@ pic_status build_tables(pic_batch* b) {
         b->tab_bytes = off;
     }
     std::vector<char> host(off, 0);
+    // FP32-mixed: each box's E/B (at its cell base in the pool, components one
+    // pool apart) as a TMA descriptor for the 8x8x8 layout
+    b->map_ok.assign(nb, 0);
+    if (rs == 4)
+        for (size_t i = 0; i < nb; ++i) {
+            const BoxInfo& B = b->box[i];
+            const void* base = static_cast<const char*>(b->pool.F[0]) + B.cbase * rs;
+            auto* m = reinterpret_cast<CUtensorMap*>(host.data() + b->off_maps) + i;
+            b->map_ok[i] = pic::encode_eb_tensor_map(m, base, B.n, b->pool.g.C, 0) ? 1 : 0;
+        }
     if (rs == 8) fill_args<double>(b, host);
     else fill_args<float>(b, host);
     std::memcpy(host.data() + b->off_blocks, blocks.data(), blocks.size() * sizeof(int4));

@@ -59,7 +59,11 @@ template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
 // shared memory, and the FP64 path is bound by FP64 arithmetic.
 template <typename R>
 using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64>, Layout<4, 4, 32, 36, 40>>;
-using LayoutCube = Layout<8, 8, 8, 12, 20>;
+// 8x8x8 tiles: the 32 cells of a warp are 4 z-rows of 8; FP32-mixed row
+// pitches of 24 words put those rows on banks 0, 24, 16 and 8 (mod 32), so
+// rows never share a bank at the same z.  FP64 keeps compact pitches.
+template <typename R>
+using LayoutCube = std::conditional_t<sizeof(R) == 4, Layout<8, 8, 8, 24, 24>, Layout<8, 8, 8, 12, 20>>;
 
 // Gather of one component from the staged box: `base` points at the first
 // stencil node.
@@ -360,15 +364,16 @@ __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, 
     }
 }
 
-// TMA staging of the FP32-mixed 4x4x32 layout: one 4-D box (z, y, x,
-// component) of 64 x 8 x 8 x 6 floats lands in the E/B block exactly (its
-// row pitch is 64).  The box starts at z = ok - 4 (a multiple of 4, as TMA
-// requires of the innermost coordinate), so the block is addressed 2 floats
-// in; coordinates outside the grid read as zero and the wrapped halo planes
-// are restaged by stage_box after the copy has landed.
-constexpr int kTmaBoxZ = 64, kTmaBoxXY = 8;
-constexpr unsigned kTmaBytes = 6u * kTmaBoxXY * kTmaBoxXY * kTmaBoxZ * 4u;
+// TMA staging of the FP32-mixed layouts: one 4-D box (z, y, x, component)
+// of eY x EY x EX x 6 floats lands in the E/B block exactly (eY, the row
+// pitch, is a multiple of 4 words and at least EZ + 2).  The box starts at
+// z = ok - 4 (a multiple of 4, as TMA requires of the innermost coordinate),
+// so the block is addressed 2 floats in; coordinates outside the grid read
+// as zero and the wrapped halo planes are restaged by stage_box after the
+// copy has landed.
 constexpr int kTmaSpinLimit = 1 << 20;
+
+template <class LY> __host__ __device__ constexpr bool tma_layout() { return LY::eY % 4 == 0 && LY::EZ + 2 <= LY::eY && LY::eY <= 256; }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
     const unsigned b = unsigned(__cvta_generic_to_shared(bar));
@@ -376,11 +381,19 @@ __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-__device__ __forceinline__ void tma_load_eb(const CUtensorMap* map, void* dst, unsigned long long* bar, int z, int y,
-                                            int x) {
+__device__ __forceinline__ void mbar_inval(unsigned long long* bar) {
+    const unsigned b = unsigned(__cvta_generic_to_shared(bar));
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(b) : "memory");
+}
+
+// Issued by one thread.  The proxy fence orders this CTA's earlier generic
+// accesses to the block (a previous tile's loads and stores) before the copy.
+__device__ __forceinline__ void tma_load_eb(const CUtensorMap* map, void* dst, unsigned long long* bar, unsigned bytes,
+                                            int z, int y, int x) {
     const unsigned d = unsigned(__cvta_generic_to_shared(dst));
     const unsigned b = unsigned(__cvta_generic_to_shared(bar));
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(kTmaBytes) : "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
     asm volatile(
         "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
         "%5}], [%6];" ::"r"(d),
@@ -449,7 +462,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     R* sm = reinterpret_cast<R*>(smem_raw);
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
-    constexpr bool kTmaLayout = kFixed && LY::eY == kTmaBoxZ && LY::EX == kTmaBoxXY && LY::EY == kTmaBoxXY;
+    constexpr bool kTmaLayout = kFixed && tma_layout<LY>();
     constexpr int kZShift = kTmaLayout ? 2 : 0;
     R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
     R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
@@ -463,17 +476,18 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     tile_origin(g, t, oi, oj, ok);
 
     // stage E, B of the tile and a halo of 2 (wrapped), zero the tile's J
+    __shared__ __align__(8) unsigned long long s_bar;
+    bool by_tma = false;
     {
         const int ex = g.T[0] + 4, ey = g.T[1] + 4, ez = g.T[2] + 4;
-        bool by_tma = false;
         if constexpr (kTmaLayout) {
-            __shared__ __align__(8) unsigned long long s_bar;
             by_tma = tmap != nullptr && (unsigned(__cvta_generic_to_shared(sm)) & 127u) == 0u &&
                      ((ok - 2 - kZShift) & 3) == 0;
             if (by_tma) {
                 if (threadIdx.x == 0) mbar_init(&s_bar);
                 __syncthreads();
-                if (threadIdx.x == 0) tma_load_eb(tmap, sm, &s_bar, ok - 2 - kZShift, oj - 2, oi - 2);
+                if (threadIdx.x == 0)
+                    tma_load_eb(tmap, sm, &s_bar, 6u * LY::eVol * 4u, ok - 2 - kZShift, oj - 2, oi - 2);
                 for (int e = threadIdx.x; e < 6 * LY::jVol / 4; e += blockDim.x)
                     reinterpret_cast<int4*>(sJi)[e] = make_int4(0, 0, 0, 0);
                 // every thread waits for the copy; if it did not land in time,
@@ -508,6 +522,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
         }
     }
     __syncthreads();
+    if (by_tma && threadIdx.x == 0) mbar_inval(&s_bar);  // every thread is past its wait
 
     // The tile's particles are cell-sorted; consecutive lanes take consecutive
     // runs of them, so the lanes of a warp work in neighbouring cells (distinct
@@ -702,7 +717,7 @@ __global__ void __launch_bounds__(tile_block<R>(), 1)
             for (int w = threadIdx.x; w < int(sizeof(StepArgs<R>) / 4); w += blockDim.x) dst[w] = src[w];
         }
         __syncthreads();
-        tile_body<P, R, LY>(sA, bt.y, smem_raw);
+        tile_body<P, R, LY>(sA, bt.y, smem_raw, sA.tmap);
         __syncthreads();
     }
 }
@@ -892,7 +907,7 @@ template <typename R, class LY> cudaError_t tile_step_order(pic_ctx* c) {
 }
 
 template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
-    return c->layout == 1 ? tile_step_order<R, LayoutRow<R>>(c) : tile_step_order<R, LayoutCube>(c);
+    return c->layout == 1 ? tile_step_order<R, LayoutRow<R>>(c) : tile_step_order<R, LayoutCube<R>>(c);
 }
 
 cudaError_t launch_tile_step(pic_ctx* c) {
@@ -904,27 +919,38 @@ cudaError_t launch_tile_step(pic_ctx* c) {
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
 }
 
-void setup_tile_tma(pic_ctx* c) {
-    c->tma = false;
-    std::memset(&c->tmap_eb, 0, sizeof(c->tmap_eb));
-    if (c->prec != PIC_FP32_MIXED || c->layout != 1 || c->g.n[2] % 4 != 0) return;
+bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], int64_t comp_stride, int layout) {
+    std::memset(map, 0, sizeof(*map));
+    if (n[2] % 4 != 0 || comp_stride % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn) {
         cudaGetLastError();
-        return;
+        return false;
     }
-    const cuuint64_t nz = cuuint64_t(c->g.n[2]), ny = cuuint64_t(c->g.n[1]), nx = cuuint64_t(c->g.n[0]);
+    using Row = LayoutRow<float>;
+    using Cube = LayoutCube<float>;
+    const cuuint32_t bz = layout == 1 ? Row::eY : Cube::eY;
+    const cuuint32_t by = layout == 1 ? Row::EY : Cube::EY;
+    const cuuint32_t bx = layout == 1 ? Row::EX : Cube::EX;
+    const cuuint64_t nz = cuuint64_t(n[2]), ny = cuuint64_t(n[1]), nx = cuuint64_t(n[0]);
     const cuuint64_t dims[4] = {nz, ny, nx, 6};
-    const cuuint64_t strides[3] = {nz * 4, ny * nz * 4, cuuint64_t(c->g.C) * 4};  // bytes, dimensions 1..3
-    const cuuint32_t box[4] = {kTmaBoxZ, kTmaBoxXY, kTmaBoxXY, 6};
+    const cuuint64_t strides[3] = {nz * 4, ny * nz * 4, cuuint64_t(comp_stride) * 4};  // bytes, dimensions 1..3
+    const cuuint32_t box[4] = {bz, by, bx, 6};
     const cuuint32_t estride[4] = {1, 1, 1, 1};
     const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
-        &c->tmap_eb, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, c->F[0], dims, strides, box, estride,
+        map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estride,
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    c->tma = r == CUDA_SUCCESS;
+    return r == CUDA_SUCCESS;
+}
+
+void setup_tile_tma(pic_ctx* c) {
+    c->tma = false;
+    std::memset(&c->tmap_eb, 0, sizeof(c->tmap_eb));
+    if (c->prec != PIC_FP32_MIXED) return;
+    c->tma = encode_eb_tensor_map(&c->tmap_eb, c->F[0], c->g.n, c->g.C, c->layout);
 }
 
 // The tile kernels need more than 48 KB of dynamic shared memory: raise the
@@ -937,9 +963,9 @@ cudaError_t configure_tile_kernels(pic_ctx* c) {
 #define PIC_CFG(R, P, LY)                                                              \
     if (e == cudaSuccess) e = set(k_tile_step<P, R, LY>, LY::template smem_bytes<R>());
     PIC_CFG(float, 1, LayoutRow<float>) PIC_CFG(float, 2, LayoutRow<float>) PIC_CFG(float, 3, LayoutRow<float>)
-    PIC_CFG(float, 1, LayoutCube) PIC_CFG(float, 2, LayoutCube) PIC_CFG(float, 3, LayoutCube)
+    PIC_CFG(float, 1, LayoutCube<float>) PIC_CFG(float, 2, LayoutCube<float>) PIC_CFG(float, 3, LayoutCube<float>)
     PIC_CFG(double, 1, LayoutRow<double>) PIC_CFG(double, 2, LayoutRow<double>) PIC_CFG(double, 3, LayoutRow<double>)
-    PIC_CFG(double, 1, LayoutCube) PIC_CFG(double, 2, LayoutCube) PIC_CFG(double, 3, LayoutCube)
+    PIC_CFG(double, 1, LayoutCube<double>) PIC_CFG(double, 2, LayoutCube<double>) PIC_CFG(double, 3, LayoutCube<double>)
 #undef PIC_CFG
     (void)c;
     return e;
@@ -947,7 +973,7 @@ cudaError_t configure_tile_kernels(pic_ctx* c) {
 
 // ---- batch of boxes ----------------------------------------------------------
 template <typename R, int P> cudaError_t tile_batch_impl(const BatchTileLaunch& L, cudaStream_t s) {
-    using LY = LayoutCube;
+    using LY = LayoutCube<R>;
     if (L.nitems <= 0) return cudaSuccess;
     const size_t smem = LY::template smem_bytes<R>();
     const int grid = L.grid < L.nitems ? L.grid : L.nitems;
@@ -979,10 +1005,9 @@ cudaError_t configure_batch_kernels() {
     auto set = [](auto kernel, size_t bytes) {
         return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
     };
-    using LY = LayoutCube;
     cudaError_t e = cudaSuccess;
 #define PIC_CFG(R, P) \
-    if (e == cudaSuccess) e = set(k_tile_step_batch<P, R, LY>, LY::template smem_bytes<R>());
+    if (e == cudaSuccess) e = set(k_tile_step_batch<P, R, LayoutCube<R>>, LayoutCube<R>::template smem_bytes<R>());
     PIC_CFG(float, 1) PIC_CFG(float, 2) PIC_CFG(float, 3) PIC_CFG(double, 1) PIC_CFG(double, 2) PIC_CFG(double, 3)
 #undef PIC_CFG
     return e;

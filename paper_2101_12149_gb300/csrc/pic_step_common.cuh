@@ -85,6 +85,7 @@ template <typename R> struct StepArgs {
     float vscale;       // FP32-mixed fixed-point scale of the deposit (largest power of two <= 2^30 / max|coef|)
     float inv_vscale;   // 1 / vscale (a power of two: exact)
     int64_t np;
+    const CUtensorMap* tmap;  // batch of boxes: the box's E/B TMA descriptor in global memory, or null
 };
 
 template <typename R> StepArgs<R> make_args(pic_ctx* c) {
@@ -128,6 +129,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
         a.inv_vscale = float(std::ldexp(1.0, 1 - e));
     }
     a.np = c->np;
+    a.tmap = nullptr;
     return a;
 }
 

@@ -217,11 +217,12 @@ def test_uneven_particle_spread(precision):
     assert max(e.values()) < tol, e
 
 
-@pytest.mark.parametrize("n", [(8, 8, 32), (8, 12, 64), (16, 8, 96)])
-def test_fp32_mixed_row_layout_halos(n):
-    """FP32-mixed grids whose z extent is a multiple of 32 (4x4x32 tiles, E/B
-    staged by TMA): tiles touching the grid's faces restage their wrapped
-    halo planes; with random fields any wrong halo value shows at O(1)."""
+@pytest.mark.parametrize("n", [(8, 8, 32), (8, 12, 64), (16, 8, 96), (8, 8, 8), (12, 20, 8), (16, 8, 24)])
+def test_fp32_mixed_tma_halos(n):
+    """FP32-mixed grids in both tile layouts (4x4x32 where nz is a multiple
+    of 32, else up to 8x8x8), E/B staged by TMA: tiles touching the grid's
+    faces restage their wrapped halo planes; with random fields any wrong
+    halo value shows at O(1)."""
     c = Case(n, 3, 2, 0.3, 95, precision=pic.FP32_MIXED, field_scale=0.5)
     c.ctx.step(2)
     c.oracle_steps(2)
