@@ -2,14 +2,14 @@
 // cell, then reorder the particle data; AMReX builds its GPU counting sort on
 // the single-pass prefix sum of Merrill and Garland).
 //
-//  k_hist     count[key] += 1, warp-aggregated (__match_any_sync) atomics
+//  k_hist     count[key] += 1, one atomic per run of equal keys in a warp
 //  k_scan     exclusive prefix sum of count into offsets in one pass:
 //             each CTA takes the next chunk ticket, publishes its aggregate,
 //             and looks back over its predecessors' published words
 //             (decoupled look-back, Merrill & Garland 2016).  Every wait is
 //             bounded; a wait that runs out sets the device error word.
 //  k_scatter  each particle takes a slot in its cell's range by decrementing
-//             count (warp-aggregated), then all its arrays move to the other
+//             count (one atomic per run of equal keys), then all its arrays move to the other
 //             buffer.  count returns to zero, ready for the next histogram.
 //  k_bin_keys pic_sort_particles only: coarse (runs of cells) or random bins
 //             for the same three kernels; the cell key moves as data.
@@ -33,6 +33,21 @@ __device__ __forceinline__ unsigned lanemask_lt() {
     return m;
 }
 
+// The lanes of this lane's run of equal keys among consecutive lanes.  The
+// particles are mostly in cell order already (sorted the step before), so a
+// run is usually all of a key's lanes; a key split over several runs just
+// takes one atomic per run.  Cheaper than __match_any_sync.
+__device__ __forceinline__ unsigned run_mask(int k) {
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(0xffffffffu, k, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != k);
+    const unsigned upto = (2u << lane) - 1u;  // lanes <= lane (all for lane 31)
+    const int first = 31 - __clz(heads & upto);
+    const unsigned above = heads & ~upto;
+    const unsigned below_end = above ? (1u << (__ffs(above) - 1)) - 1u : 0xffffffffu;
+    return below_end & ~((1u << first) - 1u);
+}
+
 __global__ void __launch_bounds__(kSortBlock) k_hist(const int* __restrict__ key, int64_t np, int* count, int64_t C,
                                                      unsigned* err) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -44,7 +59,7 @@ __global__ void __launch_bounds__(kSortBlock) k_hist(const int* __restrict__ key
             k = -1;
         }
     }
-    const unsigned mask = __match_any_sync(0xffffffffu, k);
+    const unsigned mask = run_mask(k);
     if (k >= 0) {
         const int lane = threadIdx.x & 31;
         if (lane == __ffs(mask) - 1) atomicAdd(count + k, __popc(mask));
@@ -179,7 +194,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
         for (int i = 0; i < 7; ++i) v[i] = static_cast<const E*>(src.a[i])[p];
         id = src.id[p];
     }
-    const unsigned mask = __match_any_sync(0xffffffffu, k);
+    const unsigned mask = run_mask(k);
     if (k < 0) return;
     const int lane = threadIdx.x & 31;
     const int leader = __ffs(mask) - 1;
