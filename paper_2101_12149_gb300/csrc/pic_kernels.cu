@@ -151,16 +151,20 @@ __device__ __forceinline__ void esirkepov_smem(R* __restrict__ J0, R* __restrict
 // (< 1 cell), and Q <= 1.  vscale is the largest power of two with
 // vscale max|coef| <= 2^30, so x = rn(v vscale) fits in 31 bits, and because
 // scaling by a power of two is exact, vscale is folded into the particle's
-// coefficient.  x is split as x = hi 2^15 + lo (hi = x >> 15, lo = x & 0x7fff)
-// and the halves go to two int32 arrays by native shared-memory integer
-// reductions.  Integer sums are exact and independent of order; with at most
-// 65535 particles per tile neither sum can overflow (65535 * 2^15 and
-// 65535 * (2^15 - 1) are below 2^31).  The flush rebuilds hi 2^15 + lo.
-__device__ __forceinline__ void red_fixed(int* lo, int* hi, float v_scaled) {
+// coefficient.  Two int32 arrays take, by native shared-memory integer
+// reductions, H = sum (x >> 15) and W = sum x modulo 2^32.  With at most 65535
+// particles per tile H cannot overflow (65535 * 2^15 < 2^31), and the low
+// part L = sum (x & 0x7fff) = sum x - 2^15 H lies in [0, 65535 * 32767], below
+// 2^31, so W - 2^15 H taken modulo 2^32 is L exactly.  The sums are exact and
+// independent of order; the flush rebuilds H 2^15 + L.
+__device__ __forceinline__ void red_fixed(int* w, int* hi, float v_scaled) {
     const int x = __float2int_rn(v_scaled);
-    atomicAdd(lo, x & 0x7fff);
+    atomicAdd(w, x);
     atomicAdd(hi, x >> 15);
 }
+
+// The low part L of a node from its two sums (see red_fixed).
+__device__ __forceinline__ int fixed_low(int hi, int w) { return int(unsigned(w) - (unsigned(hi) << 15)); }
 
 template <int P, class LY, int NC = P + 1, int NT = P + 2>
 __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int base, const EsirkAxis<P, float> ax[3],
@@ -439,10 +443,10 @@ __device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJ
         if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
         // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
         if (g.zopen && unsigned(ok - 4 + 4 * q) >= unsigned(g.n[2])) continue;
-        const float4 v = make_float4(fixed_to_float(hi.x, lo.x) * A.inv_vscale,
-                                     fixed_to_float(hi.y, lo.y) * A.inv_vscale,
-                                     fixed_to_float(hi.z, lo.z) * A.inv_vscale,
-                                     fixed_to_float(hi.w, lo.w) * A.inv_vscale);
+        const float4 v = make_float4(fixed_to_float(hi.x, fixed_low(hi.x, lo.x)) * A.inv_vscale,
+                                     fixed_to_float(hi.y, fixed_low(hi.y, lo.y)) * A.inv_vscale,
+                                     fixed_to_float(hi.z, fixed_low(hi.z, lo.z)) * A.inv_vscale,
+                                     fixed_to_float(hi.w, fixed_low(hi.w, lo.w)) * A.inv_vscale);
         const int gi = wrap_near(oi - 2 + a, g.n[0]);
         const int gj = wrap_near(oj - 2 + b, g.n[1]);
         const int gk = wrap_near(ok - 4 + 4 * q, g.n[2]);
@@ -675,7 +679,8 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
             const int o = a * LY::jX + b * LY::jY + kk;
             R v;
             if (kFixed)
-                v = R(fixed_to_float(sJi[2 * c * LY::jVol + LY::jVol + o], sJi[2 * c * LY::jVol + o]) *
+                v = R(fixed_to_float(sJi[2 * c * LY::jVol + LY::jVol + o],
+                                     fixed_low(sJi[2 * c * LY::jVol + LY::jVol + o], sJi[2 * c * LY::jVol + o])) *
                       A.inv_vscale);
             else
                 v = sJ[c * LY::jVol + o];
