@@ -52,9 +52,26 @@ void free_particles(pic_ctx* c) {
     for (auto& o : c->old) o = nullptr;
     c->oldkey = nullptr;
     c->sortbin = nullptr;
+    cudaFree(c->outl);
     c->outl = nullptr;
     c->np = c->cap = 0;
     c->have_old = false;
+}
+
+// The split API's old positions and moves and the old cell keys (also the
+// bins of pic_sort_particles), allocated for the particle capacity on first use.
+cudaError_t alloc_scratch(pic_ctx* c) {
+    if (c->old[0]) return cudaSuccess;
+    auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t cap = size_t(c->cap < 1 ? 1 : c->cap);
+    const size_t per = align(cap * c->rsize);
+    char* ob = nullptr;
+    cudaError_t e = cudaMalloc(&ob, 6 * per + align(cap * sizeof(int)));
+    if (e != cudaSuccess) return e;
+    for (int i = 0; i < 6; ++i) c->old[i] = ob + i * per;
+    c->oldkey = reinterpret_cast<int*>(ob + 6 * per);
+    c->sortbin = c->oldkey;  // pic_sort_particles ends any split-API step, so the two never overlap
+    return cudaSuccess;
 }
 
 // One allocation per particle buffer: 7 real arrays, key, id.
@@ -72,13 +89,8 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
         c->P[b].key = reinterpret_cast<int*>(base + 7 * per);
         c->P[b].id = reinterpret_cast<int*>(base + 7 * per + ints);
     }
-    char* ob = nullptr;
-    cudaError_t e = cudaMalloc(&ob, 6 * per + 2 * ints);
+    cudaError_t e = cudaMalloc(&c->outl, ints);
     if (e != cudaSuccess) return e;
-    for (int i = 0; i < 6; ++i) c->old[i] = ob + i * per;
-    c->oldkey = reinterpret_cast<int*>(ob + 6 * per);
-    c->sortbin = c->oldkey;  // pic_sort_particles ends any split-API step, so the two never overlap
-    c->outl = reinterpret_cast<int*>(ob + 6 * per + ints);
     c->cap = int64_t(cap);
     return cudaSuccess;
 }
@@ -705,6 +717,8 @@ pic_status pic_gather_push(pic_ctx* c) {
     if (pic_status s = check_ctx(c)) return s;
     if (c->window) return fail(PIC_ERR_STATE, "the split API runs periodic grids only");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
+    if (cudaError_t e = pic::alloc_scratch(c))
+        return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "split-API scratch") : cuda_fail(e, "scratch");
     PIC_CUDA(counted(c, "k_gather_push", 1, pic::launch_gather_push_global));
     c->have_old = true;
     return PIC_OK;
@@ -730,6 +744,8 @@ pic_status pic_sort_particles(pic_ctx* c, int32_t bin_shift) {
         c->since_sort = 0;
         return PIC_OK;
     }
+    if (cudaError_t e = pic::alloc_scratch(c))
+        return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "sort bins") : cuda_fail(e, "scratch");
     c->sort_shift = bin_shift;
     cudaError_t e = counted(c, "k_bin_keys", 1, pic::launch_bin_keys);
     if (e == cudaSuccess) e = run_sort(c);

@@ -76,7 +76,8 @@ struct pic_ctx {
     double w_max = 0.0;  // largest |weight| loaded (fixed-point scale of the FP32-mixed deposit)
     pic::PartBuf P[2];
     int cur = 0;
-    void* old[6] = {nullptr};  // split API: old position (3 arrays: FP64 x,y,z / FP32-mixed offsets) and move (3)
+    void* old[6] = {nullptr};  // split API: old position (3 arrays: FP64 x,y,z / FP32-mixed offsets) and move (3),
+                               // allocated on first use (alloc_scratch)
     int* oldkey = nullptr;     // FP32-mixed: key of the old position
     bool have_old = false;
 
@@ -230,6 +231,7 @@ cudaError_t restore_state(pic_ctx* c, const StateLayout& L, const char* src, con
 
 // particle buffers (pic_api.cu): one allocation per buffer, 7 real arrays, key, id
 cudaError_t alloc_particles(pic_ctx* c, int64_t n);
+cudaError_t alloc_scratch(pic_ctx* c);
 void free_particles(pic_ctx* c);
 
 cudaError_t launch_adj_init(pic_ctx* c, const AdjBuffers& b);
