@@ -90,7 +90,7 @@ struct pic_batch {
     char* tab = nullptr;
     size_t tab_bytes = 0;
     size_t off_args[2] = {0, 0}, off_yb = 0, off_ye = 0, off_blocks = 0, off_pbase = 0, off_counters = 0;
-    size_t off_maps = 0;          // FP32-mixed: one E/B TMA descriptor per box
+    size_t off_maps = 0;          // one E/B TMA descriptor per box
     std::vector<char> map_ok;     // per box: its descriptor is valid
     int nblocks = 0;
     // captured step loop
@@ -264,7 +264,7 @@ pic_status build_tables(pic_batch* b) {
     b->off_counters = off;
     off = align(off + 8 * sizeof(int));
     b->off_maps = off;
-    off = align(off + (rs == 4 ? nb : 0) * sizeof(CUtensorMap));
+    off = align(off + nb * sizeof(CUtensorMap));
     if (off > b->tab_bytes) {
         if (b->tab) cudaFree(b->tab);
         b->tab = nullptr;
@@ -274,16 +274,15 @@ pic_status build_tables(pic_batch* b) {
         b->tab_bytes = off;
     }
     std::vector<char> host(off, 0);
-    // FP32-mixed: each box's E/B (at its cell base in the pool, components one
-    // pool apart) as a TMA descriptor for the 8x8x8 layout
+    // each box's E/B (at its cell base in the pool, components one pool apart)
+    // as a TMA descriptor for the 8x8x8 layout
     b->map_ok.assign(nb, 0);
-    if (rs == 4)
-        for (size_t i = 0; i < nb; ++i) {
-            const BoxInfo& B = b->box[i];
-            const void* base = static_cast<const char*>(b->pool.F[0]) + B.cbase * rs;
-            auto* m = reinterpret_cast<CUtensorMap*>(host.data() + b->off_maps) + i;
-            b->map_ok[i] = pic::encode_eb_tensor_map(m, base, B.n, b->pool.g.C, 0) ? 1 : 0;
-        }
+    for (size_t i = 0; i < nb; ++i) {
+        const BoxInfo& B = b->box[i];
+        const void* base = static_cast<const char*>(b->pool.F[0]) + B.cbase * rs;
+        auto* m = reinterpret_cast<CUtensorMap*>(host.data() + b->off_maps) + i;
+        b->map_ok[i] = pic::encode_eb_tensor_map(m, base, B.n, b->pool.g.C, 0, b->pool.prec) ? 1 : 0;
+    }
     if (rs == 8) fill_args<double>(b, host);
     else fill_args<float>(b, host);
     std::memcpy(host.data() + b->off_blocks, blocks.data(), blocks.size() * sizeof(int4));

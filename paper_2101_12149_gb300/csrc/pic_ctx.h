@@ -83,8 +83,8 @@ struct pic_ctx {
 
     int* outl = nullptr;     // outsider list of the tile kernel [cap]
     int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32
-    // FP32-mixed: TMA descriptor of E and B (four dimensions z, y, x, component)
-    // whose box is one tile's staged E/B block
+    // TMA descriptor of E and B (four dimensions z, y, x, component) whose box
+    // is one tile's staged E/B block
     CUtensorMap tmap_eb;
     bool tma = false;
 
@@ -138,10 +138,11 @@ cudaError_t launch_tile_step(pic_ctx* c);        // fused gather+push+deposit, t
 cudaError_t configure_tile_kernels(pic_ctx* c);
 // encodes c->tmap_eb where the tile kernel can stage by TMA (sets c->tma)
 void setup_tile_tma(pic_ctx* c);
-// TMA descriptor of the E/B arrays of one FP32-mixed box (E and B at `base`,
-// components comp_stride floats apart) for tile layout `layout` (0: 8x8x8,
-// 1: 4x4x32); false (and a zeroed map) where TMA cannot be used
-bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], int64_t comp_stride, int layout);
+// TMA descriptor of the E/B arrays of one box (E and B at `base`, components
+// comp_stride values apart, precision `prec`) for tile layout `layout` (0:
+// 8x8x8, 1: 4x4x32); false (and a zeroed map) where TMA cannot be used
+bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], int64_t comp_stride, int layout,
+                          int prec);
 cudaError_t launch_gather_push_global(pic_ctx* c);
 cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);

@@ -58,12 +58,12 @@ template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
 // FP64 keeps compact pitches: the bank-conflict-free ones would not fit its
 // shared memory, and the FP64 path is bound by FP64 arithmetic.
 template <typename R>
-using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64>, Layout<4, 4, 32, 36, 40>>;
+using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64>, Layout<4, 4, 32, 38, 40>>;
 // 8x8x8 tiles: the 32 cells of a warp are 4 z-rows of 8; FP32-mixed row
 // pitches of 24 words put those rows on banks 0, 24, 16 and 8 (mod 32), so
 // rows never share a bank at the same z.  FP64 keeps compact pitches.
 template <typename R>
-using LayoutCube = std::conditional_t<sizeof(R) == 4, Layout<8, 8, 8, 24, 24>, Layout<8, 8, 8, 12, 20>>;
+using LayoutCube = std::conditional_t<sizeof(R) == 4, Layout<8, 8, 8, 24, 24>, Layout<8, 8, 8, 14, 20>>;
 
 // Gather of one component from the staged box: `base` points at the first
 // stencil node.
@@ -368,16 +368,18 @@ __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, 
     }
 }
 
-// TMA staging of the FP32-mixed layouts: one 4-D box (z, y, x, component)
-// of eY x EY x EX x 6 floats lands in the E/B block exactly (eY, the row
-// pitch, is a multiple of 4 words and at least EZ + 2).  The box starts at
-// z = ok - 4 (a multiple of 4, as TMA requires of the innermost coordinate),
-// so the block is addressed 2 floats in; coordinates outside the grid read
+// TMA staging: one 4-D box (z, y, x, component) of eY x EY x EX x 6 values
+// lands in the E/B block exactly (eY, the row pitch, spans a multiple of 16
+// bytes and at least EZ + 2 values).  The box starts at z = ok - 4 (TMA wants
+// the innermost coordinate on a 16-byte boundary), so the block is addressed
+// 2 values in; coordinates outside the grid read
 // as zero and the wrapped halo planes are restaged by stage_box after the
 // copy has landed.
 constexpr int kTmaSpinLimit = 1 << 20;
 
-template <class LY> __host__ __device__ constexpr bool tma_layout() { return LY::eY % 4 == 0 && LY::EZ + 2 <= LY::eY && LY::eY <= 256; }
+template <class LY, typename R> __host__ __device__ constexpr bool tma_layout() {
+    return (LY::eY * sizeof(R)) % 16 == 0 && LY::EZ + 2 <= LY::eY && LY::eY <= 256;
+}
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
     const unsigned b = unsigned(__cvta_generic_to_shared(bar));
@@ -466,7 +468,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
     R* sm = reinterpret_cast<R*>(smem_raw);
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
-    constexpr bool kTmaLayout = kFixed && tma_layout<LY>();
+    constexpr bool kTmaLayout = tma_layout<LY, R>();
     constexpr int kZShift = kTmaLayout ? 2 : 0;
     R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
     R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
@@ -491,7 +493,8 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                 if (threadIdx.x == 0) mbar_init(&s_bar);
                 __syncthreads();
                 if (threadIdx.x == 0)
-                    tma_load_eb(tmap, sm, &s_bar, 6u * LY::eVol * 4u, ok - 2 - kZShift, oj - 2, oi - 2);
+                    tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 2 - kZShift, oj - 2,
+                                oi - 2);
                 for (int e = threadIdx.x; e < 6 * LY::jVol / 4; e += blockDim.x)
                     reinterpret_cast<int4*>(sJi)[e] = make_int4(0, 0, 0, 0);
                 // every thread waits for the copy; if it did not land in time,
@@ -924,9 +927,12 @@ cudaError_t launch_tile_step(pic_ctx* c) {
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
 }
 
-bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], int64_t comp_stride, int layout) {
+bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], int64_t comp_stride, int layout,
+                          int prec) {
     std::memset(map, 0, sizeof(*map));
-    if (n[2] % 4 != 0 || comp_stride % 4 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return false;
+    const cuuint64_t rs = prec == PIC_FP64 ? 8 : 4;
+    if ((n[2] * rs) % 16 != 0 || (comp_stride * rs) % 16 != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0)
+        return false;
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
@@ -934,18 +940,19 @@ bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], in
         cudaGetLastError();
         return false;
     }
-    using Row = LayoutRow<float>;
-    using Cube = LayoutCube<float>;
-    const cuuint32_t bz = layout == 1 ? Row::eY : Cube::eY;
-    const cuuint32_t by = layout == 1 ? Row::EY : Cube::EY;
-    const cuuint32_t bx = layout == 1 ? Row::EX : Cube::EX;
+    const bool f64 = prec == PIC_FP64;
+    const cuuint32_t bz = layout == 1 ? (f64 ? LayoutRow<double>::eY : LayoutRow<float>::eY)
+                                      : (f64 ? LayoutCube<double>::eY : LayoutCube<float>::eY);
+    const cuuint32_t by = layout == 1 ? LayoutRow<float>::EY : LayoutCube<float>::EY;  // same for both precisions
+    const cuuint32_t bx = layout == 1 ? LayoutRow<float>::EX : LayoutCube<float>::EX;
     const cuuint64_t nz = cuuint64_t(n[2]), ny = cuuint64_t(n[1]), nx = cuuint64_t(n[0]);
     const cuuint64_t dims[4] = {nz, ny, nx, 6};
-    const cuuint64_t strides[3] = {nz * 4, ny * nz * 4, cuuint64_t(comp_stride) * 4};  // bytes, dimensions 1..3
+    const cuuint64_t strides[3] = {nz * rs, ny * nz * rs, cuuint64_t(comp_stride) * rs};  // bytes, dimensions 1..3
     const cuuint32_t box[4] = {bz, by, bx, 6};
     const cuuint32_t estride[4] = {1, 1, 1, 1};
     const CUresult r = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn)(
-        map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims, strides, box, estride,
+        map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<void*>(base), dims,
+        strides, box, estride,
         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -954,8 +961,7 @@ bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], in
 void setup_tile_tma(pic_ctx* c) {
     c->tma = false;
     std::memset(&c->tmap_eb, 0, sizeof(c->tmap_eb));
-    if (c->prec != PIC_FP32_MIXED) return;
-    c->tma = encode_eb_tensor_map(&c->tmap_eb, c->F[0], c->g.n, c->g.C, c->layout);
+    c->tma = encode_eb_tensor_map(&c->tmap_eb, c->F[0], c->g.n, c->g.C, c->layout, c->prec);
 }
 
 // The tile kernels need more than 48 KB of dynamic shared memory: raise the
