@@ -228,3 +228,17 @@ def test_fp32_mixed_tma_halos(n):
     c.oracle_steps(2)
     e = c.errors()
     assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+def test_tiles_of_two_z_cells_mix_tma_and_loads(precision):
+    """Tiles 4x4x2: tiles whose z origin is a multiple of 4 stage E/B by TMA,
+    the others by loads; both kinds in one launch match the oracle."""
+    c = Case((8, 8, 16), 3, 2, 0.3, 97, precision=precision, field_scale=0.5, tile=(4, 4, 2))
+    c.ctx.step(2)
+    c.oracle_steps(2)
+    e = c.errors()
+    if precision == pic.FP64:
+        assert max(e.values()) < 1e-12, e
+    else:
+        assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
