@@ -394,6 +394,8 @@ def wakefield_statement(torch, steps_cmp=50, steps_fp32=150):
     res["compared_after_steps"] = steps_cmp
     # the paper's particle and field options for this run (Sec. 4.2): Vay pusher,
     # energy-conserving gather, CKC solver at dt = 0.99 dx
+    if steps_fp32 <= 0:
+        return res
     with pic.Context(cfg["n"], dt=0.99, order=cfg["order"], precision=pic.FP32_MIXED, window_speed=cfg["speed"],
                      stream=s, solver="ckc") as c:
         c.set_particle_algorithms("vay", "energy")

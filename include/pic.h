@@ -160,8 +160,9 @@ pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
  * rises linearly over ramp_length (0 = a step) and is n0 beyond; none where
  * it is zero.  Injected particles take ids counting on from the loaded ones,
  * (i ny + j) ppc + m within a slab.  Call before pic_load_particles (it sizes
- * the particle buffers for a full box of this plasma plus two slabs;
- * exceeding that gives PIC_ERR_STATE).  PIC_ERR_STATE without a window. */
+ * the particle buffers for a full box of this plasma plus two slabs; a step
+ * whose injection would exceed them first grows them by a quarter, keeping
+ * the particles, or returns PIC_ERR_OOM).  PIC_ERR_STATE without a window. */
 pic_status pic_set_window_plasma(pic_ctx* ctx, int32_t ppc, double n0, double ramp_start,
                                  double ramp_length);
 

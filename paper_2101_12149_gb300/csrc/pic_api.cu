@@ -95,6 +95,44 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
     return cudaSuccess;
 }
 
+// Larger particle buffers for a moving-window context whose plasma has
+// outgrown them (particles that travel with the window stay in the box while
+// the front keeps filling): the current buffer's np particles move to buffer
+// 0 of the new pair in the same order; the split-API scratch is dropped and
+// comes back on first use.
+cudaError_t grow_particles(pic_ctx* c, int64_t need) {
+    const int64_t cap2 = std::max<int64_t>(need, c->cap + c->cap / 4);
+    pic_ctx fresh;
+    fresh.rsize = c->rsize;
+    cudaError_t e = alloc_particles(&fresh, cap2);
+    if (e != cudaSuccess) {
+        free_particles(&fresh);
+        return e;
+    }
+    const PartBuf& src = c->P[c->cur];
+    const size_t n = size_t(c->np);
+    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(fresh.P[0].a[i], src.a[i], n * c->rsize, cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fresh.P[0].key, src.key, n * sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(fresh.P[0].id, src.id, n * sizeof(int), cudaMemcpyDeviceToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        free_particles(&fresh);
+        return e;
+    }
+    const int64_t np = c->np;
+    free_particles(c);
+    c->P[0] = fresh.P[0];
+    c->P[1] = fresh.P[1];
+    c->outl = fresh.outl;
+    c->cap = fresh.cap;
+    c->np = np;
+    c->cur = 0;
+    return cudaSuccess;
+}
+
 }  // namespace pic
 
 namespace {
@@ -242,7 +280,11 @@ pic_status run_window_step(pic_ctx* c) {
         c->shifts += 1;
         if (c->inj_ppc > 0) {
             const int64_t total = int64_t(c->g.n[0]) * c->g.n[1] * c->inj_ppc;
-            if (c->np + total > c->cap) return fail(PIC_ERR_STATE, "particle capacity exceeded by injection");
+            if (c->np + total > c->cap) {
+                const cudaError_t e = pic::grow_particles(c, c->np + 4 * total);
+                if (e == cudaErrorMemoryAllocation) return fail(PIC_ERR_OOM, "particle buffers for the injected plasma");
+                PIC_CUDA(e);
+            }
             PIC_CUDA(counted(c, "k_inject", 1, inject));
             c->np += total;
             c->next_id += total;

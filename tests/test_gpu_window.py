@@ -164,3 +164,26 @@ def test_wakefield_full_size_sampled():
     d = c.diagnostics()
     assert abs(d["max_div_b"] - divb0) < 1e-3 * divb0
     c.close()
+
+
+def test_particle_buffers_grow_when_the_box_overfills():
+    """Plasma that travels with the window (u_z = 50, v = 0.9998 c) stays in
+    the box while every shift injects a new front slab, so the live count
+    passes the buffers sized at load (a full box plus two slabs): the step
+    grows them, keeps every particle, and still matches the oracle."""
+    cfg = CFG
+    n = cfg["n"]
+    parts = inputs.uniform_plasma(31, n, cfg["ppc"], sigma_u=0.0)
+    parts["uz"][:] = 50.0
+    c = pic.Context(n, cfl=cfg["cfl"], order=cfg["order"], precision=pic.FP64, window_speed=cfg["speed"])
+    c.set_window_plasma(cfg["ppc"], inputs.wakefield_plasma_density(cfg), cfg["ramp_start"], cfg["ramp_length"])
+    c.set_fields(inputs.laser_fields(cfg))
+    c.load_particles(-1.0, 1.0, parts)
+    steps = 14
+    c.step(steps)
+    P, F, win = _oracle(cfg, parts, steps)
+    slab = n[0] * n[1] * cfg["ppc"]
+    assert c.num_particles() > n[0] * n[1] * n[2] * cfg["ppc"] + 2 * slab
+    e = _compare(c, P, F, n)
+    assert max(e.values()) < 1e-12, e
+    c.close()
