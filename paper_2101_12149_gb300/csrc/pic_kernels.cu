@@ -459,9 +459,8 @@ __device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJ
 }
 
 // One tile t of the box described by A, by the whole CTA; `smem_raw` is the
-// CTA's dynamic shared memory; `tmap` the TMA descriptor of E/B for the
-// FP32-mixed 4x4x32 layout (null: staged by loads).  Returns with the block
-// converged.
+// CTA's dynamic shared memory; `tmap` the TMA descriptor of the box's E/B
+// (null: staged by loads).  Returns with the block converged.
 template <int P, typename R, class LY>
 __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw,
                                           const CUtensorMap* tmap = nullptr) {
