@@ -95,10 +95,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, prec):
+def profiled_traffic(kernel, prec, workload=WORKLOAD):
     """DRAM bytes per launch from the committed ncu summary, or None when the
     summary is absent or was taken on a different kernel source."""
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}_{prec}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_{prec}.md")
     if not os.path.exists(path):
         return None
     src_hash, traffic = None, None
@@ -229,8 +229,11 @@ def run_reference(args):
     rank, _, _ = dist_env()
     if rank != 0:
         return
-    from __graft_entry__ import build
-    build()
+    # this arm builds and loads only the oracle and the input generator
+    from oracle import build as obuild
+    from paper_2101_12149_gb300.inputs import build as ibuild
+    obuild.build()
+    ibuild()
     from oracle import Oracle
     from paper_2101_12149_gb300 import inputs
     w = inputs.WORKLOADS[WORKLOAD]
@@ -527,6 +530,8 @@ def main():
                     help="run the same recipe on an N^3 grid instead of 256^3 (small cases for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the timed headline run")
+    ap.add_argument("--workload", default=WORKLOAD, choices=["uniform_256", "uniform_256_o1"],
+                    help="recipe of the timed run (uniform_256: order 3, 8 ppc; uniform_256_o1: order 1, 2 ppc)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -548,7 +553,7 @@ def main():
         build()
     from paper_2101_12149_gb300 import inputs, pic
 
-    w = inputs.WORKLOADS[WORKLOAD]
+    w = inputs.WORKLOADS[args.workload]
     n, ppc, order = w["n"], w["ppc"], w["order"]
     if args.grid:
         n = (args.grid,) * 3
@@ -603,7 +608,7 @@ def main():
     hbm = bytes_per_launch(N, C, args.precision) / avg_tile_s / 1e9 if avg_tile_s > 0 else None
     alu_frac = alu_tf / alu_peak if alu_tf else None
     hbm_frac = hbm / peaks["hbm_gbs"] if hbm else None
-    traffic = profiled_traffic("k_tile_step", args.precision) if not args.grid else None
+    traffic = profiled_traffic("k_tile_step", args.precision, args.workload) if not args.grid else None
     roof_alu = {"bound": "alu", "achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
                 "traffic": traffic, "kernel": "k_tile_step",
                 "note": ("FP32 ALU roof derived from 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
@@ -622,11 +627,11 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32-mixed" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if not args.grid else f"{WORKLOAD} recipe at {args.grid}^3",
+        "config": {"workload": args.workload if not args.grid else f"{args.workload} recipe at {args.grid}^3",
                    "grid": f"{n[0]}^3", "ppc": ppc, "particles": N, "order": order,
                    "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": 1,
                    "precision": "fp32_mixed" if args.precision == "fp32" else "fp64",
-                   "l2": "inputs larger than L2 (4.8 GB of particle state per step)",
+                   "l2": f"inputs larger than L2 ({N * 36 / 1e9:.1f} GB of particle state per step)",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof_alu if (alu_frac or 0) >= (hbm_frac or 0) else roof_hbm,
         "roofline_alt": roof_hbm if (alu_frac or 0) >= (hbm_frac or 0) else roof_alu,

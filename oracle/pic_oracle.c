@@ -326,7 +326,11 @@ void orc_deposit_rho(const orc_grid* g, int p, double qw, const double x[3], dou
             for (int r2 = 0; r2 < NR; ++r2) {
                 const double wgt = wt[0][r0] * wt[1][r1] * wt[2][r2];
                 if (wgt == 0.0) continue;
+#if ORC_MUTANT == 14
+                add_to(g, rho, first[0] + r0, first[1] + r1, first[2] + r2, qw * wgt);
+#else
                 add_to(g, rho, first[0] + r0, first[1] + r1, first[2] + r2, qw * wgt / dV);
+#endif
             }
 }
 
@@ -540,13 +544,19 @@ void orc_div_face(const orc_grid* g, const double* const F[3], double* out) {
             }
 }
 
-/* Field energy 1/2 sum (|E|^2 + |B|^2) dV and kinetic energy sum w m (gamma-1). */
+/* Field energy 1/2 sum (|E|^2 + |B|^2) dV and kinetic energy sum w m (gamma-1)
+ * (the in-situ reductions of Sec. 2.6; energy density |E|^2/2 + |B|^2/2 in
+ * these units). */
 double orc_field_energy(const orc_grid* g, const double* const F[6]) {
     const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
     double s = 0.0;
     for (int c = 0; c < 6; ++c)
         for (int64_t i = 0; i < C; ++i) s += F[c][i] * F[c][i];
+#if ORC_MUTANT == 12
+    return 0.5 * s;
+#else
     return 0.5 * s * g->d[0] * g->d[1] * g->d[2];
+#endif
 }
 
 double orc_kinetic_energy(double m, int64_t np, const double* ux, const double* uy, const double* uz,
@@ -554,7 +564,11 @@ double orc_kinetic_energy(double m, int64_t np, const double* ux, const double* 
     double s = 0.0;
     for (int64_t n = 0; n < np; ++n) {
         const double u2 = ux[n] * ux[n] + uy[n] * uy[n] + uz[n] * uz[n];
+#if ORC_MUTANT == 13
+        s += w[n] * m * sqrt(1.0 + u2);
+#else
         s += w[n] * m * (sqrt(1.0 + u2) - 1.0);
+#endif
     }
     return s;
 }

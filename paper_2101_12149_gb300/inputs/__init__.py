@@ -15,6 +15,7 @@ Sec. 4.2; normalised units, electrons q = -1, m = 1, cell size 1):
   wakefield     128 x 128 x 1024, 2 ppc, order 2, moving window, laser a0 = 2
   ensemble      96 boxes with edges in {16,24,32,48,64}, 1-8 ppc, n in [0.1, 10], order 1 or 3
   adjoint_64    64^3, 4 ppc, order 2, external plane-wave drive, 200 steps
+  uniform_256_o1  256^3, 2 ppc, order 1, u ~ N(0, 0.05), n = 1 (the memory-bound case)
   WAKEFIELD     128 x 128 x 1024, moving window along z, laser + ramped plasma
   ENSEMBLE      96 independent boxes of uneven sizes
 """
@@ -39,6 +40,11 @@ WORKLOADS = {
                         pert_amp=0.0, pert_k=0.0, cfl=0.99, steps=100, seed=1),
     "adjoint_64": dict(n=(64, 64, 64), ppc=4, order=2, sigma_u=0.05, density=1.0,
                        pert_amp=0.0, pert_k=0.0, cfl=0.99, steps=200, seed=4),
+    # the 2-particle-per-cell, order-1 case on the full-size grid: the
+    # memory-bound end of the method (Sec. 4.2 notes that wakefield runs use
+    # about 2 particles per cell)
+    "uniform_256_o1": dict(n=(256, 256, 256), ppc=2, order=1, sigma_u=0.05, density=1.0,
+                           pert_amp=0.0, pert_k=0.0, cfl=0.99, steps=100, seed=5),
 }
 
 

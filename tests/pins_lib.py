@@ -550,3 +550,88 @@ def pin_ckc_stable_at_courant_one(O):
 
 
 ALL_PINS.append(pin_ckc_stable_at_courant_one)
+
+
+# ---------------------------------------------------------------- diagnostics
+
+def pin_field_energy_modes(O):
+    """Field energy of discrete Fourier modes.  Component c holding
+    A_c cos(2 pi m_c.i/n + phi_c) has sum over the grid of squares exactly
+    C A_c^2 / 2 whenever 2 m_c is not a multiple of n along some axis (the
+    cos(2 theta) part sums to zero), so 1/2 sum (|E|^2 + |B|^2) dV =
+    (C dV / 4) sum_c A_c^2; on non-unit cells, with a different amplitude,
+    mode and phase per component."""
+    n, d = (6, 4, 10), (0.5, 2.0, 1.5)
+    g = O.grid(n, d)
+    idx = np.indices(n).astype(np.float64)
+    modes = [(1, 1, 3), (2, 0, 1), (0, 1, 4), (1, 0, 0), (5, 3, 2), (1, 1, 1)]
+    amps = [0.7, 1.3, 0.25, 2.0, 0.9, 1.1]
+    F = np.zeros((9,) + n)
+    for c, (m, a) in enumerate(zip(modes, amps)):
+        ph = 2 * np.pi * sum(m[k] * idx[k] / n[k] for k in range(3)) + 0.37 * (c + 1)
+        F[c] = a * np.cos(ph)
+    C, dV = np.prod(n), np.prod(d)
+    ref = 0.25 * C * dV * sum(a * a for a in amps)
+    got = O.field_energy(g, F)
+    assert abs(got - ref) < 1e-13 * ref, f"field energy {got} vs mode sum {ref}"
+    # a single non-zero value: 1/2 v^2 dV
+    G = np.zeros((9,) + n)
+    G[4, 2, 1, 7] = 3.0
+    assert abs(O.field_energy(g, G) - 0.5 * 9.0 * dV) < 1e-15 * 4.5 * dV
+
+
+def pin_kinetic_energy_values(O):
+    """Kinetic energy sum w m (gamma - 1) at momenta whose gamma is exact:
+    |u|^2 = 3 gives gamma = 2, |u|^2 = 9/16 gives 5/4, |u|^2 = 144/25 gives
+    13/5; the non-relativistic limit 1/2 w m |u|^2 (1 - |u|^2/4) to O(u^6);
+    and the ultra-relativistic |u| = 1e6 (gamma - 1 = 999999.0000005)."""
+    m = 3.5
+    u = np.array([[1.0, 1.0, 1.0], [0.0, 0.75, 0.0], [0.0, 0.0, -2.4], [1e6, 0.0, 0.0]])
+    w = np.array([0.25, 2.0, 1.5, 1e-3])
+    gm1 = np.array([1.0, 0.25, 1.6, 999999.0000005])
+    ref = float(np.sum(w * m * gm1))
+    got = O.kinetic_energy(m, u[:, 0], u[:, 1], u[:, 2], w)
+    assert abs(got - ref) < 1e-13 * ref, f"kinetic energy {got} vs {ref}"
+    # per particle: each on its own
+    for k in range(4):
+        one = O.kinetic_energy(m, u[k:k + 1, 0], u[k:k + 1, 1], u[k:k + 1, 2], w[k:k + 1])
+        assert abs(one - w[k] * m * gm1[k]) < 1e-13 * w[k] * m * gm1[k], f"particle {k}"
+    # non-relativistic limit
+    rng = np.random.default_rng(21)
+    v = rng.normal(size=(50, 3)) * 1e-3
+    ww = rng.uniform(0.5, 2.0, 50)
+    u2 = np.sum(v * v, axis=1)
+    approx = float(np.sum(0.5 * ww * m * u2 * (1.0 - 0.25 * u2)))
+    got = O.kinetic_energy(m, v[:, 0], v[:, 1], v[:, 2], ww)
+    assert abs(got - approx) < 1e-9 * approx, "non-relativistic limit"
+
+
+def pin_rho_values(O):
+    """Nodal charge density: a particle on a node spreads q w / dV with the
+    shape's node values (p = 1: all on the node; p = 2: 1/8, 3/4, 1/8 per
+    axis; p = 3: 1/6, 2/3, 1/6), the total charge sum rho dV is q w, and the
+    first moment sum x_node rho dV is q w x (linear reproduction), on
+    non-unit cells."""
+    n, d = (8, 8, 8), (0.5, 2.0, 1.25)
+    g = O.grid(n, d)
+    dV = np.prod(d)
+    node_w = {1: [1.0], 2: [0.125, 0.75, 0.125], 3: [1 / 6, 2 / 3, 1 / 6]}
+    q, wq = -1.0, 0.3
+    for p in (1, 2, 3):
+        x = np.array([3 * d[0]]), np.array([4 * d[1]]), np.array([2 * d[2]])
+        r = O.rho(g, p, q, *x, np.array([wq]))
+        s = np.array(node_w[p])
+        h = len(s) // 2
+        ref = np.zeros(n)
+        ref[3 - h:3 + h + 1, 4 - h:4 + h + 1, 2 - h:2 + h + 1] = q * wq / dV * np.einsum("i,j,k->ijk", s, s, s)
+        assert np.max(np.abs(r - ref)) < 1e-15, f"rho of a particle on a node, p={p}"
+        pos = [np.array([v]) for v in (3.3 * d[0], 4.71 * d[1], 3.05 * d[2])]
+        r = O.rho(g, p, q, *pos, np.array([wq]))
+        assert abs(r.sum() * dV - q * wq) < 1e-15, f"total charge p={p}"
+        for a in range(3):
+            coord = np.arange(n[a]) * d[a]
+            mom = np.tensordot(r, coord, axes=([a], [0])).sum() * dV
+            assert abs(mom - q * wq * pos[a][0]) < 1e-14, f"first moment p={p} axis {a}"
+
+
+ALL_PINS.extend([pin_field_energy_modes, pin_kinetic_energy_values, pin_rho_values])

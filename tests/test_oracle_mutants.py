@@ -5,7 +5,9 @@ oracle/pic_oracle.c): a wrong shape piece, a missing staggering offset, a
 dropped Boris half kick, an Esirkepov window off by one node, 1/2 for 1/3 in
 Esirkepov's W, a flipped curl sign, a flipped current sign, momentum used as
 velocity, an energy-conserving gather that keeps order p for one component,
-a Vay pusher without its explicit magnetic half.  Every mutant must fail at
+a Vay pusher without its explicit magnetic half, CKC with the wrong
+transverse weights, a field energy without the cell volume, a kinetic
+energy of gamma m instead of (gamma - 1) m, a charge density without 1/dV.  Every mutant must fail at
 least one pin.
 """
 import pytest
@@ -25,6 +27,9 @@ MUTANTS = {
     9: "energy-conserving gather keeps order p for E_y",
     10: "Vay without the explicit half of v x B",
     11: "CKC with box-average weights",
+    12: "field energy without the cell volume",
+    13: "kinetic energy gamma m in place of (gamma - 1) m",
+    14: "charge density without 1/dV",
 }
 
 
