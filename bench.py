@@ -30,10 +30,29 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "uniform_256"
 METRIC = "particle-steps/s (gather+push+deposit+Yee), FP32-mixed vs FP64 at stated error"
 UNIT = "particle-steps/s"
-# FP32 ALU roof of one GB300: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz max SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# ALU roof of FP64 (CUDA cores) on GB300, public dense FP64 figure
-FP64_PEAK_TFLOPS = 1.25
+
+
+def derived_fp32_tflops(sms, mhz):
+    """FP32 ALU roof from the device: SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def derived_smem_gbs(sms, mhz):
+    """Shared-memory roof from the device: SMs x 32 banks x 4 B per clock x SM clock."""
+    return sms * 128 * mhz * 1e6 / 1e9
+
+
+def device_roofs(torch, pic, local, clock_summary, peaks):
+    """SM count and maximum SM clock read from the device and nvidia-smi, the
+    derived FP32 and shared-memory roofs, and the FP32 / FP64 FMA throughput
+    measured by the library's microbenchmark (the ALU peaks used)."""
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    mhz = clock_summary.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    return {"sms": sms, "sm_max_mhz": mhz,
+            "fp32_derived_tflops": derived_fp32_tflops(sms, mhz),
+            "smem_derived_gbs": derived_smem_gbs(sms, mhz),
+            "fp32_measured_tflops": pic.measure_fma_peak(pic.FP32_MIXED),
+            "fp64_measured_tflops": pic.measure_fma_peak(pic.FP64)}
 
 
 def flops_per_particle(p: int) -> int:
@@ -47,9 +66,6 @@ def flops_per_particle(p: int) -> int:
     esirk = 3 * NW + 3 * (2 * (NW - 1) + 8 * NW * NW + 2 * NW * NW * (NW - 1))
     return gather + weights + boris + advance + esirk
 
-
-# shared-memory roof: 32 banks x 4 B per clock per SM
-SMEM_PEAK_GBS = 152 * 128 * 2.07e9 / 1e9
 
 
 def smem_bytes_per_particle(p: int, prec: str) -> int:
@@ -202,6 +218,35 @@ def cpu_baseline(seconds_target=15.0):
                       f"{el:.1f} s, 1 host core"}
 
 
+def cpu_baseline_mt(seconds_target=15.0, workload=WORKLOAD, n=(64, 64, 64)):
+    """The multi-threaded CPU baseline (oracle/pic_oracle_mt.c: OpenMP,
+    private current arrays summed in thread order, the CPU deposition of
+    Sec. 3.4.1) on every host core, on a bounded sample of the workload (the
+    same recipe on a 64^3 box), a few full steps."""
+    from oracle import Oracle, OracleMT
+    from paper_2101_12149_gb300 import inputs
+    w = inputs.WORKLOADS[workload]
+    M = OracleMT(os.cpu_count() or 1)
+    g = Oracle.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+    parts = inputs.uniform_plasma(w["seed"], n, w["ppc"], sigma_u=w["sigma_u"], density=w["density"])
+    F = np.zeros((9,) + n)
+    N = parts["x"].size
+    M.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F)  # first touch of the private arrays
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        M.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F, 0.0, 0.0, (steps + 1) * dt)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds_target or steps >= 50:
+            break
+    return {"value": N * steps / el, "unit": UNIT, "cores": M.nthreads, "kind": "oracle_mt",
+            "sample": f"OpenMP baseline on the same recipe at {n[0]}^3 ({N} particles, order {w['order']}, "
+                      f"{w['ppc']} ppc), {steps} steps, {el:.1f} s, {M.nthreads} threads on "
+                      f"{os.cpu_count()} host cores"}
+
+
 def dist_env():
     """(rank, world size, local rank) from the launcher's environment."""
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
@@ -303,6 +348,60 @@ def field_error_statement(torch, steps=100):
     return res
 
 
+def step_bytes(np_, C, prec="fp32", sort=True):
+    """Algorithmic HBM bytes of one whole step: the tile kernel's (particle
+    state read and written once, E/B read and J written once per cell), the
+    field update's three passes (B half step: E, B read, B written; E step: E,
+    B, J read, E written; B half step again) and, when the particles are
+    sorted that step, the sort (key read by the histogram, every particle
+    array read and written by the scatter: FP32-mixed 76 B, FP64 144 B a
+    particle)."""
+    rs = 4 if prec == "fp32" else 8
+    yee = C * rs * (9 + 12 + 9)
+    srt = np_ * (76 if prec == "fp32" else 144) if sort else 0
+    return bytes_per_launch(np_, C, prec) + yee + srt
+
+
+def hbm_leg_statement(torch, stream, peaks, steps=20, warmup=3):
+    """The memory-bound end of the method: order 1, 2 particles per cell on the
+    full 256^3 grid (33,554,432 particles), FP32-mixed.  The step loop timed
+    as the library runs it (CUDA events on the launching stream), then again
+    with per-kernel events; the tile kernel's algorithmic bytes (60 B a
+    particle, 36 B a cell) over its time against the measured HBM copy rate,
+    and the whole step's (tile kernel, sort and field update)."""
+    from paper_2101_12149_gb300 import inputs, pic
+    w = inputs.WORKLOADS["uniform_256_o1"]
+    n, ppc = w["n"], w["ppc"]
+    C = n[0] * n[1] * n[2]
+    N = C * ppc
+    parts = inputs.workload_particles("uniform_256_o1")
+    dev = {k: torch.from_numpy(v).to(torch.cuda.current_device()) for k, v in parts.items()}
+    with pic.Context(n, cfl=w["cfl"], order=w["order"], precision=pic.FP32_MIXED, stream=stream) as ctx:
+        ctx.load_particles(-1.0, 1.0, dev)
+        del dev
+        ctx.step(warmup)
+        t = timed_run(ctx, steps, stream, torch)
+        ctx.set_timing(True)
+        timed_run(ctx, steps, stream, torch)
+        tm = ctx.get_timing()
+    torch.cuda.empty_cache()
+    ms_tile, n_tile = tm.get("k_tile_step", (0.0, 0))
+    t_tile = ms_tile / max(n_tile, 1) / 1e3
+    tile_gbs = bytes_per_launch(N, C, "fp32") / t_tile / 1e9
+    step_gbs = step_bytes(N, C) * steps / t / 1e9
+    return {"workload": "uniform_256_o1", "grid": "256^3", "ppc": ppc, "order": 1, "particles": N,
+            "precision": "fp32_mixed", "steps": steps, "ms_per_step": 1e3 * t / steps,
+            "particle_steps_per_s": N * steps / t, "cell_steps_per_s": C * steps / t,
+            "fom_per_gpu": C * (0.1 + 0.9 * ppc) / (t / steps),
+            "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in tm.items()},
+            "roofline": {"bound": "hbm", "kernel": "k_tile_step", "achieved": tile_gbs, "peak": peaks["hbm_gbs"],
+                         "unit": "GB/s", "frac": tile_gbs / peaks["hbm_gbs"],
+                         "bytes": "60 B a particle + 36 B a cell per launch"},
+            "step_roofline": {"achieved": step_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": step_gbs / peaks["hbm_gbs"],
+                              "bytes": "tile kernel + sort (76 B a particle) + field update (120 B a cell)"}}
+
+
 def ensemble_statement(torch, stream, steps=20):
     """The batched ensemble (96 uneven periodic boxes, FP32-mixed): autotuned,
     then `steps` steps timed as one graph replay with CUDA events on the
@@ -391,6 +490,14 @@ def wakefield_statement(torch, steps_cmp=50, steps_fp32=150):
                 r["particle_steps_per_s"] = 0.5 * (np0 + c.num_particles()) * steps_fp32 / t2
                 r["cell_steps_per_s"] = C * steps_fp32 / t2
                 r["shifts_end"] = c.window()["shifts"]
+                # the whole step's algorithmic bytes (tile kernel, sort, field
+                # update; the window shift's field and particle moves left out)
+                # against the measured HBM copy rate
+                npm = 0.5 * (np0 + c.num_particles())
+                gbs = step_bytes(npm, C) / (t2 / steps_fp32) / 1e9
+                peak = measured_peaks()[0]["hbm_gbs"]
+                r["step_roofline"] = {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                      "bytes": "tile kernel + sort + field update"}
             res[name] = r
     res["fp32_field_rel_l2_vs_fp64"] = float(np.linalg.norm(fields["fp32_mixed"] - fields["fp64"]) /
                                              np.linalg.norm(fields["fp64"]))
@@ -600,10 +707,12 @@ def main():
     ctx.close()
 
     peaks, peak_kind = measured_peaks()
+    clocks = clk.summary()
+    roofs = device_roofs(torch, pic, local, clocks, peaks)
     ms_tile, n_tile = timings.get("k_tile_step", (0.0, 0))
     avg_tile_s = ms_tile / max(n_tile, 1) / 1e3
     flops = N * flops_per_particle(order)
-    alu_peak = FP32_PEAK_TFLOPS if args.precision == "fp32" else FP64_PEAK_TFLOPS
+    alu_peak = roofs["fp32_measured_tflops"] if args.precision == "fp32" else roofs["fp64_measured_tflops"]
     alu_tf = flops / avg_tile_s / 1e12 if avg_tile_s > 0 else None
     hbm = bytes_per_launch(N, C, args.precision) / avg_tile_s / 1e9 if avg_tile_s > 0 else None
     alu_frac = alu_tf / alu_peak if alu_tf else None
@@ -611,15 +720,19 @@ def main():
     traffic = profiled_traffic("k_tile_step", args.precision, args.workload) if not args.grid else None
     roof_alu = {"bound": "alu", "achieved": alu_tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu_frac,
                 "traffic": traffic, "kernel": "k_tile_step",
-                "note": ("FP32 ALU roof derived from 152 SMs x 128 lanes x 2 x 2.07 GHz" if args.precision == "fp32"
-                         else "FP64 roof: GB300 dense FP64 1.25 TFLOP/s") +
-                        f"; algorithmic flops {flops_per_particle(order)} per particle"}
+                "peak_source": ("measured FP32 FMA microbenchmark (pic_measure_fma_peak)" if args.precision == "fp32"
+                                else "measured FP64 FMA microbenchmark (pic_measure_fma_peak)"),
+                "note": f"derived FP32 roof {roofs['fp32_derived_tflops']:.1f} TFLOP/s ({roofs['sms']} SMs x 128 "
+                        f"lanes x 2 x {roofs['sm_max_mhz']:.0f} MHz); algorithmic flops "
+                        f"{flops_per_particle(order)} per particle"}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": hbm_frac,
                 "traffic": traffic, "kernel": "k_tile_step", "peak_source": f"{peak_kind} hbm_gbs"}
+    smem_peak = roofs["smem_derived_gbs"]
     smem = N * smem_bytes_per_particle(order, args.precision) / avg_tile_s / 1e9 if avg_tile_s > 0 else None
-    roof_smem = {"bound": "smem", "achieved": smem, "peak": SMEM_PEAK_GBS, "unit": "GB/s",
-                 "frac": smem / SMEM_PEAK_GBS if smem else None, "kernel": "k_tile_step",
-                 "note": "shared-memory roof derived from 152 SMs x 128 B/clock x 2.07 GHz; algorithmic bytes "
+    roof_smem = {"bound": "smem", "achieved": smem, "peak": smem_peak, "unit": "GB/s",
+                 "frac": smem / smem_peak if smem else None, "kernel": "k_tile_step",
+                 "note": f"shared-memory roof derived from {roofs['sms']} SMs x 128 B/clock x "
+                         f"{roofs['sm_max_mhz']:.0f} MHz; algorithmic bytes "
                          f"{smem_bytes_per_particle(order, args.precision)} per particle (gather loads + narrow "
                          "deposit reductions); the ncu profile gives the pipe's busy fraction including bank "
                          "conflicts and the two cycles of each reduction"}
@@ -640,7 +753,12 @@ def main():
         "ms_per_step_with_kernel_events": 1e3 * t_evented / args.steps,
         "kernel_share": {k: v[0] / max(sum(x[0] for x in timings.values()), 1e-30) for k, v in timings.items()},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clocks,
+        "device_roofs": roofs,
+        # context metrics: cells advanced per second and the paper's figure of
+        # merit per GPU, cells (0.1 + 0.9 ppc) / time per step (Sec. 4.2)
+        "cell_steps_per_s": job_throughput(world, C, args.steps, t),
+        "fom_per_gpu": C * (0.1 + 0.9 * ppc) / (t / args.steps),
     }
 
     if not args.no_extras:
@@ -683,7 +801,7 @@ def main():
         line["fp64"] = {"value": job_throughput(world, N, args.fp64_steps, t64),
                         "ms_per_step": 1e3 * t64 / args.fp64_steps,
                         "steps": args.fp64_steps, "tile_kernel_tflops": fl64,
-                        "tile_kernel_frac_of_fp64_peak": fl64 / FP64_PEAK_TFLOPS if fl64 else None,
+                        "tile_kernel_frac_of_fp64_peak": fl64 / roofs["fp64_measured_tflops"] if fl64 else None,
                         "fp32_mixed_speedup": value / job_throughput(world, N, args.fp64_steps, t64)}
         # ---- stated error of FP32-mixed ----------------------------------
         if rank == 0:
@@ -699,12 +817,14 @@ def main():
                                      "ms_per_step": 1e3 * ta / (args.fp64_steps * 3), "steps": args.fp64_steps * 3,
                                      "what": "FP32-mixed, Vay pusher and energy-conserving gather"}
         if rank == 0:
+            line["hbm_bound"] = hbm_leg_statement(torch, stream, peaks)
             line["ensemble"] = ensemble_statement(torch, stream)
             line["adjoint"] = adjoint_statement(torch)
             line["sort_study"] = sort_study_statement(torch, stream, host, n)
             line["wakefield"] = wakefield_statement(torch)
         if rank == 0 and world == 1:
             line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline_mt"] = cpu_baseline_mt()
 
     if rank == 0:
         print(json.dumps(line), flush=True)

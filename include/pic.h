@@ -22,8 +22,11 @@
  * x^{n+1} = x^n + dt u/gamma -> Esirkepov J^{n+1/2} -> B half step, E full
  * step with -dt J, B half step.
  *
- * Ownership.  The context owns every device buffer; all of them are
- * allocated by pic_init_grid / pic_load_particles and none inside a step.
+ * Ownership.  The context owns every device buffer; they are allocated by
+ * pic_init_grid (fields, sort state, a 32 MiB host-copy staging buffer) and
+ * pic_load_particles (particle buffers), by the first call that needs an
+ * optional one (the split API's scratch, the charge density of
+ * pic_charge_density), and by pic_reserve_adjoint; none inside pic_step.
  * Arrays passed in are copied; the caller keeps ownership.  Getters copy out
  * into caller memory.  `on_device` = 1 means the pointer is device memory of
  * the context's GPU, 0 means host memory (pageable or pinned).
@@ -100,8 +103,8 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
  * assigns ids 0..n-1 in input order and sorts the particles by cell.
  * on_device = 0: host arrays; when all seven are in pinned (page-locked,
  * device-mapped) memory the load kernel reads them directly over the host
- * link, otherwise they pass through a device staging buffer of at most
- * 2^23 particles at a time.  Returns when the load is complete.
+ * link, otherwise they pass through the context's 32 MiB staging buffer
+ * (599,186 particles at a time).  Returns when the load is complete.
  * PIC_ERR_ARG if n < 0 or n >= 2^31, a pointer is NULL with n > 0, or a
  * value is non-finite. */
 pic_status pic_load_particles(pic_ctx* ctx, double q, double m, int64_t n,
@@ -198,16 +201,33 @@ pic_status pic_get_window(pic_ctx* ctx, int64_t* shifts, double* z_lab);
  * dL_du0: 3*n doubles, written (may be NULL): dL/du at the current state,
  *   component-major (all ux, then uy, then uz), each component in particle
  *   load order (by id).  Host memory unless on_device = 1.
- * ckpt_every >= 1.  The call allocates its work space (about
- *   (ceil(nsteps/ckpt_every) + ckpt_every + 1) states plus the adjoint
- *   arrays) and frees it before returning; PIC_ERR_OOM if that fails.
+ * ckpt_every >= 1.  Work space: about (ceil(nsteps/ckpt_every) + ckpt_every
+ *   + 1) stored states plus the adjoint arrays and the staging of dL_du0.
+ *   It is the space kept by pic_reserve_adjoint when that is large enough
+ *   (then the call allocates nothing); otherwise the call allocates it and
+ *   frees it before returning; PIC_ERR_OOM if that fails.
  * On return the context holds the state after the nsteps steps, as after
  * pic_step(ctx, nsteps).  Waits.  PIC_ERR_STATE if no particles are loaded
  * or the context has a moving window (periodic grids only). */
 pic_status pic_step_adjoint(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every, double* loss,
                             double* dL_dA, double* dL_du0, int on_device);
 
-/* Copy one field component (PIC_EX..PIC_JZ) out as FP64 / in from FP64. */
+/* Allocate and keep the work space of pic_step_adjoint for nsteps steps
+ * with checkpoints every ckpt_every steps at the current particle capacity,
+ * so that those adjoint calls (and any shorter ones) allocate nothing inside
+ * the step loop.  Replaces an earlier reservation; nsteps = 0 releases it.
+ * The space is sized by the particle buffers: a later pic_load_particles
+ * with more particles needs a new reservation (until then the adjoint
+ * allocates for the call).  PIC_ERR_STATE before pic_load_particles,
+ * PIC_ERR_OOM if the allocation fails.  Waits.  (The paper has no adjoint;
+ * this follows its Sec. 3.2: device allocation is costly, so buffers are
+ * taken once and kept, not allocated inside the time step.) */
+pic_status pic_reserve_adjoint(pic_ctx* ctx, int32_t nsteps, int32_t ckpt_every);
+
+/* Copy one field component (PIC_EX..PIC_JZ) out as FP64 / in from FP64.
+ * With host memory and the FP32-mixed precision the values pass through the
+ * context's 32 MiB staging buffer (converted on the device), chunk by chunk;
+ * nothing is allocated.  Waits. */
 pic_status pic_get_field(pic_ctx* ctx, int32_t which, double* dst, int on_device);
 pic_status pic_set_field(pic_ctx* ctx, int32_t which, const double* src, int on_device);
 
@@ -216,7 +236,9 @@ pic_status pic_num_particles(pic_ctx* ctx, int64_t* n);
 
 /* Copy particle state out as FP64 (positions in [0, L)), in the library's
  * current (cell-sorted) order; `id` gives each particle's load index.  Any
- * pointer may be NULL to skip that array. */
+ * pointer may be NULL to skip that array.  To host memory the values pass
+ * through the context's 32 MiB staging buffer, 524,288 particles at a time;
+ * nothing is allocated.  Waits. */
 pic_status pic_get_particles(pic_ctx* ctx, double* x, double* y, double* z,
                              double* ux, double* uy, double* uz, double* w,
                              int32_t* id, int on_device);
@@ -233,6 +255,43 @@ pic_status pic_get_time(pic_ctx* ctx, int64_t* steps, double* t);
  * 1/2 sum(|E|^2+|B|^2) dV, out[1] = kinetic energy sum w m (gamma - 1),
  * out[2] = sum of charge q w, out[3] = max |div B| dV^(1/3).  Waits. */
 pic_status pic_diagnostics(pic_ctx* ctx, double out[4]);
+
+/* Nodal charge density of the current particles (Sec. 3.4.1 deposits
+ * charge and current; rho sits on the nodes):
+ *   rho(i,j,k) = sum_p (q w_p / dV) s_p(x_p/dx - i) s_p(y_p/dy - j) s_p(z_p/dz - k)
+ * with the order-p shapes, folded periodically (z open: nodes beyond the z
+ * ends take nothing).  Deposited on the device in FP64 whatever the
+ * precision (FP32-mixed positions are exact in FP64), order of the additions
+ * free.  dst: C doubles, element (i ny + j) nz + k, host or device memory per
+ * on_device.  The first call of this or the two continuity calls allocates
+ * the diagnostics' two density arrays (2 C doubles), kept until pic_destroy.
+ * Waits. */
+pic_status pic_charge_density(pic_ctx* ctx, double* dst, int on_device);
+
+/* Discrete continuity of the last step (Sec. 3.4.1: the Esirkepov current
+ * conserves charge exactly, rho^{n+1} - rho^n + dt div J^{n+1/2} = 0 node by
+ * node).  pic_continuity_mark deposits rho^n of the current particles and
+ * keeps it.  After exactly one step (pic_step(ctx, 1), or the split API's
+ * gather/push, deposit and Yee calls), pic_continuity_residual deposits
+ * rho^{n+1}, forms r = rho^{n+1} - rho^n + dt div J at every node with the
+ * step's own current (the context's J arrays; div J the nodal difference of
+ * the edge-centred J, periodic) and returns out[0] = max|r| / max|rho^n|,
+ * out[1] = max|r|, out[2] = max|rho^n|; rho^{n+1} then becomes the mark, so
+ * the two calls chain step by step.  With a moving window the residual
+ * covers the z-planes at least order + 2 cells from the z ends (current
+ * beyond the ends is dropped and particles leaving are removed) and a window
+ * shift since the mark is PIC_ERR_STATE, as is a missing mark or any other
+ * number of steps since it.  Waits. */
+pic_status pic_continuity_mark(pic_ctx* ctx);
+pic_status pic_continuity_residual(pic_ctx* ctx, double out[3]);
+
+/* FP32-mixed precision: the Lorentz factor above which the push's magnetic
+ * rotation (Boris: gamma^- and the rotation; Vay: the solve, for |u'| above
+ * it) is computed in FP64 instead of FP32.  Default 1e3; +infinity never
+ * switches, 1 always does.  The FP64 path ignores it.  PIC_ERR_ARG for
+ * gamma < 1 or NaN.  Waits.  (The paper runs FP64 throughout; Sec. 3.1
+ * names reduced precision as a way to cut the memory footprint.) */
+pic_status pic_set_fp64_gamma(pic_ctx* ctx, double gamma);
 
 /* Wait for queued work; returns the device error word's status. */
 pic_status pic_sync(pic_ctx* ctx);
@@ -252,14 +311,16 @@ pic_status pic_launch_count(pic_ctx* ctx, int64_t* n);
 
 /* Counting sort of caller-owned keys that allocates nothing.
  *
- * The paper has no counterpart: this entry point exists for callers that
- * cannot allocate device memory, e.g. code running while a CUDA stream is
- * being captured (where cudaMalloc is not allowed), or hosts that hand a
- * library only the buffers it may touch.  It runs the same histogram,
- * single-pass scan and scatter as the particle sort of pic_step on
- * caller arrays, with its scratch (per-bin counts, the scan's look-back
- * words, an error word) in one static device array of about 16 MiB that
- * every GPU loading the library holds until the process exits.
+ * The paper has no counterpart.  This entry point is for callers that are
+ * not allowed to allocate device memory: a host application that gives a
+ * library only the buffers it may touch and keeps the device's memory budget
+ * to itself, or a loop with timing guarantees where the implicit device-wide
+ * synchronisation of cudaMalloc/cudaFree cannot be afforded.  It runs the same
+ * histogram and single-pass scan as the particle sort of pic_step, then a
+ * scatter of a permutation, on caller arrays.  Its scratch (per-bin counts,
+ * the scan's look-back words, an error word) is one static device array of
+ * about 16 MiB that every GPU loading the library holds until the process
+ * exits; no call allocates or frees anything.
  *
  * keys: n int32 bin indices in [0, nbins) (device memory).
  * offsets: nbins+1 int32 (device, written): offsets[b] is the first slot of
@@ -269,13 +330,18 @@ pic_status pic_launch_count(pic_ctx* ctx, int64_t* n);
  * nbins: 1 .. 4,194,304 (the scratch limit); larger values give PIC_ERR_ARG.
  * cuda_stream: a cudaStream_t (NULL = legacy default stream).
  *
- * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call clears what it uses and waits for
- * completion.  All calls share the one scratch array, so calls that overlap
- * on the GPU (other threads or streams) race: serialise them.
- * PIC_ERR_ARG: bad sizes, NULL arrays, or a key outside [0, nbins);
- * PIC_ERR_TIMEOUT: a bounded device-side wait ran out. */
+ * Set-up: the first call on a device (and the first after that device's
+ * context was reset) looks up the scratch array's device address with
+ * cudaGetSymbolAddress, with that device current; make that first call before
+ * any stream capture.  Each call clears the part of the scratch it uses (the
+ * array keeps the previous call's contents), then waits for its work to
+ * finish and reads the error word.  All calls share the one array, so calls
+ * that overlap on the GPU (from other threads or streams) race: serialise
+ * them.  A CUDA error already pending on the calling thread is left in place
+ * and returned as PIC_ERR_CUDA before anything is launched.
+ * PIC_ERR_ARG: bad sizes, NULL arrays, or a key outside [0, nbins) (the
+ * offsets then count only the keys inside); PIC_ERR_TIMEOUT: a bounded
+ * device-side wait ran out. */
 pic_status pic_sort_keys_noalloc(const int32_t* keys, int64_t n, int32_t nbins, int32_t* offsets,
                                  int32_t* perm, void* cuda_stream);
 
@@ -366,6 +432,15 @@ pic_status pic_batch_destroy(pic_batch* b);
 
 /* Release every buffer of the context (NULL is allowed). */
 pic_status pic_destroy(pic_ctx* ctx);
+
+/* Measured fused multiply-add throughput of the current device in TFLOP/s
+ * (FMA = 2 flops): precision PIC_FP32_MIXED times FP32 FMAs, PIC_FP64 FP64
+ * FMAs.  Independent register FMA chains on every SM, timed with CUDA events
+ * (best of three launches after a warm-up).  The ALU ceiling of the roofline
+ * the paper draws for its kernels (Sec. 3.4, roofline figure), measured
+ * rather than taken from a data sheet.  PIC_ERR_ARG for another precision
+ * or a NULL output.  Waits. */
+pic_status pic_measure_fma_peak(int32_t precision, double* tflops);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* pic_last_error(void);

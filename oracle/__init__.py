@@ -81,6 +81,49 @@ def load(mutant: int = 0):
         return _libs[mutant]
 
 
+_mt_lib = None
+
+
+def load_mt():
+    """The multi-threaded CPU baseline library (OpenMP)."""
+    global _mt_lib
+    with _lock:
+        if _mt_lib is None:
+            lib = ct.CDLL(os.path.abspath(_build.build_mt()))
+            P, D, I, L, G = ct.c_void_p, ct.c_double, ct.c_int, ct.c_int64, ct.POINTER(_Grid)
+            lib.orc_mt_pic_step.restype = None
+            lib.orc_mt_pic_step.argtypes = [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I, I, P]
+            lib.orc_mt_threads.restype = I
+            lib.orc_mt_threads.argtypes = [I]
+            _mt_lib = lib
+        return _mt_lib
+
+
+class OracleMT:
+    """The multi-threaded CPU baseline (pic_oracle_mt.c): the oracle's step on
+    several threads, each depositing into private current arrays that are
+    summed in thread order (the CPU deposition scheme of Sec. 3.4.1)."""
+
+    def __init__(self, nthreads: int = 0):
+        self.lib = load_mt()
+        self.nthreads = int(self.lib.orc_mt_threads(int(nthreads)))
+        self._scratch = np.empty(0)
+
+    def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0, pusher=0, gather=0):
+        keys = ("x", "y", "z", "ux", "uy", "uz", "w")
+        for k in keys:
+            assert parts[k].dtype == np.float64 and parts[k].flags.c_contiguous
+        assert fields.dtype == np.float64 and fields.flags.c_contiguous
+        C = int(g.n[0] * g.n[1] * g.n[2])
+        if self._scratch.size < 3 * C * self.nthreads:
+            self._scratch = np.empty(3 * C * self.nthreads)
+        self.lib.orc_mt_pic_step(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
+                                 *[parts[k].ctypes.data_as(ct.c_void_p) for k in keys],
+                                 (ct.c_void_p * 9)(*[fields[c].ctypes.data for c in range(9)]),
+                                 float(drive_amp), float(drive_k), float(t), int(pusher), int(gather),
+                                 self.nthreads, self._scratch.ctypes.data_as(ct.c_void_p))
+
+
 class Oracle:
     """Thin numpy wrapper over one oracle build."""
 

@@ -35,5 +35,25 @@ def build(mutant: int = 0, force: bool = False) -> str:
     return out
 
 
+MT_SRCS = [SRC, os.path.join(HERE, "pic_oracle_mt.c")]
+
+
+def build_mt(force: bool = False) -> str:
+    """The multi-threaded CPU baseline (OpenMP): the serial oracle's functions
+    plus pic_oracle_mt.c, in a library of its own."""
+    out = os.path.join(BUILD_DIR, "liboracle_mt.so")
+    hdr = os.path.join(HERE, "pic_oracle.h")
+    if (not force and os.path.exists(out)
+            and os.path.getmtime(out) >= max([os.path.getmtime(s) for s in MT_SRCS] + [os.path.getmtime(hdr)])):
+        return out
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    tmp = out + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", *MT_SRCS, "-o", tmp,
+           "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, out)
+    return out
+
+
 if __name__ == "__main__":
     print(build(force=True))

@@ -381,6 +381,24 @@ pic::AdjBuffers adj_buffers(const pic_ctx* c, char* base) {
     return b;
 }
 
+// Work space of pic_step_adjoint: the stored states (checkpoints, one
+// segment's per-step states, the final state), the adjoint arrays and the
+// staging of dL/du0 for a host destination, each 256-byte aligned.
+struct AdjSpace {
+    int nseg = 0, nstates = 0;
+    size_t states = 0, work = 0, out = 0, total = 0;
+    AdjSpace(const pic_ctx* c, int nsteps, int k) {
+        auto align = [](size_t b) { return (b + 255) & ~size_t(255); };
+        nseg = (nsteps + k - 1) / k;
+        const int seg_slots = nsteps > 0 ? (nsteps < k ? nsteps : k) - 1 : 0;
+        nstates = nseg + seg_slots + 1;
+        states = align(size_t(nstates) * StateLayout(c).total);
+        work = align(adj_work_bytes(c));
+        out = align(3 * size_t(c->cap < 1 ? 1 : c->cap) * sizeof(double));
+        total = states + work + out;
+    }
+};
+
 template <typename Fn> cudaError_t adj_counted(pic_ctx* c, int kernels, Fn fn) {
     clear_stale("adjoint kernels");
     cudaError_t e = fn();
@@ -517,6 +535,10 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     c->stream = static_cast<cudaStream_t>(cuda_stream);
     c->rsize = D.precision == PIC_FP64 ? 8 : 4;
     cudaGetDevice(&c->device);
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess || c->sms < 1) {
+        cudaGetLastError();
+        c->sms = 1;
+    }
     pic::Geom& g = c->g;
     // Tiles: 4 x 4 x 32 cells when the grid allows (a warp's lanes then walk
     // one z-row of cells), else the largest powers of two up to 8 per axis.
@@ -540,7 +562,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
             return fail(PIC_ERR_ARG, "tile extents must be powers of two dividing the grid");
         }
     if (T[0] <= 8 && T[1] <= 8 && T[2] <= 8) c->layout = 0;
-    else if (T[0] <= 4 && T[1] <= 4 && T[2] <= 32) c->layout = 1;
+    else if (T[0] <= 4 && T[1] <= 4 && T[2] <= 32) c->layout = D.precision == PIC_FP32_MIXED && D.order == 1 ? 2 : 1;
     else {
         delete c;
         return fail(PIC_ERR_ARG, "tiles must fit 8x8x8 or 4x4x32 cells");
@@ -586,6 +608,7 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
     if ((e = cudaMalloc(&c->d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter allocation");
     if ((e = cudaMemset(c->d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMalloc(&c->dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");
+    if ((e = cudaMalloc(&c->stage, pic::kStageBytes)) != cudaSuccess) return bail(e, "host-copy staging buffer");
     *out = c;
     return PIC_OK;
 }
@@ -602,6 +625,9 @@ pic_status pic_destroy(pic_ctx* c) {
     cudaFree(c->err);
     cudaFree(c->d_step);
     cudaFree(c->dsum);
+    cudaFree(c->stage);
+    cudaFree(c->adj_space);
+    cudaFree(c->rho);
     destroy_timing(c);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     delete c;
@@ -668,8 +694,10 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
             e = pic::launch_load_particles(c, mapped, n, 0);
             loads = 1;
         } else {
-            const int64_t chunk = std::min<int64_t>(n, int64_t(1) << 23);
-            e = cudaMalloc(&staged, 7 * size_t(chunk) * sizeof(double));
+            // the staging buffer is reused chunk after chunk: stream order keeps
+            // each copy behind the load kernel of the chunk before
+            const int64_t chunk = std::min<int64_t>(n, int64_t(pic::kStageBytes / (7 * sizeof(double))));
+            staged = static_cast<double*>(c->stage);
             for (int64_t b0 = 0; e == cudaSuccess && b0 < n; b0 += chunk) {
                 const int64_t cnt = std::min(chunk, n - b0);
                 const double* part[7];
@@ -688,7 +716,6 @@ pic_status pic_load_particles(pic_ctx* c, double q, double m, int64_t n, const d
     }
     if (e == cudaSuccess) c->launches += loads;
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (staged) cudaFree(staged);
     if (e != cudaSuccess) return cuda_fail(e, n > 0 ? "particle load kernel" : "particle load");
     unsigned hw[8];
     PIC_CUDA(cudaMemcpy(hw, c->err, sizeof(hw), cudaMemcpyDeviceToHost));
@@ -874,16 +901,25 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (pic_status s = read_error_word(c)) return s;
     const int k = ckpt_every;
-    const int nseg = (nsteps + k - 1) / k;
-    const int seg_slots = nsteps > 0 ? (nsteps < k ? nsteps : k) - 1 : 0;
-    const int nstates = nseg + seg_slots + 1;  // checkpoints, segment states, final state
+    const AdjSpace sp(c, nsteps, k);
+    const int nseg = sp.nseg;
+    const int nstates = sp.nstates;  // checkpoints, segment states, final state
     StateLayout L(c);
-    DeviceBlock states, work;
-    if (states.alloc(size_t(nstates) * L.total) != cudaSuccess || work.alloc(adj_work_bytes(c)) != cudaSuccess) {
-        clear_stale("adjoint work space");
-        return fail(PIC_ERR_OOM, "adjoint work space");
+    // the space kept by pic_reserve_adjoint when it is large enough, else one
+    // allocated for this call
+    DeviceBlock own;
+    char* space = c->adj_space;
+    if (!space || c->adj_space_bytes < sp.total) {
+        if (own.alloc(sp.total) != cudaSuccess) {
+            clear_stale("adjoint work space");
+            return fail(PIC_ERR_OOM, "adjoint work space");
+        }
+        space = own.p;
     }
-    auto state_at = [&](int i) { return states.p + size_t(i) * L.total; };
+    char* const states_p = space;
+    char* const work_p = space + sp.states;
+    char* const out_p = space + sp.states + sp.work;
+    auto state_at = [&](int i) { return states_p + size_t(i) * L.total; };
     std::vector<StateMeta> meta(nstates);
     // forward sweep with checkpoints
     for (int s = 0; s < nsteps; ++s) {
@@ -898,8 +934,8 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (pic_status s = pic_diagnostics(c, diag)) return s;
     if (loss) *loss = diag[0];
     // reverse sweep
-    pic::AdjBuffers b = adj_buffers(c, work.p);
-    PIC_CUDA(cudaMemsetAsync(work.p, 0, adj_work_bytes(c), c->stream));
+    pic::AdjBuffers b = adj_buffers(c, work_p);
+    PIC_CUDA(cudaMemsetAsync(work_p, 0, adj_work_bytes(c), c->stream));
     PIC_CUDA(adj_counted(c, 6, [&] { return pic::launch_adj_init(c, b); }));
     std::vector<int> view(k);
     for (int seg = nseg - 1; seg >= 0; --seg) {
@@ -921,15 +957,7 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (pic_status s = read_error_word(c)) return s;
     if (dL_dA) PIC_CUDA(cudaMemcpyAsync(dL_dA, b.lamA, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (dL_du0) {
-        double* dst = dL_du0;
-        DeviceBlock staged;
-        if (!on_device) {
-            if (staged.alloc(3 * size_t(c->np) * sizeof(double)) != cudaSuccess) {
-                clear_stale("adjoint output");
-                return fail(PIC_ERR_OOM, "adjoint output staging");
-            }
-            dst = reinterpret_cast<double*>(staged.p);
-        }
+        double* dst = on_device ? dL_du0 : reinterpret_cast<double*>(out_p);
         PIC_CUDA(adj_counted(c, 3, [&] { return pic::launch_adj_output(c, b, dst); }));
         if (!on_device)
             PIC_CUDA(cudaMemcpyAsync(dL_du0, dst, 3 * size_t(c->np) * sizeof(double), cudaMemcpyDeviceToHost,
@@ -941,53 +969,80 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     return read_error_word(c);
 }
 
+pic_status pic_reserve_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
+    PIC_CUDA(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->adj_space) {
+        PIC_CUDA(cudaFree(c->adj_space));
+        c->adj_space = nullptr;
+        c->adj_space_bytes = 0;
+    }
+    if (nsteps == 0) return PIC_OK;
+    if (c->cap == 0) return fail(PIC_ERR_STATE, "load the particles first (the space is sized by their capacity)");
+    const AdjSpace sp(c, nsteps, ckpt_every);
+    char* p = nullptr;
+    if (cudaMalloc(&p, sp.total) != cudaSuccess) {
+        clear_stale("adjoint reservation");
+        return fail(PIC_ERR_OOM, "adjoint work space");
+    }
+    c->adj_space = p;
+    c->adj_space_bytes = sp.total;
+    return PIC_OK;
+}
+
 pic_status pic_get_field(pic_ctx* c, int32_t which, double* dst, int on_device) {
     if (pic_status s = check_ctx(c)) return s;
+    if (!c->stage) return fail(PIC_ERR_STATE, "context has no staging buffer");
     if (which < 0 || which > 8 || !dst) return fail(PIC_ERR_ARG, "bad field index or NULL destination");
-    const size_t bytes = c->g.C * sizeof(double);
+    const int64_t C = c->g.C;
     clear_stale("field read");
     if (on_device) {
-        PIC_CUDA(pic::launch_field_to_f64(c, which, dst));
+        PIC_CUDA(pic::launch_field_to_f64(c, which, dst, 0, C));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
     if (c->prec == PIC_FP64) {
-        PIC_CUDA(cudaMemcpyAsync(dst, c->F[which], bytes, cudaMemcpyDeviceToHost, c->stream));
+        PIC_CUDA(cudaMemcpyAsync(dst, c->F[which], C * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
-    double* tmp = nullptr;
-    PIC_CUDA(cudaMalloc(&tmp, bytes));
-    cudaError_t e = pic::launch_field_to_f64(c, which, tmp);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, bytes, cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return cuda_fail(e, "get field");
+    // FP32 values converted on the device, chunk by chunk through the staging buffer
+    const int64_t chunk = int64_t(pic::kStageBytes / sizeof(double));
+    double* st = static_cast<double*>(c->stage);
+    for (int64_t i0 = 0; i0 < C; i0 += chunk) {
+        const int64_t cnt = std::min(chunk, C - i0);
+        PIC_CUDA(pic::launch_field_to_f64(c, which, st, i0, cnt));
+        PIC_CUDA(cudaMemcpyAsync(dst + i0, st, size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+    }
     return PIC_OK;
 }
 
 pic_status pic_set_field(pic_ctx* c, int32_t which, const double* src, int on_device) {
     if (pic_status s = check_ctx(c)) return s;
+    if (!c->stage) return fail(PIC_ERR_STATE, "context has no staging buffer");
     if (which < 0 || which > 8 || !src) return fail(PIC_ERR_ARG, "bad field index or NULL source");
-    const size_t bytes = c->g.C * sizeof(double);
+    const int64_t C = c->g.C;
     clear_stale("field write");
     if (on_device) {
-        PIC_CUDA(pic::launch_field_from_f64(c, which, src));
+        PIC_CUDA(pic::launch_field_from_f64(c, which, src, 0, C));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
     if (c->prec == PIC_FP64) {
-        PIC_CUDA(cudaMemcpyAsync(c->F[which], src, bytes, cudaMemcpyHostToDevice, c->stream));
+        PIC_CUDA(cudaMemcpyAsync(c->F[which], src, C * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
-    double* tmp = nullptr;
-    PIC_CUDA(cudaMalloc(&tmp, bytes));
-    cudaError_t e = cudaMemcpyAsync(tmp, src, bytes, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = pic::launch_field_from_f64(c, which, tmp);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return cuda_fail(e, "set field");
+    const int64_t chunk = int64_t(pic::kStageBytes / sizeof(double));
+    double* st = static_cast<double*>(c->stage);
+    for (int64_t i0 = 0; i0 < C; i0 += chunk) {
+        const int64_t cnt = std::min(chunk, C - i0);
+        PIC_CUDA(cudaMemcpyAsync(st, src + i0, size_t(cnt) * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        PIC_CUDA(pic::launch_field_from_f64(c, which, st, i0, cnt));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+    }
     return PIC_OK;
 }
 
@@ -1001,27 +1056,34 @@ pic_status pic_num_particles(pic_ctx* c, int64_t* n) {
 pic_status pic_get_particles(pic_ctx* c, double* x, double* y, double* z, double* ux, double* uy, double* uz,
                              double* w, int32_t* id, int on_device) {
     if (pic_status s = check_ctx(c)) return s;
+    if (!c->stage) return fail(PIC_ERR_STATE, "context has no staging buffer");
     double* dst[7] = {x, y, z, ux, uy, uz, w};
     if (c->np == 0) return PIC_OK;
     clear_stale("particle read");
     if (on_device) {
-        PIC_CUDA(pic::launch_get_particles(c, dst, id));
+        PIC_CUDA(pic::launch_get_particles(c, dst, id, 0, c->np));
         PIC_CUDA(cudaStreamSynchronize(c->stream));
         return PIC_OK;
     }
+    // chunk by chunk through the staging buffer: 7 FP64 arrays and the ids of
+    // `chunk` particles (64 bytes a particle)
     const int64_t n = c->np;
-    char* tmp = nullptr;
-    PIC_CUDA(cudaMalloc(&tmp, 7 * n * sizeof(double) + n * sizeof(int32_t)));
-    double* ddst[7];
-    for (int i = 0; i < 7; ++i) ddst[i] = dst[i] ? reinterpret_cast<double*>(tmp) + i * n : nullptr;
-    int32_t* did = id ? reinterpret_cast<int32_t*>(tmp + 7 * n * sizeof(double)) : nullptr;
-    cudaError_t e = pic::launch_get_particles(c, ddst, did);
-    for (int i = 0; i < 7 && e == cudaSuccess; ++i)
-        if (dst[i]) e = cudaMemcpyAsync(dst[i], ddst[i], n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess && id) e = cudaMemcpyAsync(id, did, n * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
-    if (e != cudaSuccess) return cuda_fail(e, "get particles");
+    const int64_t chunk = int64_t(pic::kStageBytes / 64);
+    char* st = static_cast<char*>(c->stage);
+    double* sdst[7];
+    for (int i = 0; i < 7; ++i) sdst[i] = dst[i] ? reinterpret_cast<double*>(st) + i * chunk : nullptr;
+    int32_t* sid = id ? reinterpret_cast<int32_t*>(st + 7 * chunk * sizeof(double)) : nullptr;
+    for (int64_t p0 = 0; p0 < n; p0 += chunk) {
+        const int64_t cnt = std::min(chunk, n - p0);
+        PIC_CUDA(pic::launch_get_particles(c, sdst, sid, p0, cnt));
+        for (int i = 0; i < 7; ++i)
+            if (dst[i])
+                PIC_CUDA(cudaMemcpyAsync(dst[i] + p0, sdst[i], size_t(cnt) * sizeof(double), cudaMemcpyDeviceToHost,
+                                         c->stream));
+        if (id)
+            PIC_CUDA(cudaMemcpyAsync(id + p0, sid, size_t(cnt) * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+        PIC_CUDA(cudaStreamSynchronize(c->stream));
+    }
     return PIC_OK;
 }
 
@@ -1064,6 +1126,88 @@ pic_status pic_diagnostics(pic_ctx* c, double out[4]) {
     std::memcpy(&mx, &bits, sizeof(mx));
     out[3] = mx;
     return read_error_word(c);
+}
+
+// The two FP64 density arrays of the charge and continuity diagnostics,
+// allocated on first use.
+static pic_status ensure_rho(pic_ctx* c) {
+    if (c->rho) return PIC_OK;
+    if (cudaMalloc(&c->rho, 2 * size_t(c->g.C) * sizeof(double)) != cudaSuccess) {
+        c->rho = nullptr;
+        clear_stale("charge density");
+        return fail(PIC_ERR_OOM, "charge density arrays");
+    }
+    c->have_mark = false;
+    return PIC_OK;
+}
+
+static double* rho_array(pic_ctx* c, int which) { return c->rho + size_t(which) * size_t(c->g.C); }
+
+pic_status pic_charge_density(pic_ctx* c, double* dst, int on_device) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!dst) return fail(PIC_ERR_ARG, "NULL destination");
+    if (pic_status s = ensure_rho(c)) return s;
+    clear_stale("charge density");
+    double* r = rho_array(c, 1 - c->rho_mark);  // the marked density stays
+    PIC_CUDA(pic::launch_charge_density(c, r));
+    c->launches += c->np > 0 ? 1 : 0;
+    PIC_CUDA(cudaMemcpyAsync(dst, r, size_t(c->g.C) * sizeof(double),
+                             on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    return read_error_word(c);
+}
+
+pic_status pic_continuity_mark(pic_ctx* c) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (pic_status s = ensure_rho(c)) return s;
+    clear_stale("continuity mark");
+    PIC_CUDA(pic::launch_charge_density(c, rho_array(c, c->rho_mark)));
+    c->launches += c->np > 0 ? 1 : 0;
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    c->have_mark = true;
+    c->mark_step = c->step;
+    c->mark_shifts = c->shifts;
+    return read_error_word(c);
+}
+
+pic_status pic_continuity_residual(pic_ctx* c, double out[3]) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!out) return fail(PIC_ERR_ARG, "NULL output");
+    if (!c->rho || !c->have_mark) return fail(PIC_ERR_STATE, "no pic_continuity_mark before the step");
+    if (c->step != c->mark_step + 1 || c->shifts != c->mark_shifts)
+        return fail(PIC_ERR_STATE, "the residual needs exactly one step since the mark and no window shift");
+    clear_stale("continuity residual");
+    const int m = c->rho_mark;
+    PIC_CUDA(pic::launch_charge_density(c, rho_array(c, 1 - m)));
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(c->dsum + 16);
+    PIC_CUDA(pic::launch_continuity(c, rho_array(c, m), rho_array(c, 1 - m), d));
+    c->launches += c->np > 0 ? 2 : 1;
+    unsigned long long h[2];
+    PIC_CUDA(cudaMemcpyAsync(h, d, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    PIC_CUDA(cudaStreamSynchronize(c->stream));
+    double mr, m0;
+    std::memcpy(&mr, &h[0], sizeof(double));
+    std::memcpy(&m0, &h[1], sizeof(double));
+    out[0] = m0 > 0.0 ? mr / m0 : mr;
+    out[1] = mr;
+    out[2] = m0;
+    // the new density is the mark of the next step
+    c->rho_mark = 1 - m;
+    c->mark_step = c->step;
+    c->mark_shifts = c->shifts;
+    return read_error_word(c);
+}
+
+pic_status pic_set_fp64_gamma(pic_ctx* c, double gamma) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (!(gamma >= 1.0)) return fail(PIC_ERR_ARG, "gamma must be >= 1 (or +infinity)");
+    PIC_CUDA(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (c->graph) {  // a kernel argument baked into the graph
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->gamma_fp64 = gamma;
+    return PIC_OK;
 }
 
 pic_status pic_sync(pic_ctx* c) {

@@ -154,6 +154,8 @@ pic_ctx make_view(const pic_batch* b, int i) {
     v.err = P.err;
     v.d_step = P.d_step;
     v.dsum = P.dsum;
+    v.stage = P.stage;
+    v.sms = b->sms;
     v.step = P.step;
     return v;
 }
@@ -534,6 +536,7 @@ pic_status pic_batch_init(int32_t nboxes, const int32_t* n, const double* d, con
     if ((e = cudaMalloc(&P.d_step, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMemset(P.d_step, 0, sizeof(long long))) != cudaSuccess) return bail(e, "step counter");
     if ((e = cudaMalloc(&P.dsum, 32 * sizeof(double))) != cudaSuccess) return bail(e, "diagnostics scratch");
+    if ((e = cudaMalloc(&P.stage, pic::kStageBytes)) != cudaSuccess) return bail(e, "host-copy staging buffer");
     if ((e = pic::configure_batch_kernels()) != cudaSuccess) return bail(e, "configure batch kernels");
     *out = b;
     return PIC_OK;
@@ -553,6 +556,7 @@ pic_status pic_batch_destroy(pic_batch* b) {
     cudaFree(P.err);
     cudaFree(P.d_step);
     cudaFree(P.dsum);
+    cudaFree(P.stage);
     cudaFree(b->tab);
     if (b->own_stream) cudaStreamDestroy(P.stream);
     delete b;

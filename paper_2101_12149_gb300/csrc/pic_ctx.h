@@ -82,7 +82,9 @@ struct pic_ctx {
     bool have_old = false;
 
     int* outl = nullptr;     // outsider list of the tile kernel [cap]
-    int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32
+    int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32,
+                             // 2 = 4x4x32 with a halo of 1 (FP32-mixed, order 1)
+    int sms = 1;             // streaming multiprocessors of the device (persistent grids)
     // TMA descriptor of E and B (four dimensions z, y, x, component) whose box
     // is one tile's staged E/B block
     CUtensorMap tmap_eb;
@@ -101,7 +103,8 @@ struct pic_ctx {
     uint64_t seed = 0;
     int64_t reorders = 0;      // pic_sort_particles calls with random bins so far
 
-    unsigned* err = nullptr;       // device error word [4] + outsider count [1] (8 words allocated)
+    unsigned* err = nullptr;       // device error word [4] + outsider count [1] + tile queue counter [1]
+                                   // (8 words allocated; words 6, 7 carry the load's largest weight)
     long long* d_step = nullptr;   // device copy of the step counter (drive time)
     double* dsum = nullptr;        // diagnostics scratch
     int64_t step = 0;
@@ -109,6 +112,15 @@ struct pic_ctx {
     int solver = 0;   // 0 Yee, 1 CKC (B update with the transverse-averaged curl)
     int pusher = 0;   // 0 Boris, 1 Vay
     int egather = 0;  // 0 momentum-conserving, 1 energy-conserving gather
+    double gamma_fp64 = 1e3;  // FP32-mixed: gamma above which the push's rotation runs in FP64 (inf: never)
+
+    // charge density and continuity diagnostics: two FP64 density arrays
+    // (allocated on first use), the one holding the mark, and the step count
+    // and window shifts at the mark
+    double* rho = nullptr;
+    int rho_mark = 0;
+    bool have_mark = false;
+    int64_t mark_step = 0, mark_shifts = 0;
 
     bool timing = false;
     pic::Timer timers[16];
@@ -128,7 +140,19 @@ struct pic_ctx {
     int graph_cur = 0;
     int graph_kernels = 0;
     int64_t launches = 0;
+
+    // staging buffer of the host getters and setters (kStageBytes, allocated
+    // by pic_init_grid): FP32 fields and particle state pass through it in
+    // chunks, converted to or from FP64 on the device
+    void* stage = nullptr;
+    // adjoint work space kept by pic_reserve_adjoint (null: none)
+    char* adj_space = nullptr;
+    size_t adj_space_bytes = 0;
 };
+
+namespace pic {
+constexpr size_t kStageBytes = size_t(32) << 20;
+}
 
 namespace pic {
 
@@ -150,10 +174,17 @@ cudaError_t launch_yee_e(pic_ctx* c);
 cudaError_t launch_step_counter(pic_ctx* c);
 // particles [base, base + n) from arrays that start at particle base
 cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n, int64_t base = 0);
-cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id);
-cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst);
-cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src);
+// particles [p0, p0 + cnt) (current order) into element 0.. of dst / id
+cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id, int64_t p0, int64_t cnt);
+// field values [i0, i0 + cnt) to / from FP64 (dst / src hold cnt values)
+cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst, int64_t i0, int64_t cnt);
+cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src, int64_t i0, int64_t cnt);
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
+// nodal charge density of the current particles into rho (C doubles, zeroed first)
+cudaError_t launch_charge_density(pic_ctx* c, double* rho);
+// out[0] = max |rho1 - rho0 + dt div J| (J: the context's current), out[1] =
+// max |rho0| over the nodes the residual covers, as FP64 bit patterns (zeroed first)
+cudaError_t launch_continuity(pic_ctx* c, const double* rho0, const double* rho1, unsigned long long* out);
 // moving window: move fields and particles down one cell along z (particles
 // below z = 0 die), then fill the front slab with plasma at slots [np, np + nx*ny*ppc)
 cudaError_t launch_window_shift(pic_ctx* c);

@@ -171,8 +171,10 @@ __device__ __forceinline__ void staggered_weights_ec(R f, int& first, R w[P + 1]
 // Relativistic Boris push (u = gamma v):
 //   k = q dt / (2 m);  u- = u + k E;  g- = sqrt(1 + |u-|^2);  t = k B / g-;
 //   s = 2 t / (1 + |t|^2);  u' = u- + u- x t;  u+ = u- + u' x s;  u = u+ + k E.
-// The FP32 instantiation switches to FP64 for g-, t, s and the rotation when
-// g- > 1e3 (ultra-relativistic particles).
+// The FP32 instantiation pushes a particle whose g-^2 exceeds g2_fp64
+// (ultra-relativistic; the library's default threshold is g- > 1e3) wholly in
+// FP64: both half kicks, g-, t, s and the rotation, so its stored FP32
+// momentum is rounded once per step.
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void boris_rotate(R k, const R B[3], R um[3], R gm) {
@@ -189,20 +191,22 @@ __device__ __forceinline__ void boris_rotate(R k, const R B[3], R um[3], R gm) {
 }
 
 template <typename R>
-__device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
+__device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3], float g2_fp64 = 1e6f) {
     R um[3] = {u[0] + k * E[0], u[1] + k * E[1], u[2] + k * E[2]};
     const R g2 = R(1) + um[0] * um[0] + um[1] * um[1] + um[2] * um[2];
-    if (sizeof(R) == 4 && g2 > R(1e6)) {
-        double umd[3] = {double(um[0]), double(um[1]), double(um[2])};
+    if (sizeof(R) == 4 && float(g2) > g2_fp64) {
+        const double kd = double(k);
+        const double Ed[3] = {double(E[0]), double(E[1]), double(E[2])};
+        double umd[3] = {double(u[0]) + kd * Ed[0], double(u[1]) + kd * Ed[1], double(u[2]) + kd * Ed[2]};
         const double Bd[3] = {double(B[0]), double(B[1]), double(B[2])};
         const double gmd = sqrt(1.0 + umd[0] * umd[0] + umd[1] * umd[1] + umd[2] * umd[2]);
-        boris_rotate<double>(double(k), Bd, umd, gmd);
-        um[0] = R(umd[0]);
-        um[1] = R(umd[1]);
-        um[2] = R(umd[2]);
-    } else {
-        boris_rotate<R>(k, B, um, sqrt_<R>(g2));
+        boris_rotate<double>(kd, Bd, umd, gmd);
+        u[0] = R(umd[0] + kd * Ed[0]);
+        u[1] = R(umd[1] + kd * Ed[1]);
+        u[2] = R(umd[2] + kd * Ed[2]);
+        return;
     }
+    boris_rotate<R>(k, B, um, sqrt_<R>(g2));
     u[0] = um[0] + k * E[0];
     u[1] = um[1] + k * E[1];
     u[2] = um[2] + k * E[2];
@@ -215,7 +219,8 @@ __device__ __forceinline__ void boris(R k, const R E[3], const R B[3], R u[3]) {
 // sigma = 1 + |u'|^2 - |tau|^2, gamma_new^2 = (sigma + sqrt(sigma^2 +
 // 4(|tau|^2 + u*^2)))/2, t = tau/gamma_new, s = 1/(1 + |t|^2),
 // u_new = s (u' + (u'.t) t + u' x t).  kq = q dt / (2 m).  The FP32
-// instantiation works in FP64 when |u'| > 1e3.
+// instantiation pushes wholly in FP64 when |u'|^2 > g2_fp64 (default:
+// |u'| > 1e3).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ __forceinline__ void vay_core(T kq, const T B[3], const T up[3], T u[3]) {
@@ -233,18 +238,25 @@ __device__ __forceinline__ void vay_core(T kq, const T B[3], const T up[3], T u[
 }
 
 template <typename R>
-__device__ __forceinline__ void vay(R kq, const R E[3], const R B[3], R u[3]) {
+__device__ __forceinline__ void vay(R kq, const R E[3], const R B[3], R u[3], float g2_fp64 = 1e6f) {
     const R g0 = sqrt_<R>(R(1) + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const R v[3] = {u[0] / g0, u[1] / g0, u[2] / g0};
     R up[3];
     up[0] = u[0] + R(2) * kq * E[0] + kq * (v[1] * B[2] - v[2] * B[1]);
     up[1] = u[1] + R(2) * kq * E[1] + kq * (v[2] * B[0] - v[0] * B[2]);
     up[2] = u[2] + R(2) * kq * E[2] + kq * (v[0] * B[1] - v[1] * B[0]);
-    if (sizeof(R) == 4 && up[0] * up[0] + up[1] * up[1] + up[2] * up[2] > R(1e6)) {
+    if (sizeof(R) == 4 && float(up[0] * up[0] + up[1] * up[1] + up[2] * up[2]) > g2_fp64) {
+        // the whole push in FP64 (u' included), rounded once into the FP32 momentum
+        const double kd = double(kq);
         const double Bd[3] = {double(B[0]), double(B[1]), double(B[2])};
-        const double upd[3] = {double(up[0]), double(up[1]), double(up[2])};
+        const double u0[3] = {double(u[0]), double(u[1]), double(u[2])};
+        const double gd = sqrt(1.0 + u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2]);
+        const double vd[3] = {u0[0] / gd, u0[1] / gd, u0[2] / gd};
+        const double upd[3] = {u0[0] + 2.0 * kd * double(E[0]) + kd * (vd[1] * Bd[2] - vd[2] * Bd[1]),
+                               u0[1] + 2.0 * kd * double(E[1]) + kd * (vd[2] * Bd[0] - vd[0] * Bd[2]),
+                               u0[2] + 2.0 * kd * double(E[2]) + kd * (vd[0] * Bd[1] - vd[1] * Bd[0])};
         double ud[3];
-        vay_core<double>(double(kq), Bd, upd, ud);
+        vay_core<double>(kd, Bd, upd, ud);
         u[0] = R(ud[0]);
         u[1] = R(ud[1]);
         u[2] = R(ud[2]);

@@ -35,20 +35,28 @@ namespace pic {
 // Shared-memory boxes of one tile, sized for the largest tile of the layout
 // (MX x MY x MZ cells); smaller tiles use the low corner, so every stride is a
 // compile-time constant and each shared access is base + immediate.
-//   E/B box: cells [-2, T+2) per axis, z rows of pitch EP
-//   J box:   x, y [-2, T+3), z [-4, T+4), z rows of pitch JP (z padded so the
+//   E/B box: cells [-H, T+H) per axis, z rows of pitch EP
+//   J box:   x, y [-H, T+H+1), z [-4, T+4), z rows of pitch JP (z padded so the
 //            flush moves aligned float4s)
-// Two layouts.  4 x 4 x 32 when nz is a multiple of 32: the lanes of a warp
-// take the particles of one z-row of 32 cells (tile_body), and with row and
-// plane pitches that are multiples of 32 words the bank of every access is
-// its z index, so lanes in distinct cells hit distinct banks whatever their
-// staggering offsets along x and y.  Otherwise up to 8 x 8 x 8 cells.
-template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
-    static constexpr int EX = MX + 4, EY = MY + 4, EZ = MZ + 4;
+// H is the halo the shape order needs: the gather of order p reaches nodes
+// -2..+2 around a particle's cell for p = 2, 3 and -1..+1 for p = 1, and the
+// Esirkepov window of a move shorter than a cell one node further up.
+// Layouts.  4 x 4 x 32 when nz is a multiple of 32: the lanes of a warp take
+// the particles of z-rows of 32 cells, and with row and plane pitches that
+// are multiples of 32 words the bank of every access is its z index, so lanes
+// in distinct cells hit distinct banks whatever their staggering offsets
+// along x and y.  Otherwise up to 8 x 8 x 8 cells.  Order 1 in FP32-mixed on
+// 4 x 4 x 32 tiles uses a halo of 1 and row pitches of 40 words: 81.6 KB a
+// tile, so two 256-thread CTAs share an SM and one's staging and flush
+// overlap the other's particles.
+template <int MX, int MY, int MZ, int EP, int JP, int H_ = 2, int THREADS = 512, int MINB = 1> struct Layout {
+    static constexpr int H = H_;
+    static constexpr int kThreads = THREADS, kMinBlocks = MINB;
+    static constexpr int EX = MX + 2 * H, EY = MY + 2 * H, EZ = MZ + 2 * H;
     static constexpr int eY = EP, eX = EY * EP, eVol = EX * EY * EP;
-    static constexpr int JX = MX + 5, JY = MY + 5, JZ = MZ + 8;
+    static constexpr int JX = MX + 2 * H + 1, JY = MY + 2 * H + 1, JZ = MZ + 8;
     static constexpr int jY = JP, jX = JY * JP, jVol = JX * JY * JP;
-    static_assert(EP >= EZ && JP >= JZ && JP % 4 == 0, "row pitches");
+    static_assert(EP >= EZ && JP >= JZ && JP % 4 == 0 && H >= 1 && H <= 2, "row pitches, halo");
     // FP64: J box of doubles (3 components); FP32-mixed: J box of fixed-point
     // (lo, hi) int32 pairs (3 components x 2 arrays)
     template <typename R> static constexpr size_t smem_bytes() {
@@ -58,12 +66,16 @@ template <int MX, int MY, int MZ, int EP, int JP> struct Layout {
 // FP64 keeps compact pitches: the bank-conflict-free ones would not fit its
 // shared memory, and the FP64 path is bound by FP64 arithmetic.
 template <typename R>
-using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64>, Layout<4, 4, 32, 38, 40>>;
+using LayoutRow = std::conditional_t<sizeof(R) == 4, Layout<4, 4, 32, 64, 64, 2, 512, 1>,
+                                     Layout<4, 4, 32, 38, 40, 2, 256, 1>>;
 // 8x8x8 tiles: the 32 cells of a warp are 4 z-rows of 8; FP32-mixed row
 // pitches of 24 words put those rows on banks 0, 24, 16 and 8 (mod 32), so
 // rows never share a bank at the same z.  FP64 keeps compact pitches.
 template <typename R>
-using LayoutCube = std::conditional_t<sizeof(R) == 4, Layout<8, 8, 8, 24, 24>, Layout<8, 8, 8, 14, 20>>;
+using LayoutCube = std::conditional_t<sizeof(R) == 4, Layout<8, 8, 8, 24, 24, 2, 512, 1>,
+                                      Layout<8, 8, 8, 14, 20, 2, 256, 1>>;
+// Order 1, FP32-mixed, 4 x 4 x 32 tiles: halo 1, two CTAs of 256 threads per SM.
+using LayoutRow1 = Layout<4, 4, 32, 40, 40, 1, 256, 2>;
 
 // Gather of one component from the staged box: `base` points at the first
 // stencil node.
@@ -234,7 +246,7 @@ __device__ __forceinline__ void esirkepov_smem_fixed(int* __restrict__ sJ, int b
 }
 
 // Deposit of one particle into the staged J box: the window's first node is
-// (li + 2 + b_x, lj + 2 + b_y, lk + 4 + b_z) in box coordinates.  NARROW: all
+// (li + H + b_x, lj + H + b_y, lk + 4 + b_z) in box coordinates.  NARROW: all
 // three axes have both shapes starting at node b, so the stencil is P cumulative
 // slots by (P + 1)^2 transverse nodes (the skipped slots hold exact zeros and,
 // on the cumulative axis, the rounding residue of sum dS = 0).
@@ -244,7 +256,7 @@ __device__ __forceinline__ void tile_deposit(const StepArgs<R>& A, R* sJ, int li
     constexpr int NC = NARROW ? P : P + 1;
     constexpr int NT = NARROW ? P + 1 : P + 2;
     const R coef[3] = {A.jc[0] * wq, A.jc[1] * wq, A.jc[2] * wq};
-    const int bx = li + 2 + ax[0].b, by = lj + 2 + ax[1].b, bz = lk + 4 + ax[2].b;
+    const int bx = li + LY::H + ax[0].b, by = lj + LY::H + ax[1].b, bz = lk + 4 + ax[2].b;
     PIC_CHECK_OR(bx >= 0 && bx + P + 1 < LY::JX && by >= 0 && by + P + 1 < LY::JY && bz >= 0 && bz + P + 1 < LY::JZ,
                  A.err, 4, ((long long)(ax[0].b + 8) << 16) | ((ax[1].b + 8) << 8) | (ax[2].b + 8), return);
     const int base = bx * LY::jX + by * LY::jY + bz;
@@ -322,10 +334,6 @@ __device__ __forceinline__ float fixed_to_float(int hi, int lo) {
     return __ll2float_rn((long long)hi * 32768 + lo);
 }
 
-// Block size of the tile kernel: FP32-mixed 512 threads (one CTA per SM, its
-// shared memory holding the fixed-point J box), FP64 256.
-template <typename R> constexpr int tile_block() { return sizeof(R) == 4 ? 512 : 256; }
-
 // Periodic index of a cell at most one period outside [0, n) (any i, n > 0,
 // without a division in that common case).
 __device__ __forceinline__ int wrap_near(int i, int n) {
@@ -335,7 +343,7 @@ __device__ __forceinline__ int wrap_near(int i, int n) {
 }
 
 // Stage the sub-box [a0,a1) x [b0,b1) x [k0,k1) of the tile's E/B block (cells
-// [-2, T+2) per axis around the tile origin oi, oj, ok), periodic wrap in x, y
+// [-H, T+H) per axis around the tile origin oi, oj, ok), periodic wrap in x, y
 // and in z unless z is open, where nothing lies beyond the ends.
 // kFull: the whole block of the layout's own tile shape (compile-time
 // divisors; the sub-box arguments are ignored).
@@ -353,9 +361,9 @@ __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, 
         r -= (a - a0) * eb * ek;
         const int b = b0 + r / ek;
         const int kk = k0 + r - (b - b0) * ek;
-        const int gi = wrap_near(oi - 2 + a, g.n[0]);
-        const int gj = wrap_near(oj - 2 + b, g.n[1]);
-        const int kz = ok - 2 + kk;
+        const int gi = wrap_near(oi - LY::H + a, g.n[0]);
+        const int gj = wrap_near(oj - LY::H + b, g.n[1]);
+        const int kz = ok - LY::H + kk;
         R v = R(0);
         if (!g.zopen || unsigned(kz) < unsigned(g.n[2])) {
             const int gk = wrap_near(kz, g.n[2]);
@@ -370,15 +378,14 @@ __device__ __forceinline__ void stage_box(const StepArgs<R>& A, R* sEB, int oi, 
 
 // TMA staging: one 4-D box (z, y, x, component) of eY x EY x EX x 6 values
 // lands in the E/B block exactly (eY, the row pitch, spans a multiple of 16
-// bytes and at least EZ + 2 values).  The box starts at z = ok - 4 (TMA wants
-// the innermost coordinate on a 16-byte boundary), so the block is addressed
-// 2 values in; coordinates outside the grid read
-// as zero and the wrapped halo planes are restaged by stage_box after the
-// copy has landed.
+// bytes and covers [ok - 4, ok + T + H)).  The box starts at z = ok - 4 (TMA
+// wants the innermost coordinate on a 16-byte boundary), so the block is
+// addressed 4 - H values in; coordinates outside the grid read as zero and the
+// wrapped halo planes are restaged by stage_box after the copy has landed.
 constexpr int kTmaSpinLimit = 1 << 20;
 
 template <class LY, typename R> __host__ __device__ constexpr bool tma_layout() {
-    return (LY::eY * sizeof(R)) % 16 == 0 && LY::EZ + 2 <= LY::eY && LY::eY <= 256;
+    return (LY::eY * sizeof(R)) % 16 == 0 && LY::EZ + 4 - LY::H <= LY::eY && LY::eY <= 256;
 }
 
 __device__ __forceinline__ void mbar_init(unsigned long long* bar) {
@@ -423,10 +430,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 
 // Flush of the fixed-point J box in groups of 4 consecutive z nodes (aligned
-// float4 reductions into HBM).  JYc, Q4c > 0: the box extents are the
+// float4 reductions into HBM); every group read is cleared, so the box is
+// zero again for the next tile.  JYc, Q4c > 0: the box extents are the
 // layout's (compile-time divisors); 0: the runtime jy, q4.
 template <typename R, class LY, int JYc, int Q4c>
-__device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJi, int oi, int oj, int ok, int jx,
+__device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, int* sJi, int oi, int oj, int ok, int jx,
                                              int jy_rt, int q4_rt) {
     const Geom& g = A.g;
     const int jy = JYc > 0 ? JYc : jy_rt;
@@ -440,17 +448,21 @@ __device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJ
         const int a = row / jy;
         const int b = row - a * jy;
         const int o = 2 * c * LY::jVol + a * LY::jX + b * LY::jY + 4 * q;
-        const int4 lo = *reinterpret_cast<const int4*>(sJi + o);
-        const int4 hi = *reinterpret_cast<const int4*>(sJi + o + LY::jVol);
+        int4* plo = reinterpret_cast<int4*>(sJi + o);
+        int4* phi = reinterpret_cast<int4*>(sJi + o + LY::jVol);
+        const int4 lo = *plo;
+        const int4 hi = *phi;
         if ((lo.x | lo.y | lo.z | lo.w | hi.x | hi.y | hi.z | hi.w) == 0) continue;
+        *plo = make_int4(0, 0, 0, 0);
+        *phi = make_int4(0, 0, 0, 0);
         // a group of 4 starts at a multiple of 4 and nz % 4 == 0: it is all inside or all beyond the z ends
         if (g.zopen && unsigned(ok - 4 + 4 * q) >= unsigned(g.n[2])) continue;
         const float4 v = make_float4(fixed_to_float(hi.x, fixed_low(hi.x, lo.x)) * A.inv_vscale,
                                      fixed_to_float(hi.y, fixed_low(hi.y, lo.y)) * A.inv_vscale,
                                      fixed_to_float(hi.z, fixed_low(hi.z, lo.z)) * A.inv_vscale,
                                      fixed_to_float(hi.w, fixed_low(hi.w, lo.w)) * A.inv_vscale);
-        const int gi = wrap_near(oi - 2 + a, g.n[0]);
-        const int gj = wrap_near(oj - 2 + b, g.n[1]);
+        const int gi = wrap_near(oi - LY::H + a, g.n[0]);
+        const int gj = wrap_near(oj - LY::H + b, g.n[1]);
         const int gk = wrap_near(ok - 4 + 4 * q, g.n[2]);
         PIC_CHECK_OR(gk + 3 < g.n[2] && ((gk & 3) == 0), A.err, 6, gk, continue);
         float* dst = reinterpret_cast<float*>(A.J[c]) + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk;
@@ -458,131 +470,145 @@ __device__ __forceinline__ void flush_fixed4(const StepArgs<R>& A, const int* sJ
     }
 }
 
-// One tile t of the box described by A, by the whole CTA; `smem_raw` is the
-// CTA's dynamic shared memory; `tmap` the TMA descriptor of the box's E/B
-// (null: staged by loads).  Returns with the block converged.
-template <int P, typename R, class LY>
-__device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw,
-                                          const CUtensorMap* tmap = nullptr) {
-    R* sm = reinterpret_cast<R*>(smem_raw);
+// Flush of the tile's J box into the global arrays (periodic fold), clearing
+// every value it reads.
+template <typename R, class LY>
+__device__ __forceinline__ void flush_tile(const StepArgs<R>& A, R* sJ, int oi, int oj, int ok) {
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
-    constexpr bool kTmaLayout = tma_layout<LY, R>();
-    constexpr int kZShift = kTmaLayout ? 2 : 0;
-    R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
-    R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
     int* sJi = reinterpret_cast<int*>(sJ);
-
-    const int beg = A.offsets[(int64_t)t * g.cpt];
-    const int end = A.offsets[(int64_t)(t + 1) * g.cpt];
-    if (end <= beg) return;
-    PIC_CHECK_OR(beg >= 0 && end <= A.np, A.err, 1, ((long long)beg << 32) | unsigned(end), return);
-    int oi, oj, ok;
-    tile_origin(g, t, oi, oj, ok);
-
-    // stage E, B of the tile and a halo of 2 (wrapped), zero the tile's J
-    __shared__ __align__(8) unsigned long long s_bar;
-    bool by_tma = false;
-    {
-        const int ex = g.T[0] + 4, ey = g.T[1] + 4, ez = g.T[2] + 4;
-        if constexpr (kTmaLayout) {
-            by_tma = tmap != nullptr && (unsigned(__cvta_generic_to_shared(sm)) & 127u) == 0u &&
-                     ((ok - 2 - kZShift) & 3) == 0;
-            if (by_tma) {
-                if (threadIdx.x == 0) mbar_init(&s_bar);
-                __syncthreads();
-                if (threadIdx.x == 0)
-                    tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 2 - kZShift, oj - 2,
-                                oi - 2);
-                for (int e = threadIdx.x; e < 6 * LY::jVol / 4; e += blockDim.x)
-                    reinterpret_cast<int4*>(sJi)[e] = make_int4(0, 0, 0, 0);
-                // every thread waits for the copy; if it did not land in time,
-                // all wait once more (it is still writing into this CTA's
-                // shared memory) and the tile is skipped with the error set
-                const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0u, kTmaSpinLimit));
-                if (late) {
-                    if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
-                    mbar_wait(&s_bar, 0u, kTmaSpinLimit);
-                    __syncthreads();
-                    return;
-                }
-                // halo planes that wrap around the grid came in as zeros
-                if (oi < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, 2 - oi, 0, ey, 0, ez);
-                if (oi + ex - 2 > g.n[0]) stage_box<R, LY>(A, sEB, oi, oj, ok, g.n[0] - oi + 2, ex, 0, ey, 0, ez);
-                if (oj < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, 2 - oj, 0, ez);
-                if (oj + ey - 2 > g.n[1]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, g.n[1] - oj + 2, ey, 0, ez);
-                if (!g.zopen) {
-                    if (ok < 2) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, 2 - ok);
-                    if (ok + ez - 2 > g.n[2]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, g.n[2] - ok + 2, ez);
-                }
-            }
-        }
-        if (!by_tma) {
-            if (ex == LY::EX && ey == LY::EY && ez == LY::EZ)
-                stage_box<R, LY, true>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
-            else
-                stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
-            // J box zeroed 16 bytes at a time (jVol is a multiple of 4; the box starts 16-byte aligned)
-            const int n16 = kFixed ? 6 * LY::jVol / 4 : 3 * LY::jVol / 2;
-            for (int e = threadIdx.x; e < n16; e += blockDim.x) reinterpret_cast<int4*>(sJ)[e] = make_int4(0, 0, 0, 0);
-        }
+    const int jx = g.T[0] + 2 * LY::H + 1, jy = g.T[1] + 2 * LY::H + 1, jz = g.T[2] + 8;
+    if (kFixed && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
+        // the layout's own tile shape indexes the J box with constants
+        if (jx == LY::JX && jy == LY::JY && jz == LY::JZ)
+            flush_fixed4<R, LY, LY::JY, LY::JZ / 4>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
+        else
+            flush_fixed4<R, LY, 0, 0>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
+        return;
     }
-    __syncthreads();
-    if (by_tma && threadIdx.x == 0) mbar_inval(&s_bar);  // every thread is past its wait
+    const int vol = jx * jy * jz;
+    for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) {
+        const int c = e / vol;
+        int r = e - c * vol;
+        const int a = r / (jy * jz);
+        r -= a * jy * jz;
+        const int b = r / jz;
+        const int kk = r - b * jz;
+        const int o = a * LY::jX + b * LY::jY + kk;
+        R v;
+        if (kFixed) {
+            int* plo = sJi + 2 * c * LY::jVol + o;
+            int* phi = plo + LY::jVol;
+            const int lo = *plo, hi = *phi;
+            if ((lo | hi) == 0) continue;
+            *plo = 0;
+            *phi = 0;
+            v = R(fixed_to_float(hi, fixed_low(hi, lo)) * A.inv_vscale);
+        } else {
+            R* pv = sJ + c * LY::jVol + o;
+            v = *pv;
+            if (v == R(0)) continue;
+            *pv = R(0);
+        }
+        if (g.zopen && unsigned(ok - 4 + kk) >= unsigned(g.n[2])) continue;
+        const int gi = wrap_near(oi - LY::H + a, g.n[0]);
+        const int gj = wrap_near(oj - LY::H + b, g.n[1]);
+        const int gk = wrap_near(ok - 4 + kk, g.n[2]);
+        atomicAdd(A.J[c] + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk, v);
+    }
+}
 
-    // The tile's particles are cell-sorted; consecutive lanes take consecutive
-    // runs of them, so the lanes of a warp work in neighbouring cells (distinct
-    // shared-memory banks).  When the tile's cells split evenly over the warps
-    // and the particles are spread evenly enough (no warp's share above 1.25x
-    // the mean + 32), warp w owns the w-th group of cells (one z-row of the
-    // FP32-mixed tile) and its lanes split that group's particles: no two
-    // warps then deposit into the same row at the same time.  Otherwise the
-    // whole tile is cut into runs of about one cell's worth (or A.run).
-    const int cnt = end - beg;
+// Zero the whole J box (once per CTA: afterwards each flush clears what it reads).
+template <typename R, class LY> __device__ __forceinline__ void zero_jbox(R* sJ) {
+    const int n16 = sizeof(R) == 4 ? 6 * LY::jVol / 4 : 3 * LY::jVol / 2;
+    for (int e = threadIdx.x; e < n16; e += blockDim.x) reinterpret_cast<int4*>(sJ)[e] = make_int4(0, 0, 0, 0);
+}
+
+// How one tile's particles are split over the CTA's warps.  The tile's
+// particles are cell-sorted; consecutive lanes take consecutive runs of them,
+// so the lanes of a warp work in neighbouring cells (distinct shared-memory
+// banks).  When the tile's cells split evenly over the warps and the
+// particles are spread evenly enough (no warp's share above 1.25x the mean +
+// 32), warp w owns the w-th group of cells (z-rows of the 4 x 4 x 32 tile)
+// and its lanes split that group's particles: no two warps then deposit into
+// the same row at the same time.  Otherwise the whole tile is cut into runs
+// of about one cell's worth (or A.run).  Per-warp values.
+struct TileWork {
+    int beg, end;                              // the tile's particles
+    int wbeg, wend, run, nrun, rstart, rstride;
+};
+
+template <typename R>
+__device__ __forceinline__ void plan_tile(const StepArgs<R>& A, int t, TileWork& w) {
+    const Geom& g = A.g;
+    w.beg = A.offsets[(int64_t)t * g.cpt];
+    w.end = A.offsets[(int64_t)(t + 1) * g.cpt];
+    const int cnt = w.end - w.beg;
     const int lane = threadIdx.x & 31;
     const int nwarp = blockDim.x >> 5;
-    int wbeg = beg, wend = end, run, nrun, rstart, rstride;
+    w.wbeg = w.beg;
+    w.wend = w.end;
     bool by_warp = false;
     if (A.run <= 0 && g.cpt % nwarp == 0 && nwarp <= 32) {
         const int cpw = g.cpt / nwarp;
         const int64_t c0 = (int64_t)t * g.cpt;
-        const int gsize = lane < nwarp ? A.offsets[c0 + (int64_t)(lane + 1) * cpw] - A.offsets[c0 + (int64_t)lane * cpw] : 0;
+        const int gsize =
+            lane < nwarp ? A.offsets[c0 + (int64_t)(lane + 1) * cpw] - A.offsets[c0 + (int64_t)lane * cpw] : 0;
         const int gmax = __reduce_max_sync(0xffffffffu, gsize);
         by_warp = int64_t(gmax) * nwarp * 4 <= int64_t(cnt) * 5 + int64_t(128) * nwarp;
         if (by_warp) {
             const int wid = threadIdx.x >> 5;
-            wbeg = A.offsets[c0 + (int64_t)wid * cpw];
-            wend = A.offsets[c0 + (int64_t)(wid + 1) * cpw];
-            PIC_CHECK_OR(beg <= wbeg && wbeg <= wend && wend <= end, A.err, 1,
-                         ((long long)wbeg << 32) | unsigned(wend), wbeg = wend = beg);
+            w.wbeg = A.offsets[c0 + (int64_t)wid * cpw];
+            w.wend = A.offsets[c0 + (int64_t)(wid + 1) * cpw];
+            PIC_CHECK_OR(w.beg <= w.wbeg && w.wbeg <= w.wend && w.wend <= w.end, A.err, 1,
+                         ((long long)w.wbeg << 32) | unsigned(w.wend), w.wbeg = w.wend = w.beg);
         }
     }
     if (by_warp) {
-        run = max(1, (wend - wbeg + 31) >> 5);
-        nrun = (wend - wbeg + run - 1) / run;  // at most 32: one pass of the warp
-        rstart = 0;
-        rstride = 32;
+        w.run = max(1, (w.wend - w.wbeg + 31) >> 5);
+        w.nrun = (w.wend - w.wbeg + w.run - 1) / w.run;  // at most 32: one pass of the warp
+        w.rstart = 0;
+        w.rstride = 32;
     } else {
-        run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
-        nrun = (cnt + run - 1) / run;
-        rstart = threadIdx.x - lane;
-        rstride = blockDim.x;
+        w.run = A.run > 0 ? A.run : max(1, (cnt + (g.cpt >> 1)) / g.cpt);
+        w.nrun = (cnt + w.run - 1) / w.run;
+        w.rstart = threadIdx.x - lane;
+        w.rstride = blockDim.x;
     }
-    // Warps step their lanes' runs in lockstep.  A move whose old and new
-    // shapes start on the same node along every axis (most moves: crossing a
-    // cell face is rare) deposits the narrow stencil at once; the others go to
-    // a per-warp queue held one slot per lane in registers and are deposited
-    // 32 at a time with the full window, so neither kind runs with idle lanes.
+}
+
+// This lane's first particle of a tile (its loads issued early; see tile_particles).
+template <typename R>
+__device__ __forceinline__ void first_particle(const StepArgs<R>& A, const TileWork& w, RawParticle<R>& next) {
+    const int lane = threadIdx.x & 31;
+    const int rr = w.rstart + lane;
+    const int p0 = w.wbeg + rr * w.run;
+    if (rr < w.nrun && p0 < w.wend) load_raw<R>(A, p0, next);
+}
+
+// Gather + push + advance + Esirkepov of one tile's particles, reading E/B from
+// the staged block and depositing into the J box.  `next` holds this lane's
+// first particle (first_particle).  Warps step their lanes' runs in
+// lockstep.  A move whose old and new shapes start on the same node along
+// every axis (most moves: crossing a cell face is rare) deposits the narrow
+// stencil at once; the others go to a per-warp queue held one slot per lane
+// in registers and are deposited 32 at a time with the full window, so
+// neither kind runs with idle lanes.
+template <int P, typename R, class LY>
+__device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileWork& w, int oi, int oj, int ok,
+                                               const R* sEB, R* sJ, RawParticle<R> next) {
+    const Geom& g = A.g;
+    constexpr bool kFixed = sizeof(R) == 4;
+    const int lane = threadIdx.x & 31;
     TileMove<R> qs = TileMove<R>::zero();  // this lane's queue slot
     int qn = 0;                            // queued moves (warp-uniform)
-    for (int rbase = rstart; rbase < nrun; rbase += rstride) {
+    for (int rbase = w.rstart; rbase < w.nrun; rbase += w.rstride) {
         const int rr = rbase + lane;
-        const int p0 = wbeg + rr * run;
-        const int len = rr < nrun ? min(run, wend - p0) : 0;
+        const int p0 = w.wbeg + rr * w.run;
+        const int len = rr < w.nrun ? min(w.run, w.wend - p0) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
         // the next particle's loads are issued before the current one's work
-        RawParticle<R> next;
-        if (len > 0) load_raw<R>(A, p0, next);
+        if (rbase != w.rstart && len > 0) load_raw<R>(A, p0, next);
         for (int it = 0; it < maxlen; ++it) {
             const int p = p0 + it;
             bool wide = false;
@@ -597,7 +623,7 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                 const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
                 // the fixed-point sums are exact for up to 65535 particles per tile
                 const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
-                                    unsigned(lk) < unsigned(g.T[2]) && (!kFixed || p - beg < 65535);
+                                    unsigned(lk) < unsigned(g.T[2]) && (!kFixed || p - w.beg < 65535);
                 if (!inside) {
                     const int slot = atomicAdd(A.outn, 1);
                     A.outl[slot] = p;
@@ -607,9 +633,10 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
                         GatherW<P, R> G;
                         int fn[3], fs[3];
                         gather_weights<P, R>(f0, G, fn, fs, A.egather != 0);
-                        const int bnx = (li + 2 + fn[0]) * LY::eX, bsx = (li + 2 + fs[0]) * LY::eX;
-                        const int bny = (lj + 2 + fn[1]) * LY::eY, bsy = (lj + 2 + fs[1]) * LY::eY;
-                        const int bnz = lk + 2 + fn[2], bsz = lk + 2 + fs[2];
+                        constexpr int H = LY::H;
+                        const int bnx = (li + H + fn[0]) * LY::eX, bsx = (li + H + fs[0]) * LY::eX;
+                        const int bny = (lj + H + fn[1]) * LY::eY, bsy = (lj + H + fs[1]) * LY::eY;
+                        const int bnz = lk + H + fn[2], bsz = lk + H + fs[2];
                         EB[0] = interp_smem<P, R, LY>(sEB + 0 * LY::eVol + bsx + bny + bnz, G.ws[0], G.wn[1], G.wn[2]);
                         EB[1] = interp_smem<P, R, LY>(sEB + 1 * LY::eVol + bnx + bsy + bnz, G.wn[0], G.ws[1], G.wn[2]);
                         EB[2] = interp_smem<P, R, LY>(sEB + 2 * LY::eVol + bnx + bny + bsz, G.wn[0], G.wn[1], G.ws[2]);
@@ -659,59 +686,213 @@ __device__ __forceinline__ void tile_body(const StepArgs<R>& A, const int t, uns
         }
     }
     if (lane < qn) qs.template deposit<P, LY>(A, sJ);
-    __syncthreads();
+}
 
-    // flush the tile's current into the global arrays (periodic fold)
-    const int jx = g.T[0] + 5, jy = g.T[1] + 5, jz = g.T[2] + 8;
-    if (kFixed && (g.T[2] % 4) == 0 && (g.n[2] % 4) == 0) {
-        // the layout's own tile shape indexes the J box with constants
-        if (jx == LY::JX && jy == LY::JY && jz == LY::JZ)
-            flush_fixed4<R, LY, LY::JY, LY::JZ / 4>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
-        else
-            flush_fixed4<R, LY, 0, 0>(A, sJi, oi, oj, ok, jx, jy, jz / 4);
-    } else {
-        const int vol = jx * jy * jz;
-        for (int e = threadIdx.x; e < 3 * vol; e += blockDim.x) {
-            const int c = e / vol;
-            int r = e - c * vol;
-            const int a = r / (jy * jz);
-            r -= a * jy * jz;
-            const int b = r / jz;
-            const int kk = r - b * jz;
-            const int o = a * LY::jX + b * LY::jY + kk;
-            R v;
-            if (kFixed)
-                v = R(fixed_to_float(sJi[2 * c * LY::jVol + LY::jVol + o],
-                                     fixed_low(sJi[2 * c * LY::jVol + LY::jVol + o], sJi[2 * c * LY::jVol + o])) *
-                      A.inv_vscale);
-            else
-                v = sJ[c * LY::jVol + o];
-            if (v == R(0)) continue;
-            if (g.zopen && unsigned(ok - 4 + kk) >= unsigned(g.n[2])) continue;
-            const int gi = wrap_near(oi - 2 + a, g.n[0]);
-            const int gj = wrap_near(oj - 2 + b, g.n[1]);
-            const int gk = wrap_near(ok - 4 + kk, g.n[2]);
-            atomicAdd(A.J[c] + ((int64_t)gi * g.n[1] + gj) * g.n[2] + gk, v);
-        }
+// Whether tile t stages its E/B block by TMA: the layout allows it, a
+// descriptor exists, the block is 128-byte aligned and the box's z start
+// (ok - 4) is on a 16-byte boundary.
+template <typename R, class LY>
+__device__ __forceinline__ bool tile_uses_tma(const CUtensorMap* tmap, const R* sm, int ok) {
+    if constexpr (!tma_layout<LY, R>()) return false;
+    return tmap != nullptr && (unsigned(__cvta_generic_to_shared(sm)) & 127u) == 0u && ((ok - 4) & 3) == 0;
+}
+
+// Halo planes of a TMA-staged block that wrap around the grid came in as
+// zeros: restage them by loads.
+template <typename R, class LY>
+__device__ __forceinline__ void restage_wrapped(const StepArgs<R>& A, R* sEB, int oi, int oj, int ok) {
+    const Geom& g = A.g;
+    constexpr int H = LY::H;
+    const int ex = g.T[0] + 2 * H, ey = g.T[1] + 2 * H, ez = g.T[2] + 2 * H;
+    if (oi < H) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, H - oi, 0, ey, 0, ez);
+    if (oi + ex - H > g.n[0]) stage_box<R, LY>(A, sEB, oi, oj, ok, g.n[0] - oi + H, ex, 0, ey, 0, ez);
+    if (oj < H) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, H - oj, 0, ez);
+    if (oj + ey - H > g.n[1]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, g.n[1] - oj + H, ey, 0, ez);
+    if (!g.zopen) {
+        if (ok < H) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, H - ok);
+        if (ok + ez - H > g.n[2]) stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, g.n[2] - ok + H, ez);
     }
 }
 
+// Stage the whole block by loads.
+template <typename R, class LY>
+__device__ __forceinline__ void stage_all(const StepArgs<R>& A, R* sEB, int oi, int oj, int ok) {
+    const Geom& g = A.g;
+    const int ex = g.T[0] + 2 * LY::H, ey = g.T[1] + 2 * LY::H, ez = g.T[2] + 2 * LY::H;
+    if (ex == LY::EX && ey == LY::EY && ez == LY::EZ)
+        stage_box<R, LY, true>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
+    else
+        stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
+}
+
+// One tile t of the box described by A, by the whole CTA (the batch kernel);
+// `smem_raw` is the CTA's dynamic shared memory, whose J box is zero on entry
+// and is left zero; `tmap` the TMA descriptor of the box's E/B (null: staged
+// by loads).  Returns with the block converged; false if a TMA wait ran out
+// (the error word is set; the CTA must not use its shared memory again).
 template <int P, typename R, class LY>
-__global__ void __launch_bounds__(tile_block<R>(), 1)
-    k_tile_step(StepArgs<R> A, const __grid_constant__ CUtensorMap tmap, int use_tma) {
+__device__ __forceinline__ bool tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw,
+                                          const CUtensorMap* tmap = nullptr) {
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    const Geom& g = A.g;
+    constexpr int kZShift = tma_layout<LY, R>() ? 4 - LY::H : 0;
+    R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
+    R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
+
+    TileWork w;
+    plan_tile<R>(A, t, w);
+    if (w.end <= w.beg) return true;
+    PIC_CHECK_OR(w.beg >= 0 && w.end <= A.np, A.err, 1, ((long long)w.beg << 32) | unsigned(w.end), return true);
+    int oi, oj, ok;
+    tile_origin(g, t, oi, oj, ok);
+    RawParticle<R> next;
+    first_particle<R>(A, w, next);
+
+    // stage E, B of the tile and its halo (wrapped)
+    __shared__ __align__(8) unsigned long long s_bar;
+    const bool by_tma = tile_uses_tma<R, LY>(tmap, sm, ok);
+    if (by_tma) {
+        if (threadIdx.x == 0) mbar_init(&s_bar);
+        __syncthreads();
+        if (threadIdx.x == 0)
+            tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 4, oj - LY::H, oi - LY::H);
+        // every thread waits for the copy; if it did not land in time, all
+        // wait once more (it is still writing into this CTA's shared memory)
+        // and the caller stops using the block
+        const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0u, kTmaSpinLimit));
+        if (late) {
+            if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
+            mbar_wait(&s_bar, 0u, kTmaSpinLimit);
+            __syncthreads();
+            return false;
+        }
+        restage_wrapped<R, LY>(A, sEB, oi, oj, ok);
+    } else {
+        stage_all<R, LY>(A, sEB, oi, oj, ok);
+    }
+    __syncthreads();
+    if (by_tma && threadIdx.x == 0) mbar_inval(&s_bar);  // every thread is past its wait
+
+    tile_particles<P, R, LY>(A, w, oi, oj, ok, sEB, sJ, next);
+    __syncthreads();
+    flush_tile<R, LY>(A, sJ, oi, oj, ok);
+    return true;
+}
+
+// Next tile with particles from the queue (one thread), or -1 when none is left.
+__device__ __forceinline__ int next_tile(const int* __restrict__ offsets, int cpt, int ntiles, int* queue) {
+    for (;;) {
+        const int t = atomicAdd(queue, 1);
+        if (t >= ntiles) return -1;
+        if (offsets[(int64_t)(t + 1) * cpt] > offsets[(int64_t)t * cpt]) return t;
+    }
+}
+
+// Persistent tile loop of one box: each CTA pulls tiles from a queue counter
+// (zeroed before the launch) and pipelines them.  While it flushes tile t's
+// current, the TMA copy of tile t+1's E/B block is already in flight (the
+// gather of t is done with the block) and each lane's first particle of t+1
+// is loading; the flush clears the J box as it reads it, so no zeroing pass is
+// needed between tiles.  The E/B block is free once every warp has finished
+// tile t's particles; the J box once the flush is done.
+template <int P, typename R, class LY>
+__device__ __forceinline__ void tile_loop(const StepArgs<R>& A, int* queue, unsigned char* smem_raw,
+                                          const CUtensorMap* tmap) {
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    const Geom& g = A.g;
+    constexpr int kZShift = tma_layout<LY, R>() ? 4 - LY::H : 0;
+    R* sEB = sm + kZShift;
+    R* sJ = sm + 6 * LY::eVol;
+    const int ntiles = int(g.ntiles);
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_tile[2];
+
+    zero_jbox<R, LY>(sJ);
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar);
+        s_tile[0] = next_tile(A.offsets, g.cpt, ntiles, queue);
+    }
+    __syncthreads();
+    int t = s_tile[0];
+    if (t < 0) {
+        if (threadIdx.x == 0) mbar_inval(&s_bar);
+        return;
+    }
+    int oi, oj, ok;
+    tile_origin(g, t, oi, oj, ok);
+    TileWork w;
+    plan_tile<R>(A, t, w);
+    RawParticle<R> next;
+    first_particle<R>(A, w, next);
+    bool by_tma = tile_uses_tma<R, LY>(tmap, sm, ok);
+    if (by_tma) {
+        if (threadIdx.x == 0)
+            tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 4, oj - LY::H, oi - LY::H);
+    } else {
+        stage_all<R, LY>(A, sEB, oi, oj, ok);
+    }
+    unsigned phase = 0;  // parity of the barrier phase the next TMA copy completes
+    for (;;) {
+        if (threadIdx.x == 0) s_tile[1] = next_tile(A.offsets, g.cpt, ntiles, queue);
+        if (by_tma) {
+            // every thread waits for the copy; if it did not land in time, all
+            // wait once more (it is still writing into this CTA's shared
+            // memory), then the CTA stops: its block cannot be reused safely
+            const bool late = __syncthreads_or(!mbar_wait(&s_bar, phase, kTmaSpinLimit));
+            if (late) {
+                if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
+                mbar_wait(&s_bar, phase, kTmaSpinLimit);
+                __syncthreads();
+                return;
+            }
+            phase ^= 1u;
+            restage_wrapped<R, LY>(A, sEB, oi, oj, ok);
+        }
+        __syncthreads();  // E/B of t staged; s_tile[1] visible
+        PIC_CHECK_OR(w.beg >= 0 && w.end <= A.np, A.err, 1, ((long long)w.beg << 32) | unsigned(w.end),
+                     w.wbeg = w.wend = w.beg);
+        tile_particles<P, R, LY>(A, w, oi, oj, ok, sEB, sJ, next);
+        __syncthreads();  // every warp is done with t's E/B block and deposits
+        const int tn = s_tile[1];
+        int ni = 0, nj = 0, nk = 0;
+        bool tma_n = false;
+        if (tn >= 0) {
+            tile_origin(g, tn, ni, nj, nk);
+            tma_n = tile_uses_tma<R, LY>(tmap, sm, nk);
+            if (tma_n && threadIdx.x == 0)
+                tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), nk - 4, nj - LY::H, ni - LY::H);
+            plan_tile<R>(A, tn, w);
+            first_particle<R>(A, w, next);
+        }
+        flush_tile<R, LY>(A, sJ, oi, oj, ok);
+        if (tn >= 0 && !tma_n) stage_all<R, LY>(A, sEB, ni, nj, nk);
+        if (tn < 0) break;
+        __syncthreads();  // J box clear; a load-staged block complete
+        t = tn;
+        oi = ni, oj = nj, ok = nk;
+        by_tma = tma_n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&s_bar);
+}
+
+template <int P, typename R, class LY>
+__global__ void __launch_bounds__(LY::kThreads, LY::kMinBlocks)
+    k_tile_step(StepArgs<R> A, const __grid_constant__ CUtensorMap tmap, int use_tma, int* queue) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    tile_body<P, R, LY>(A, int(blockIdx.x), smem_raw, use_tma ? &tmap : nullptr);
+    tile_loop<P, R, LY>(A, queue, smem_raw, use_tma ? &tmap : nullptr);
 }
 
 // Batch of boxes: a persistent grid pulls (box, tile) items from a queue
 // counter (zeroed before the launch); each item's box arguments are copied
 // into shared memory first.  Items are ordered heaviest first.
 template <int P, typename R, class LY>
-__global__ void __launch_bounds__(tile_block<R>(), 1)
+__global__ void __launch_bounds__(LY::kThreads, LY::kMinBlocks)
     k_tile_step_batch(const StepArgs<R>* __restrict__ boxes, const int2* __restrict__ items, int nitems, int* queue) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(16) StepArgs<R> sA;
     __shared__ int s_item;
+    zero_jbox<R, LY>(reinterpret_cast<R*>(smem_raw) + 6 * LY::eVol);
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
         __syncthreads();
@@ -724,8 +905,9 @@ __global__ void __launch_bounds__(tile_block<R>(), 1)
             for (int w = threadIdx.x; w < int(sizeof(StepArgs<R>) / 4); w += blockDim.x) dst[w] = src[w];
         }
         __syncthreads();
-        tile_body<P, R, LY>(sA, bt.y, smem_raw, sA.tmap);
+        const bool ok = tile_body<P, R, LY>(sA, bt.y, smem_raw, sA.tmap);
         __syncthreads();
+        if (!ok) break;  // a TMA copy may still be landing in this CTA's block
     }
 }
 
@@ -888,17 +1070,32 @@ __global__ void __launch_bounds__(kBlock) k_deposit(StepArgs<R> A) {
 // ---------------------------------------------------------------------------
 static inline unsigned blocks_for(int64_t n) { return unsigned((n + kBlock - 1) / kBlock); }
 
+// Persistent CTAs of the tile kernel: as many as fit on the GPU at once (the
+// SM count times the CTAs per SM the kernel's resources allow), at most one
+// per tile.
+template <typename R, int P, class LY> int tile_grid(const pic_ctx* c) {
+    static int per_sm = 0;  // per instantiation; found outside stream capture by pic_init_grid
+    if (per_sm == 0) {
+        int n = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_tile_step<P, R, LY>, LY::kThreads,
+                                                          LY::template smem_bytes<R>()) != cudaSuccess ||
+            n < 1) {
+            cudaGetLastError();
+            n = 1;
+        }
+        per_sm = n;
+    }
+    const int64_t g = int64_t(c->sms) * per_sm;
+    return int(g < c->g.ntiles ? g : c->g.ntiles);
+}
+
 template <typename R, int P, class LY> cudaError_t tile_step_impl(pic_ctx* c) {
     StepArgs<R> A = make_args<R>(c);
     const size_t smem = LY::template smem_bytes<R>();
-    static size_t configured = 0;  // per instantiation; set outside stream capture by pic_init_grid
-    if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_tile_step<P, R, LY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             int(smem));
-        if (e != cudaSuccess) return e;
-        configured = smem;
-    }
-    k_tile_step<P, R, LY><<<unsigned(c->g.ntiles), tile_block<R>(), smem, c->stream>>>(A, c->tmap_eb, c->tma ? 1 : 0);
+    // the tile queue counter sits after the outsider count (zeroed with it)
+    int* queue = reinterpret_cast<int*>(c->err + 5);
+    k_tile_step<P, R, LY><<<unsigned(tile_grid<R, P, LY>(c)), LY::kThreads, smem, c->stream>>>(
+        A, c->tmap_eb, c->tma ? 1 : 0, queue);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_outsiders<P, R><<<152 * 4, kBlock, 0, c->stream>>>(A);
@@ -914,14 +1111,16 @@ template <typename R, class LY> cudaError_t tile_step_order(pic_ctx* c) {
 }
 
 template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
+    if constexpr (sizeof(R) == 4)
+        if (c->layout == 2) return tile_step_impl<float, 1, LayoutRow1>(c);
     return c->layout == 1 ? tile_step_order<R, LayoutRow<R>>(c) : tile_step_order<R, LayoutCube<R>>(c);
 }
 
 cudaError_t launch_tile_step(pic_ctx* c) {
     // J is one allocation of three components (see pic_api.cu); the outsider
-    // counter sits after the four error words
+    // count and the tile queue counter sit after the four error words
     cudaError_t e = cudaMemsetAsync(c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->err + 4, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->err + 4, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
 }
@@ -940,10 +1139,13 @@ bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], in
         return false;
     }
     const bool f64 = prec == PIC_FP64;
-    const cuuint32_t bz = layout == 1 ? (f64 ? LayoutRow<double>::eY : LayoutRow<float>::eY)
-                                      : (f64 ? LayoutCube<double>::eY : LayoutCube<float>::eY);
-    const cuuint32_t by = layout == 1 ? LayoutRow<float>::EY : LayoutCube<float>::EY;  // same for both precisions
-    const cuuint32_t bx = layout == 1 ? LayoutRow<float>::EX : LayoutCube<float>::EX;
+    if (layout == 2 && f64) return false;  // the halo-1 layout is FP32-mixed only
+    const cuuint32_t bz = layout == 2 ? LayoutRow1::eY
+                          : layout == 1 ? (f64 ? LayoutRow<double>::eY : LayoutRow<float>::eY)
+                                        : (f64 ? LayoutCube<double>::eY : LayoutCube<float>::eY);
+    // x, y extents are the same for both precisions
+    const cuuint32_t by = layout == 2 ? LayoutRow1::EY : layout == 1 ? LayoutRow<float>::EY : LayoutCube<float>::EY;
+    const cuuint32_t bx = layout == 2 ? LayoutRow1::EX : layout == 1 ? LayoutRow<float>::EX : LayoutCube<float>::EX;
     const cuuint64_t nz = cuuint64_t(n[2]), ny = cuuint64_t(n[1]), nx = cuuint64_t(n[0]);
     const cuuint64_t dims[4] = {nz, ny, nx, 6};
     const cuuint64_t strides[3] = {nz * rs, ny * nz * rs, cuuint64_t(comp_stride) * rs};  // bytes, dimensions 1..3
@@ -972,12 +1174,35 @@ cudaError_t configure_tile_kernels(pic_ctx* c) {
     cudaError_t e = cudaSuccess;
 #define PIC_CFG(R, P, LY)                                                              \
     if (e == cudaSuccess) e = set(k_tile_step<P, R, LY>, LY::template smem_bytes<R>());
+    PIC_CFG(float, 1, LayoutRow1)
     PIC_CFG(float, 1, LayoutRow<float>) PIC_CFG(float, 2, LayoutRow<float>) PIC_CFG(float, 3, LayoutRow<float>)
     PIC_CFG(float, 1, LayoutCube<float>) PIC_CFG(float, 2, LayoutCube<float>) PIC_CFG(float, 3, LayoutCube<float>)
     PIC_CFG(double, 1, LayoutRow<double>) PIC_CFG(double, 2, LayoutRow<double>) PIC_CFG(double, 3, LayoutRow<double>)
     PIC_CFG(double, 1, LayoutCube<double>) PIC_CFG(double, 2, LayoutCube<double>) PIC_CFG(double, 3, LayoutCube<double>)
 #undef PIC_CFG
-    (void)c;
+    // the persistent grids' CTAs per SM, found now (outside any stream capture)
+    if (e == cudaSuccess) {
+        switch (c->order) {
+        case 1:
+            if (c->prec == PIC_FP64) (void)(c->layout == 1 ? tile_grid<double, 1, LayoutRow<double>>(c)
+                                                           : tile_grid<double, 1, LayoutCube<double>>(c));
+            else (void)(c->layout == 2   ? tile_grid<float, 1, LayoutRow1>(c)
+                        : c->layout == 1 ? tile_grid<float, 1, LayoutRow<float>>(c)
+                                         : tile_grid<float, 1, LayoutCube<float>>(c));
+            break;
+        case 2:
+            if (c->prec == PIC_FP64) (void)(c->layout == 1 ? tile_grid<double, 2, LayoutRow<double>>(c)
+                                                           : tile_grid<double, 2, LayoutCube<double>>(c));
+            else (void)(c->layout == 1 ? tile_grid<float, 2, LayoutRow<float>>(c)
+                                       : tile_grid<float, 2, LayoutCube<float>>(c));
+            break;
+        default:
+            if (c->prec == PIC_FP64) (void)(c->layout == 1 ? tile_grid<double, 3, LayoutRow<double>>(c)
+                                                           : tile_grid<double, 3, LayoutCube<double>>(c));
+            else (void)(c->layout == 1 ? tile_grid<float, 3, LayoutRow<float>>(c)
+                                       : tile_grid<float, 3, LayoutCube<float>>(c));
+        }
+    }
     return e;
 }
 
@@ -987,7 +1212,7 @@ template <typename R, int P> cudaError_t tile_batch_impl(const BatchTileLaunch& 
     if (L.nitems <= 0) return cudaSuccess;
     const size_t smem = LY::template smem_bytes<R>();
     const int grid = L.grid < L.nitems ? L.grid : L.nitems;
-    k_tile_step_batch<P, R, LY><<<unsigned(grid), tile_block<R>(), smem, s>>>(
+    k_tile_step_batch<P, R, LY><<<unsigned(grid), LY::kThreads, smem, s>>>(
         static_cast<const StepArgs<R>*>(L.boxes), L.items, L.nitems, L.queue);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

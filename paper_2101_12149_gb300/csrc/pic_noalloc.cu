@@ -3,8 +3,9 @@
 // memory.  Its scratch (per-bin counts, the scan's look-back words and an
 // error word) lives in one file-scope static __device__ array; the call
 // allocates nothing.  The histogram and scan kernels are the ones pic_step
-// runs (pic_sort.cu); only the scatter of a permutation is specific to this
-// entry point.
+// runs (pic_sort.cu, constants in pic_sort.cuh); only the scatter of a
+// permutation is specific to this entry point.
+#include <cuda.h>  // CUcontext (the type only: cuCtxGetCurrent is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -13,23 +14,19 @@
 
 #include "pic_ctx.h"
 #include "pic_device.cuh"
+#include "pic_sort.cuh"
 
 namespace pic {
 
 // message reported by pic_last_error() (pic_api.cu)
 void set_last_error(const std::string& msg);
 
-// kernels of pic_sort.cu
-__global__ void k_hist(const int* key, int64_t np, int* count, int64_t C, unsigned* err);
-__global__ void k_scan(const int* count, int* offsets, int64_t C, unsigned long long* status, int nchunks,
-                       unsigned* err);
-
 namespace {
 
-constexpr int kBlockNA = 256;
-constexpr int kScanChunkNA = 256 * 16;  // items per scan CTA, as in pic_sort.cu
+constexpr int kBlockNA = kSortBlock;
 constexpr int64_t kMaxBins = int64_t(1) << 22;
-constexpr int64_t kMaxChunks = kMaxBins / kScanChunkNA;
+constexpr int64_t kMaxChunks = kMaxBins / kScanChunk;
+static_assert(kMaxBins % kScanChunk == 0, "the bin limit is a whole number of scan chunks");
 
 // layout: [error words: 4 x u32 = 16 B][pad to 256 B]
 //         [look-back words + ticket: (kMaxChunks + 1) x u64]
@@ -46,6 +43,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+CUcontext g_scratch_ctx[kMaxDevices] = {nullptr};  // the context each address belongs to
 
 __device__ __forceinline__ unsigned lanemask_lt_na() {
     unsigned m;
@@ -76,19 +74,41 @@ __global__ void __launch_bounds__(kBlockNA) k_perm_scatter(const int* __restrict
     if (dest >= 0 && dest < n) perm[dest] = int(p);
 }
 
-// Device address of the scratch array for the current device, resolved once
-// per device.
+// The calling thread's current CUDA context (null if the driver entry point is
+// unavailable): a device reset or a new primary context loads the module again
+// and can move the scratch array, so its address is looked up again whenever
+// the context differs from the one it was taken in.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext*);
+    static Fn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<Fn>(p);
+    }();
+    CUcontext ctx = nullptr;
+    if (!fn || fn(&ctx) != CUDA_SUCCESS) return nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array for the current device: looked up with
+// cudaGetSymbolAddress on the first call per device (that device current), and
+// again after the device's context has changed.
 cudaError_t scratch_for_current_device(unsigned char** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    const CUcontext ctx = current_context();
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    if (!g_scratch_ptr[dev] || (ctx && ctx != g_scratch_ctx[dev])) {
         void* ptr = nullptr;
         e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return e;
         g_scratch_ptr[dev] = ptr;
+        g_scratch_ctx[dev] = current_context();  // the lookup may have created the primary context
     }
     *out = static_cast<unsigned char*>(g_scratch_ptr[dev]);
     return cudaSuccess;
@@ -106,6 +126,12 @@ extern "C" pic_status pic_sort_keys_noalloc(const int32_t* keys, int64_t n, int3
                                             int32_t* perm, void* cuda_stream) {
     using namespace pic;
     if (n < 0 || n >= (int64_t(1) << 31)) return na_fail(PIC_ERR_ARG, "n must be in [0, 2^31)");
+    // an error left by the caller's earlier work stays where it is (not
+    // cleared): the launches below could not be told apart from it
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess)
+        return na_fail(PIC_ERR_CUDA, std::string("a CUDA error is pending from earlier work: ") +
+                                         cudaGetErrorString(pending));
     if (nbins < 1 || nbins > kMaxBins)
         return na_fail(PIC_ERR_ARG, "nbins must be in [1, 4194304], the no-allocation scratch limit");
     if (!offsets || (n > 0 && (!keys || !perm))) return na_fail(PIC_ERR_ARG, "NULL array");
@@ -116,14 +142,13 @@ extern "C" pic_status pic_sort_keys_noalloc(const int32_t* keys, int64_t n, int3
     unsigned* err = reinterpret_cast<unsigned*>(base);
     unsigned long long* status = reinterpret_cast<unsigned long long*>(base + kErrBytes);
     int* count = reinterpret_cast<int*>(base + kErrBytes + kStatusPadded);
-    const int nchunks = int((int64_t(nbins) + kScanChunkNA - 1) / kScanChunkNA);
+    const int nchunks = int((int64_t(nbins) + kScanChunk - 1) / kScanChunk);
     // the scratch keeps the previous call's contents: clear the error words,
     // the look-back words and ticket, and this call's counts
     e = cudaMemsetAsync(err, 0, kErrBytes, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, (size_t(nchunks) + 1) * sizeof(unsigned long long), s);
     if (e == cudaSuccess) e = cudaMemsetAsync(count, 0, size_t(nbins) * sizeof(int), s);
     if (e != cudaSuccess) return na_fail(PIC_ERR_CUDA, std::string("scratch clear: ") + cudaGetErrorString(e));
-    cudaGetLastError();
     if (n > 0) {
         const unsigned nb = unsigned((n + kBlockNA - 1) / kBlockNA);
         k_hist<<<nb, kBlockNA, 0, s>>>(keys, n, count, nbins, err);

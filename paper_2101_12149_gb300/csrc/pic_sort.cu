@@ -19,12 +19,10 @@
 
 #include "pic_ctx.h"
 #include "pic_device.cuh"
+#include "pic_sort.cuh"
 
 namespace pic {
 
-constexpr int kSortBlock = 256;
-constexpr int kScanItems = 16;
-constexpr int kScanChunk = kSortBlock * kScanItems;
 constexpr int kSpinLimit = 1 << 20;
 
 __device__ __forceinline__ unsigned lanemask_lt() {

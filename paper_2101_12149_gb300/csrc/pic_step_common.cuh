@@ -86,6 +86,7 @@ template <typename R> struct StepArgs {
     float inv_vscale;   // 1 / vscale (a power of two: exact)
     int64_t np;
     const CUtensorMap* tmap;  // batch of boxes: the box's E/B TMA descriptor in global memory, or null
+    float g2_fp64;            // FP32-mixed: gamma^2 above which the push's rotation runs in FP64
 };
 
 template <typename R> StepArgs<R> make_args(pic_ctx* c) {
@@ -130,6 +131,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     }
     a.np = c->np;
     a.tmap = nullptr;
+    a.g2_fp64 = std::isfinite(c->gamma_fp64) ? float(c->gamma_fp64 * c->gamma_fp64) : INFINITY;
     return a;
 }
 
@@ -370,8 +372,8 @@ __device__ __forceinline__ void push_particle(const StepArgs<R>& A, R EB[6], con
         const double xp = sizeof(R) == 8 ? xg0[0] : (double(cell[0]) + double(f0[0])) * A.g.d[0];
         EB[1] += R(A.drive_amp * cos(A.drive_k * xp - A.drive_k * t));
     }
-    if (A.pusher) vay<R>(A.kq, EB, EB + 3, u);
-    else boris<R>(A.kq, EB, EB + 3, u);
+    if (A.pusher) vay<R>(A.kq, EB, EB + 3, u, A.g2_fp64);
+    else boris<R>(A.kq, EB, EB + 3, u, A.g2_fp64);
     mv.ok = true;
     if (sizeof(R) == 8) {
         const double gi = 1.0 / sqrt(1.0 + double(u[0]) * double(u[0]) + double(u[1]) * double(u[1]) +

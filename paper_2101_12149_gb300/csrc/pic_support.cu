@@ -4,6 +4,7 @@
 // re-keying of particles after a change of tile shape.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -227,11 +228,13 @@ __global__ void k_load(StepArgs<R> A, const double* x, const double* y, const do
     if (!ok) raise_error(A.err, ERRBIT_PARTICLE);
 }
 
+// Particles [p0, p0 + cnt) into element 0.. of the destination arrays.
 template <typename R>
-__global__ void k_store(StepArgs<R> A, double* x, double* y, double* z, double* ux, double* uy, double* uz,
-                        double* w, const int* idsrc, int32_t* id) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= A.np) return;
+__global__ void k_store(StepArgs<R> A, int64_t p0, int64_t cnt, double* x, double* y, double* z, double* ux,
+                        double* uy, double* uz, double* w, const int* idsrc, int32_t* id) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cnt) return;
+    const int64_t p = p0 + i;
     const Geom& g = A.g;
     double* xs[3] = {x, y, z};
     double* us[3] = {ux, uy, uz};
@@ -240,12 +243,12 @@ __global__ void k_store(StepArgs<R> A, double* x, double* y, double* z, double* 
     for (int a = 0; a < 3; ++a) {
         if (xs[a]) {
             double v = sizeof(R) == 8 ? double(A.pa[a][p]) : (double(cell[a]) + double(A.pa[a][p])) * g.d[a];
-            xs[a][p] = wrap_pos(v, g.L[a]);
+            xs[a][i] = wrap_pos(v, g.L[a]);
         }
-        if (us[a]) us[a][p] = double(A.pa[3 + a][p]);
+        if (us[a]) us[a][i] = double(A.pa[3 + a][p]);
     }
-    if (w) w[p] = double(A.pa[6][p]);
-    if (id) id[p] = idsrc[p];
+    if (w) w[i] = double(A.pa[6][p]);
+    if (id) id[i] = idsrc[p];
 }
 
 template <typename S, typename D> __global__ void k_convert(const S* src, D* dst, int64_t n) {
@@ -525,33 +528,37 @@ cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id) {
-    if (c->np == 0) return cudaSuccess;
+cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id, int64_t p0, int64_t cnt) {
+    if (cnt <= 0) return cudaSuccess;
     if (c->prec == PIC_FP64) {
         auto A = make_args<double>(c);
-        k_store<double><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
-                                                                    dst[5], dst[6], c->P[c->cur].id, id);
+        k_store<double><<<blocks_for(cnt), kBlock, 0, c->stream>>>(A, p0, cnt, dst[0], dst[1], dst[2], dst[3],
+                                                                   dst[4], dst[5], dst[6], c->P[c->cur].id, id);
     } else {
         auto A = make_args<float>(c);
-        k_store<float><<<blocks_for(c->np), kBlock, 0, c->stream>>>(A, dst[0], dst[1], dst[2], dst[3], dst[4],
-                                                                   dst[5], dst[6], c->P[c->cur].id, id);
+        k_store<float><<<blocks_for(cnt), kBlock, 0, c->stream>>>(A, p0, cnt, dst[0], dst[1], dst[2], dst[3],
+                                                                  dst[4], dst[5], dst[6], c->P[c->cur].id, id);
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst) {
+cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst, int64_t i0, int64_t cnt) {
+    if (cnt <= 0) return cudaSuccess;
     if (c->prec == PIC_FP64)
-        return cudaMemcpyAsync(dst, c->F[which], c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    k_convert<float, double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(static_cast<const float*>(c->F[which]),
-                                                                         dst, c->g.C);
+        return cudaMemcpyAsync(dst, static_cast<const double*>(c->F[which]) + i0, cnt * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream);
+    k_convert<float, double><<<blocks_for(cnt), kBlock, 0, c->stream>>>(
+        static_cast<const float*>(c->F[which]) + i0, dst, cnt);
     return cudaGetLastError();
 }
 
-cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src) {
+cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src, int64_t i0, int64_t cnt) {
+    if (cnt <= 0) return cudaSuccess;
     if (c->prec == PIC_FP64)
-        return cudaMemcpyAsync(c->F[which], src, c->g.C * sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
-    k_convert<double, float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(src, static_cast<float*>(c->F[which]),
-                                                                         c->g.C);
+        return cudaMemcpyAsync(static_cast<double*>(c->F[which]) + i0, src, cnt * sizeof(double),
+                               cudaMemcpyDeviceToDevice, c->stream);
+    k_convert<double, float><<<blocks_for(cnt), kBlock, 0, c->stream>>>(src, static_cast<float*>(c->F[which]) + i0,
+                                                                       cnt);
     return cudaGetLastError();
 }
 
@@ -577,6 +584,136 @@ template <typename R> cudaError_t diag_impl(pic_ctx* c, double* d_out) {
 
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out) {
     return c->prec == PIC_FP64 ? diag_impl<double>(c, d_out) : diag_impl<float>(c, d_out);
+}
+
+// ---------------------------------------------------------------------------
+// charge density and the discrete continuity residual (Sec. 3.4.1: the
+// Esirkepov current conserves charge exactly; Sec. 2.6 reductions)
+// ---------------------------------------------------------------------------
+// rho(node) += (q w / dV) S_x S_y S_z of each particle (order-P node weights
+// at its position, FP64), periodic fold; with z open nodes beyond the z ends
+// take nothing.  One particle per thread, FP64 atomics.
+template <int P, typename R> __global__ void __launch_bounds__(kBlock) k_rho(StepArgs<R> A, double q_dv, double* rho) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= A.np) return;
+    const Geom& g = A.g;
+    int cell[3];
+    double f[3];
+    if (sizeof(R) == 8) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) split_pos(double(A.pa[a][p]), g.d[a], g.n[a], cell[a], f[a]);
+    } else {
+        const int key = A.key[p];
+        if (key < g.kbase || key >= dead_key(g)) return;
+        cell_of(g, key, cell[0], cell[1], cell[2]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[a] = double(A.pa[a][p]);
+    }
+    double w[3][P + 1];
+    int first[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Shape<P, double>::weights(f[a], first[a], w[a]);
+    const double qw = q_dv * double(A.pa[6][p]);
+#pragma unroll
+    for (int i = 0; i <= P; ++i) {
+        const int64_t gi = wrap_once(cell[0] + first[0] + i, g.n[0]);
+#pragma unroll
+        for (int j = 0; j <= P; ++j) {
+            const int64_t gj = wrap_once(cell[1] + first[1] + j, g.n[1]);
+            const double wij = qw * w[0][i] * w[1][j];
+#pragma unroll
+            for (int k = 0; k <= P; ++k) {
+                const int kz = cell[2] + first[2] + k;
+                if (g.zopen && unsigned(kz) >= unsigned(g.n[2])) continue;
+                atomicAdd(rho + (gi * g.n[1] + gj) * g.n[2] + wrap_once(kz, g.n[2]), wij * w[2][k]);
+            }
+        }
+    }
+}
+
+// r = rho1 - rho0 + dt div J at every node of z-planes [k0, k1), div J the
+// nodal divergence of the edge-centred current ((Jx[i] - Jx[i-1])/dx + ...,
+// periodic; with z open J beyond the ends is zero); out[0] = max |r|,
+// out[1] = max |rho0| (non-negative FP64 values compared as bit patterns).
+// One warp per z-row at a time.
+template <typename R>
+__global__ void k_continuity(const double* rho0, const double* rho1, const R* Jx, const R* Jy, const R* Jz, int nx,
+                             int ny, int nz, double dtdx, double dtdy, double dtdz, int zopen, int k0, int k1,
+                             unsigned long long* out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t rows = (int64_t)nx * ny;
+    double mr = 0.0, m0 = 0.0;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
+         r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int i = int(r / ny), j = int(r - (int64_t)i * ny);
+        const int64_t c0 = r * nz;
+        const int64_t im0 = ((int64_t)wrap_once(i - 1, nx) * ny + j) * nz;
+        const int64_t jm0 = ((int64_t)i * ny + wrap_once(j - 1, ny)) * nz;
+        for (int k = k0 + lane; k < k1; k += 32) {
+            const int64_t c = c0 + k;
+            const double jz_dn = zopen && k == 0 ? 0.0 : double(Jz[c0 + wrap_once(k - 1, nz)]);
+            const double div = (double(Jx[c]) - double(Jx[im0 + k])) * dtdx +
+                               (double(Jy[c]) - double(Jy[jm0 + k])) * dtdy + (double(Jz[c]) - jz_dn) * dtdz;
+            const double res = rho1[c] - rho0[c] + div;
+            mr = fmax(mr, fabs(res));
+            m0 = fmax(m0, fabs(rho0[c]));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, o));
+        m0 = fmax(m0, __shfl_down_sync(0xffffffffu, m0, o));
+    }
+    if (lane == 0) {
+        atomicMax(out, (unsigned long long)__double_as_longlong(mr));
+        atomicMax(out + 1, (unsigned long long)__double_as_longlong(m0));
+    }
+}
+
+template <typename R, int P> cudaError_t rho_impl(pic_ctx* c, double* rho) {
+    k_rho<P, R><<<blocks_for(c->np), kBlock, 0, c->stream>>>(make_args<R>(c),
+                                                             c->q / (c->g.d[0] * c->g.d[1] * c->g.d[2]), rho);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_charge_density(pic_ctx* c, double* rho) {
+    cudaError_t e = cudaMemsetAsync(rho, 0, size_t(c->g.C) * sizeof(double), c->stream);
+    if (e != cudaSuccess || c->np == 0) return e;
+    if (c->prec == PIC_FP64) {
+        switch (c->order) {
+        case 1: return rho_impl<double, 1>(c, rho);
+        case 2: return rho_impl<double, 2>(c, rho);
+        default: return rho_impl<double, 3>(c, rho);
+        }
+    }
+    switch (c->order) {
+    case 1: return rho_impl<float, 1>(c, rho);
+    case 2: return rho_impl<float, 2>(c, rho);
+    default: return rho_impl<float, 3>(c, rho);
+    }
+}
+
+template <typename R>
+cudaError_t continuity_impl(pic_ctx* c, const double* rho0, const double* rho1, unsigned long long* out) {
+    // with z open the residual covers the planes whose stencils never reach
+    // beyond the ends (the current there is dropped, particles leaving are removed)
+    const int margin = c->g.zopen ? c->order + 2 : 0;
+    const int k0 = margin, k1 = c->g.n[2] - margin;
+    const int64_t rows = int64_t(c->g.n[0]) * c->g.n[1];
+    const unsigned nb = unsigned(std::min<int64_t>((rows * 32 + kBlock - 1) / kBlock, 152 * 8));
+    k_continuity<R><<<nb, kBlock, 0, c->stream>>>(rho0, rho1, static_cast<const R*>(c->F[6]),
+                                                  static_cast<const R*>(c->F[7]), static_cast<const R*>(c->F[8]),
+                                                  c->g.n[0], c->g.n[1], c->g.n[2], c->dt / c->g.d[0],
+                                                  c->dt / c->g.d[1], c->dt / c->g.d[2], c->g.zopen, k0,
+                                                  k1 > k0 ? k1 : k0, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_continuity(pic_ctx* c, const double* rho0, const double* rho1, unsigned long long* out) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    return c->prec == PIC_FP64 ? continuity_impl<double>(c, rho0, rho1, out)
+                               : continuity_impl<float>(c, rho0, rho1, out);
 }
 
 template <typename R> cudaError_t window_shift_impl(pic_ctx* c) {

@@ -81,6 +81,12 @@ def load_library(path: str = LIB_PATH):
             "pic_launch_count": [P, ct.POINTER(I64)],
             "pic_destroy": [P],
             "pic_sort_keys_noalloc": [P, I64, I32, P, P, P],
+            "pic_reserve_adjoint": [P, I32, I32],
+            "pic_charge_density": [P, P, ct.c_int],
+            "pic_continuity_mark": [P],
+            "pic_continuity_residual": [P, P],
+            "pic_set_fp64_gamma": [P, D],
+            "pic_measure_fma_peak": [I32, ct.POINTER(D)],
             "pic_batch_init": [I32, P, P, P, D, D, I32, P, ct.POINTER(P)],
             "pic_batch_load_particles": [P, D, D, P, P, P, P, P, P, P, P, ct.c_int],
             "pic_batch_step": [P, I32],
@@ -287,6 +293,32 @@ class Context:
         _check(self.lib.pic_diagnostics(self.h, out))
         return {"field_energy": out[0], "kinetic_energy": out[1], "charge": out[2], "max_div_b": out[3]}
 
+    def charge_density(self, out=None):
+        """Nodal charge density of the current particles (FP64, shape (nx, ny, nz))."""
+        if out is None:
+            out = np.empty(self.n)
+        p, dev = _ptr(out)
+        _check(self.lib.pic_charge_density(self.h, p, dev))
+        return out
+
+    def continuity_mark(self):
+        _check(self.lib.pic_continuity_mark(self.h))
+
+    def continuity_residual(self):
+        """max|rho^{n+1} - rho^n + dt div J| over the last step: relative to
+        max|rho^n|, absolute, and max|rho^n|; the new density becomes the mark."""
+        out = (ct.c_double * 3)()
+        _check(self.lib.pic_continuity_residual(self.h, out))
+        return {"relative": out[0], "absolute": out[1], "rho_max": out[2]}
+
+    def set_fp64_gamma(self, gamma):
+        """FP32-mixed: Lorentz factor above which the push's rotation runs in FP64 (inf: never)."""
+        _check(self.lib.pic_set_fp64_gamma(self.h, float(gamma)))
+
+    def reserve_adjoint(self, nsteps, ckpt_every=20):
+        """Keep the work space of step_adjoint(nsteps, ckpt_every) (0 releases it)."""
+        _check(self.lib.pic_reserve_adjoint(self.h, int(nsteps), int(ckpt_every)))
+
     def sync(self):
         _check(self.lib.pic_sync(self.h))
 
@@ -418,6 +450,14 @@ class Batch:
         v = ct.c_int64()
         _check(self.lib.pic_batch_launch_count(self.h, ct.byref(v)))
         return v.value
+
+
+def measure_fma_peak(precision):
+    """Measured FMA throughput of the current device in TFLOP/s (FP32_MIXED: FP32, FP64: FP64)."""
+    lib = load_library()
+    out = ct.c_double()
+    _check(lib.pic_measure_fma_peak(int(precision), ct.byref(out)))
+    return out.value
 
 
 def sort_keys_noalloc(keys, nbins, offsets, perm, stream=None):

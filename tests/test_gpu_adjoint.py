@@ -195,3 +195,39 @@ def test_autograd_function_returns_the_library_gradients():
     assert abs(A.grad.item() - 3.0 * dA) < 1e-12 * abs(3.0 * dA)
     assert u0.grad.is_cuda
     assert _rel(u0.grad.cpu().numpy(), 3.0 * du) < 1e-12
+
+
+@pytest.mark.slow
+def test_fp64_adjoint_200_steps_matches_oracle_adjoint():
+    """The differentiation workload's full length on its 16^3 copy: 200 steps,
+    checkpoints every 20, the discrete adjoint on the GPU against the oracle's
+    (exact for the discrete map up to the order of additions), with the work
+    space reserved up front (pic_reserve_adjoint), so the adjoint call itself
+    allocates nothing."""
+    n, p, ppc, steps, ckpt = (16, 16, 16), 2, 4, 200, 20
+    loss_o, dA_o, du_o = _oracle_adjoint(n, p, ppc, steps)
+    with pic.Context(n, cfl=CFL, precision=pic.FP64, order=p) as c:
+        c.load_particles(-1.0, 1.0, _parts(n, ppc))
+        c.set_external_drive(A0, 2 * np.pi / n[0])
+        c.reserve_adjoint(steps, ckpt)
+        loss, dA, du = c.step_adjoint(steps, ckpt)
+    print(f"200-step adjoint: loss {loss:.6e} vs {loss_o:.6e}; dL/dA {dA:.9e} vs {dA_o:.9e}; "
+          f"dL/du rel {_rel(du, du_o):.2e}")
+    assert abs(loss - loss_o) < 1e-12 * loss_o, (loss, loss_o)
+    assert abs(dA - dA_o) < 1e-10 * abs(dA_o), (dA, dA_o)
+    assert _rel(du, du_o) < 1e-10, _rel(du, du_o)
+
+
+def test_reserved_adjoint_space_gives_the_same_gradients():
+    """pic_reserve_adjoint only changes where the work space comes from."""
+    n, p, ppc, steps, ckpt = (8, 8, 8), 2, 2, 12, 5
+    ref = _gpu_adjoint(n, p, ppc, steps, ckpt)
+    with pic.Context(n, cfl=CFL, precision=pic.FP64, order=p) as c:
+        c.load_particles(-1.0, 1.0, _parts(n, ppc))
+        c.set_external_drive(A0, 2 * np.pi / n[0])
+        c.reserve_adjoint(steps, ckpt)
+        got = c.step_adjoint(steps, ckpt)
+        c.reserve_adjoint(0)
+    # the two runs differ only in the order of floating-point atomic additions
+    assert abs(got[0] - ref[0]) < 1e-13 * ref[0] and abs(got[1] - ref[1]) < 1e-11 * abs(ref[1])
+    assert _rel(got[2], ref[2]) < 1e-11

@@ -149,3 +149,29 @@ def test_uniform_256_fp32_mixed_field_error_over_100_steps():
     err = rel_l2(F[pic.FP32_MIXED], F[pic.FP64])
     print(f"256^3, 100 steps: FP32-mixed vs FP64 field relative L2 {err:.3e}")
     assert err < 1e-5, err
+
+
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+def test_uniform_256_continuity_residual(precision):
+    """Discrete continuity on the full 256^3 x 8 ppc order-3 workload, over the
+    first two steps and two steps later in the run (fields grown from the
+    plasma's noise): max |rho^{n+1} - rho^n + dt div J| / max |rho^n|, FP64
+    <= 1e-13, FP32-mixed stated (bound 2e-6)."""
+    import torch
+    parts = inputs.workload_particles("uniform_256")
+    stream = torch.cuda.Stream()
+    bound = 1e-13 if precision == pic.FP64 else 2e-6
+    with pic.Context(W["n"], cfl=W["cfl"], order=W["order"], precision=precision, stream=stream) as c:
+        c.load_particles(-1.0, 1.0, parts)
+        res = []
+        c.continuity_mark()
+        for _ in range(2):
+            c.step(1)
+            res.append(c.continuity_residual()["relative"])
+        c.step(8)
+        c.continuity_mark()
+        for _ in range(2):
+            c.step(1)
+            res.append(c.continuity_residual()["relative"])
+    print(f"256^3 continuity residual precision {precision}: {res}")
+    assert max(res) < bound, res

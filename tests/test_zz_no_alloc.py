@@ -76,3 +76,57 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
         pic.sort_keys_noalloc(k, (1 << 22) + 1, off, k)
     assert ei.value.status == pic.PIC_ERR_ARG
     assert "4194304" in str(ei.value)
+
+
+def _check_sort(keys_np, nbins, off, pm):
+    """offsets are the exclusive prefix sum of the histogram; perm is a
+    permutation that groups the keys by bin in ascending bin order."""
+    ref_off = np.concatenate([[0], np.cumsum(np.bincount(keys_np, minlength=nbins))])
+    assert np.array_equal(off, ref_off)
+    assert np.array_equal(np.sort(pm), np.arange(keys_np.size))
+    assert np.all(np.diff(keys_np[pm]) >= 0)
+
+
+def test_noalloc_at_the_bin_limit():
+    """nbins = 4,194,304, the scratch limit: 1,024 scan chunks, so each
+    chunk's look-back spans many 32-chunk windows; then a smaller call on the
+    same scratch, whose counts must start from zero again."""
+    nbins = 1 << 22
+    rng = np.random.default_rng(7)
+    stream = torch.cuda.current_stream()
+    for nb, n in ((nbins, 3_000_000), (5000, 20_000)):
+        keys_np = rng.integers(0, nb, size=n).astype(np.int64)
+        keys_np[:1000] = nb - 1  # a crowded last bin
+        keys = torch.from_numpy(keys_np.astype(np.int32)).cuda()
+        off = torch.full((nb + 1,), -7, dtype=torch.int32, device="cuda")
+        perm = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        pic.sort_keys_noalloc(keys, nb, off, perm, stream=stream)
+        torch.cuda.synchronize()
+        _check_sort(keys_np, nb, off.cpu().numpy().astype(np.int64), perm.cpu().numpy().astype(np.int64))
+
+
+def test_noalloc_empty_and_out_of_range_keys():
+    """n = 0 gives all-zero offsets (two scan chunks at nbins = 5000); a key
+    equal to nbins is rejected with PIC_ERR_ARG; a valid call afterwards
+    sorts correctly (the scratch is cleared after an error)."""
+    nb = 5000
+    off = torch.full((nb + 1,), -7, dtype=torch.int32, device="cuda")
+    empty = torch.zeros(0, dtype=torch.int32, device="cuda")
+    pic.sort_keys_noalloc(empty, nb, off, empty)
+    torch.cuda.synchronize()
+    assert np.array_equal(off.cpu().numpy(), np.zeros(nb + 1, dtype=np.int32))
+
+    rng = np.random.default_rng(8)
+    keys_np = rng.integers(0, nb, size=4000).astype(np.int64)
+    bad = keys_np.copy()
+    bad[123] = nb
+    perm = torch.zeros(bad.size, dtype=torch.int32, device="cuda")
+    with pytest.raises(pic.PicError) as ei:
+        pic.sort_keys_noalloc(torch.from_numpy(bad.astype(np.int32)).cuda(), nb, off, perm)
+    assert ei.value.status == pic.PIC_ERR_ARG
+    assert "outside" in str(ei.value)
+
+    keys = torch.from_numpy(keys_np.astype(np.int32)).cuda()
+    pic.sort_keys_noalloc(keys, nb, off, perm)
+    torch.cuda.synchronize()
+    _check_sort(keys_np, nb, off.cpu().numpy().astype(np.int64), perm.cpu().numpy().astype(np.int64))
