@@ -285,6 +285,22 @@ pic_status pic_charge_density(pic_ctx* ctx, double* dst, int on_device);
 pic_status pic_continuity_mark(pic_ctx* ctx);
 pic_status pic_continuity_residual(pic_ctx* ctx, double out[3]);
 
+/* Filter along z of the fields the particles gather (Sec. 4.2 applies the
+ * Godfrey filter to E and B before gathering them; the paper gives no
+ * coefficients, so this is the compensated binomial form of that filter
+ * family): before each step's gather, E and B are copied through `passes`
+ * passes of the stencil (1/4, 1/2, 1/4) along z and one compensation pass
+ * (-passes/4, 1 + passes/2, -passes/4), each reading the previous pass's
+ * output, periodic along z or zero beyond the z ends with a moving window.
+ * The transfer function on a mode e^{ikz} is cos^(2 passes)(k dz/2)
+ * (1 + passes sin^2(k dz/2)): long waves pass (1 - O(k^4)), the Nyquist mode
+ * is removed.  The particles gather from the filtered copy; the field update
+ * advances the unfiltered fields.  passes = 0 switches it off.  The first
+ * call with passes > 0 allocates the copy (6 C values).  PIC_ERR_ARG for
+ * passes outside [0, 16] or nz beyond the shared-memory column (about 25,600
+ * FP32 / 12,800 FP64 cells); pic_step_adjoint needs it off.  Waits. */
+pic_status pic_set_gather_filter(pic_ctx* ctx, int32_t passes);
+
 /* FP32-mixed precision: the Lorentz factor above which the push's magnetic
  * rotation (Boris: gamma^- and the rotation; Vay: the solve, for |u'| above
  * it) is computed in FP64 instead of FP32.  Default 1e3; +infinity never

@@ -50,6 +50,8 @@ def _declare(lib):
         "orc_pic_step_full": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I, I]),
         "orc_yee_b_ckc": (None, [G, D, P, P]),
         "orc_yee_step_ckc": (None, [G, D, P, P, P]),
+        "orc_filter_z": (None, [G, I, P, P]),
+        "orc_pic_step_filtered": (None, [G, I, D, D, D, L, P, P, P, P, P, P, P, P, D, D, D, I, I, I, I]),
         "orc_div_edge": (None, [G, P, P]),
         "orc_div_face": (None, [G, P, P]),
         "orc_field_energy": (D, [G, P]),
@@ -225,18 +227,33 @@ class Oracle:
                               self._ptr_array([fields[6], fields[7], fields[8]]))
 
     def pic_step(self, g, p, dt, q, m, parts, fields, drive_amp=0.0, drive_k=0.0, t=0.0, pusher=0, gather=0,
-                 solver=0):
+                 solver=0, filter_passes=0):
         """One PIC step, in place on parts (dict of x,y,z,ux,uy,uz,w float64
         arrays) and fields (9, nx, ny, nz); pusher 0 Boris / 1 Vay, gather 0
-        momentum- / 1 energy-conserving."""
+        momentum- / 1 energy-conserving; filter_passes > 0: the particles
+        gather from E and B filtered along z (orc_filter_z)."""
         keys = ("x", "y", "z", "ux", "uy", "uz", "w")
         for k in keys:
             assert parts[k].dtype == np.float64 and parts[k].flags.c_contiguous
         assert fields.dtype == np.float64 and fields.flags.c_contiguous
+        if filter_passes:
+            self.lib.orc_pic_step_filtered(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
+                                           *[self._ptr(parts[k]) for k in keys],
+                                           self._ptr_array([fields[c] for c in range(9)]),
+                                           float(drive_amp), float(drive_k), float(t), int(pusher), int(gather),
+                                           int(solver), int(filter_passes))
+            return
         self.lib.orc_pic_step_full(ct.byref(g), int(p), float(dt), float(q), float(m), parts["x"].size,
                                    *[self._ptr(parts[k]) for k in keys],
                                    self._ptr_array([fields[c] for c in range(9)]),
                                    float(drive_amp), float(drive_k), float(t), int(pusher), int(gather), int(solver))
+
+    def filter_z(self, g, npass, F):
+        """orc_filter_z on one component (nx, ny, nz)."""
+        F = self._f64(F)
+        out = np.empty_like(F)
+        self.lib.orc_filter_z(ct.byref(g), int(npass), self._ptr(F), self._ptr(out))
+        return out
 
     # -- moving window (z open) -----------------------------------------
     # Readings of the wakefield run: z is open (fields beyond the ends are
@@ -282,7 +299,8 @@ class Oracle:
         assert g.zopen
         Lz = g.n[2] * g.d[2]
         self.pic_step(g, p, dt, q, m, parts, fields, 0.0, 0.0, win["step"] * dt, pusher=win.get("pusher", 0),
-                      gather=win.get("gather", 0), solver=win.get("solver", 0))
+                      gather=win.get("gather", 0), solver=win.get("solver", 0),
+                      filter_passes=win.get("filter_passes", 0))
         keep = (parts["z"] >= 0.0) & (parts["z"] < Lz)
         parts = {k: np.ascontiguousarray(v[keep]) for k, v in parts.items()}
         win["step"] += 1

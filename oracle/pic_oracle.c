@@ -479,16 +479,84 @@ void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, i
     orc_pic_step_full(g, p, dt, q, m, np, x, y, z, ux, uy, uz, w, fields, drive_amp, drive_k, t, pusher, gather, 0);
 }
 
+/* The step with the fields the particles gather from given separately (F:
+ * Ex..Bz as gathered; fields: the ones the Yee update advances). */
+static void step_impl(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                      double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                      const double* const F[6], double drive_amp, double drive_k, double t, int pusher, int gather,
+                      int solver);
+
 /* The same with a choice of field solver too (0 Yee, 1 CKC). */
 void orc_pic_step_full(const orc_grid* g, int p, double dt, double q, double m, int64_t np,
                        double* x, double* y, double* z, double* ux, double* uy, double* uz,
                        const double* w, double* const fields[9],
                        double drive_amp, double drive_k, double t, int pusher, int gather, int solver) {
+    const double* const F[6] = {fields[0], fields[1], fields[2], fields[3], fields[4], fields[5]};
+    step_impl(g, p, dt, q, m, np, x, y, z, ux, uy, uz, w, fields, F, drive_amp, drive_k, t, pusher, gather, solver);
+}
+
+/* Digital filter along z applied to E and B before the gather (the Godfrey
+ * filter of the paper's plasma-acceleration run, Sec. 4.2; the paper gives no
+ * coefficients, so this is the compensated binomial form of that family of
+ * filters): npass passes of the stencil (1/4, 1/2, 1/4), then one
+ * compensation pass (-npass/4, 1 + npass/2, -npass/4); each pass reads the
+ * previous one's output, periodic along z, or zero beyond the z ends when z
+ * is open.  On a periodic Fourier mode e^{i k z} one pass multiplies by
+ * cos^2(k dz/2), the compensation by 1 + npass sin^2(k dz/2): the transfer
+ * function cos^(2 npass)(k dz/2) (1 + npass sin^2(k dz/2)) is 1 at k = 0, 0 at
+ * the Nyquist mode and 1 - O(k^4) for long waves.  npass = 0: a copy. */
+void orc_filter_z(const orc_grid* g, int npass, const double* in, double* out) {
+    const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    double* tmp = (double*)malloc((size_t)C * sizeof(double));
+    memcpy(out, in, (size_t)C * sizeof(double));
+    for (int pass = 0; pass <= npass && npass > 0; ++pass) {
+        double a, b; /* stencil (a, b, a) */
+        if (pass < npass) {
+            a = 0.25;
+            b = 0.5;
+        } else {
+#if ORC_MUTANT == 15
+            a = 0.25 * npass; /* planted: compensation with the wrong sign */
+#else
+            a = -0.25 * npass;
+#endif
+            b = 1.0 - 2.0 * a;
+        }
+        memcpy(tmp, out, (size_t)C * sizeof(double));
+        for (int64_t i = 0; i < g->n[0]; ++i)
+            for (int64_t j = 0; j < g->n[1]; ++j)
+                for (int64_t k = 0; k < g->n[2]; ++k)
+                    out[idx3(g, i, j, k)] = a * fetch(g, tmp, i, j, k - 1) + b * tmp[idx3(g, i, j, k)] +
+                                            a * fetch(g, tmp, i, j, k + 1);
+    }
+    free(tmp);
+}
+
+/* The step with the particles gathering from E and B filtered along z by
+ * orc_filter_z (npass passes); the Yee update advances the unfiltered fields. */
+void orc_pic_step_filtered(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x,
+                           double* y, double* z, double* ux, double* uy, double* uz, const double* w,
+                           double* const fields[9], double drive_amp, double drive_k, double t, int pusher,
+                           int gather, int solver, int npass) {
+    const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
+    double* buf = (double*)malloc(6 * (size_t)C * sizeof(double));
+    const double* F[6];
+    for (int c = 0; c < 6; ++c) {
+        orc_filter_z(g, npass, fields[c], buf + c * C);
+        F[c] = buf + c * C;
+    }
+    step_impl(g, p, dt, q, m, np, x, y, z, ux, uy, uz, w, fields, F, drive_amp, drive_k, t, pusher, gather, solver);
+    free(buf);
+}
+
+static void step_impl(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
+                      double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
+                      const double* const F[6], double drive_amp, double drive_k, double t, int pusher, int gather,
+                      int solver) {
     const int64_t C = (int64_t)g->n[0] * g->n[1] * g->n[2];
     double* const E[3] = {fields[0], fields[1], fields[2]};
     double* const B[3] = {fields[3], fields[4], fields[5]};
     double* const J[3] = {fields[6], fields[7], fields[8]};
-    const double* const F[6] = {fields[0], fields[1], fields[2], fields[3], fields[4], fields[5]};
     const double L[3] = {g->n[0] * g->d[0], g->n[1] * g->d[1], g->n[2] * g->d[2]};
     for (int c = 0; c < 3; ++c) memset(J[c], 0, (size_t)C * sizeof(double));
     for (int64_t n = 0; n < np; ++n) {

@@ -37,6 +37,11 @@ void orc_pic_step_full(const orc_grid* g, int p, double dt, double q, double m, 
 void orc_pic_step_alg(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x, double* y,
                       double* z, double* ux, double* uy, double* uz, const double* w, double* const fields[9],
                       double drive_amp, double drive_k, double t, int pusher, int gather);
+void orc_filter_z(const orc_grid* g, int npass, const double* in, double* out);
+void orc_pic_step_filtered(const orc_grid* g, int p, double dt, double q, double m, int64_t np, double* x,
+                           double* y, double* z, double* ux, double* uy, double* uz, const double* w,
+                           double* const fields[9], double drive_amp, double drive_k, double t, int pusher,
+                           int gather, int solver, int npass);
 void orc_div_edge(const orc_grid* g, const double* const F[3], double* out);
 void orc_div_face(const orc_grid* g, const double* const F[3], double* out);
 double orc_field_energy(const orc_grid* g, const double* const F[6]);

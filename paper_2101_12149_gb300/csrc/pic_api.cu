@@ -249,6 +249,7 @@ cudaError_t run_yee(pic_ctx* c) {
 cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
     cudaError_t e;
     if (with_sort && (e = run_sort(c)) != cudaSuccess) return e;
+    if (c->filter_passes > 0 && (e = counted(c, "k_filter_z", 1, pic::launch_filter)) != cudaSuccess) return e;
     if ((e = counted(c, "k_tile_step", 2, pic::launch_tile_step)) != cudaSuccess) return e;
     return run_yee(c);
 }
@@ -271,6 +272,7 @@ cudaError_t inject(pic_ctx* c) { return pic::launch_inject(c); }
 // next cell, then a sort that also drops the removed particles.  The state
 // after the step is sorted and holds only live particles.
 pic_status run_window_step(pic_ctx* c) {
+    if (c->filter_passes > 0) PIC_CUDA(counted(c, "k_filter_z", 1, pic::launch_filter));
     PIC_CUDA(counted(c, "k_tile_step", 2, pic::launch_tile_step));
     PIC_CUDA(run_yee(c));
     c->step += 1;
@@ -628,6 +630,7 @@ pic_status pic_destroy(pic_ctx* c) {
     cudaFree(c->stage);
     cudaFree(c->adj_space);
     cudaFree(c->rho);
+    cudaFree(c->Fg);
     destroy_timing(c);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     delete c;
@@ -788,6 +791,7 @@ pic_status pic_gather_push(pic_ctx* c) {
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     if (cudaError_t e = pic::alloc_scratch(c))
         return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "split-API scratch") : cuda_fail(e, "scratch");
+    if (c->filter_passes > 0) PIC_CUDA(counted(c, "k_filter_z", 1, pic::launch_filter));
     PIC_CUDA(counted(c, "k_gather_push", 1, pic::launch_gather_push_global));
     c->have_old = true;
     return PIC_OK;
@@ -894,8 +898,9 @@ pic_status pic_step_adjoint(pic_ctx* c, int32_t nsteps, int32_t ckpt_every, doub
     if (pic_status s = check_ctx(c)) return s;
     if (nsteps < 0 || ckpt_every < 1) return fail(PIC_ERR_ARG, "nsteps must be >= 0 and ckpt_every >= 1");
     if (c->window) return fail(PIC_ERR_STATE, "the adjoint runs periodic grids only");
-    if (c->pusher || c->egather || c->solver)
-        return fail(PIC_ERR_STATE, "the adjoint differentiates Boris, momentum-conserving gather and Yee only");
+    if (c->pusher || c->egather || c->solver || c->filter_passes)
+        return fail(PIC_ERR_STATE,
+                    "the adjoint differentiates Boris, momentum-conserving gather and Yee only (no z filter)");
     if (c->np == 0) return fail(PIC_ERR_STATE, "no particles loaded");
     PIC_CUDA(ensure_tile_order(c));
     PIC_CUDA(cudaStreamSynchronize(c->stream));
@@ -1196,6 +1201,29 @@ pic_status pic_continuity_residual(pic_ctx* c, double out[3]) {
     c->mark_step = c->step;
     c->mark_shifts = c->shifts;
     return read_error_word(c);
+}
+
+pic_status pic_set_gather_filter(pic_ctx* c, int32_t passes) {
+    if (pic_status s = check_ctx(c)) return s;
+    if (passes < 0 || passes > 16) return fail(PIC_ERR_ARG, "passes must be in [0, 16]");
+    if (passes > 0 && pic::filter_smem_bytes(c) > 200 * 1024)
+        return fail(PIC_ERR_ARG, "the z filter holds a z column in shared memory: nz too large");
+    PIC_CUDA(c->stream ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize());
+    if (passes > 0 && !c->Fg) {
+        if (cudaMalloc(&c->Fg, 6 * size_t(c->g.C) * c->rsize) != cudaSuccess) {
+            c->Fg = nullptr;
+            clear_stale("filter allocation");
+            return fail(PIC_ERR_OOM, "filtered field copy");
+        }
+        c->tma_g = pic::encode_eb_tensor_map(&c->tmap_g, c->Fg, c->g.n, c->g.C, c->layout, c->prec);
+        PIC_CUDA(pic::configure_filter(c));
+    }
+    if (c->graph) {  // the gathered arrays are kernel arguments baked into the graph
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    c->filter_passes = passes;
+    return PIC_OK;
 }
 
 pic_status pic_set_fp64_gamma(pic_ctx* c, double gamma) {

@@ -113,6 +113,13 @@ struct pic_ctx {
     int pusher = 0;   // 0 Boris, 1 Vay
     int egather = 0;  // 0 momentum-conserving, 1 energy-conserving gather
     double gamma_fp64 = 1e3;  // FP32-mixed: gamma above which the push's rotation runs in FP64 (inf: never)
+    // z filter of the gathered fields: passes (0 = off), the filtered E and B
+    // (6 arrays of C values, allocated when first switched on) and their TMA
+    // descriptor for the tile kernel
+    int filter_passes = 0;
+    void* Fg = nullptr;
+    CUtensorMap tmap_g;
+    bool tma_g = false;
 
     // charge density and continuity diagnostics: two FP64 density arrays
     // (allocated on first use), the one holding the mark, and the step count
@@ -180,6 +187,10 @@ cudaError_t launch_get_particles(pic_ctx* c, double* const dst[7], int32_t* id, 
 cudaError_t launch_field_to_f64(pic_ctx* c, int which, double* dst, int64_t i0, int64_t cnt);
 cudaError_t launch_field_from_f64(pic_ctx* c, int which, const double* src, int64_t i0, int64_t cnt);
 cudaError_t launch_diagnostics(pic_ctx* c, double* d_out);
+// z filter of E, B into c->Fg (pic_set_gather_filter); nothing when off
+cudaError_t launch_filter(pic_ctx* c);
+cudaError_t configure_filter(const pic_ctx* c);
+size_t filter_smem_bytes(const pic_ctx* c);
 // nodal charge density of the current particles into rho (C doubles, zeroed first)
 cudaError_t launch_charge_density(pic_ctx* c, double* rho);
 // out[0] = max |rho1 - rho0 + dt div J| (J: the context's current), out[1] =

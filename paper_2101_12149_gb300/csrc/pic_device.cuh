@@ -178,7 +178,8 @@ __device__ __forceinline__ void staggered_weights_ec(R f, int& first, R w[P + 1]
 // ---------------------------------------------------------------------------
 template <typename R>
 __device__ __forceinline__ void boris_rotate(R k, const R B[3], R um[3], R gm) {
-    const R t0 = k * B[0] / gm, t1 = k * B[1] / gm, t2 = k * B[2] / gm;
+    const R kg = k / gm;  // one division for the three components of t
+    const R t0 = kg * B[0], t1 = kg * B[1], t2 = kg * B[2];
     const R tt = t0 * t0 + t1 * t1 + t2 * t2;
     const R sc = R(2) / (R(1) + tt);
     const R s0 = sc * t0, s1 = sc * t1, s2 = sc * t2;

@@ -594,8 +594,38 @@ __device__ __forceinline__ void first_particle(const StepArgs<R>& A, const TileW
 // stencil at once; the others go to a per-warp queue held one slot per lane
 // in registers and are deposited 32 at a time with the full window, so
 // neither kind runs with idle lanes.
+// decode_particle for a particle of tile t (origin oi, oj, ok): in FP32-mixed
+// a key inside the tile is unpacked with shifts and masks alone; a key of
+// another tile (an outsider, only between sorts) takes the full decode.
+template <typename R>
+__device__ __forceinline__ void decode_in_tile(const StepArgs<R>& A, const RawParticle<R>& r, int t, int oi, int oj,
+                                               int ok, int cell[3], R f0[3], double xg0[3], R u[3], R& wq) {
+    if constexpr (sizeof(R) == 4) {
+        const Geom& g = A.g;
+        const int kk = r.key - g.kbase;
+        const int ls = g.lT[1] + g.lT[2];
+        if ((kk >> (g.lT[0] + ls)) == t) {
+            const int l = kk & (g.cpt - 1);
+            cell[0] = oi + (l >> ls);
+            cell[1] = oj + ((l >> g.lT[2]) & (g.T[1] - 1));
+            cell[2] = ok + (l & (g.T[2] - 1));
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                f0[a] = r.a[a];
+                xg0[a] = 0.0;
+            }
+            u[0] = r.a[3];
+            u[1] = r.a[4];
+            u[2] = r.a[5];
+            wq = r.a[6];
+            return;
+        }
+    }
+    decode_particle<R>(A, r, cell, f0, xg0, u, wq);
+}
+
 template <int P, typename R, class LY>
-__device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileWork& w, int oi, int oj, int ok,
+__device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileWork& w, int t, int oi, int oj, int ok,
                                                const R* sEB, R* sJ, RawParticle<R> next) {
     const Geom& g = A.g;
     constexpr bool kFixed = sizeof(R) == 4;
@@ -619,7 +649,7 @@ __device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileW
                 int cell[3];
                 R f0[3], u[3], wq;
                 double xg0[3];
-                decode_particle<R>(A, raw, cell, f0, xg0, u, wq);
+                decode_in_tile<R>(A, raw, t, oi, oj, ok, cell, f0, xg0, u, wq);
                 const int li = cell[0] - oi, lj = cell[1] - oj, lk = cell[2] - ok;
                 // the fixed-point sums are exact for up to 65535 particles per tile
                 const bool inside = unsigned(li) < unsigned(g.T[0]) && unsigned(lj) < unsigned(g.T[1]) &&
@@ -773,7 +803,7 @@ __device__ __forceinline__ bool tile_body(const StepArgs<R>& A, const int t, uns
     __syncthreads();
     if (by_tma && threadIdx.x == 0) mbar_inval(&s_bar);  // every thread is past its wait
 
-    tile_particles<P, R, LY>(A, w, oi, oj, ok, sEB, sJ, next);
+    tile_particles<P, R, LY>(A, w, t, oi, oj, ok, sEB, sJ, next);
     __syncthreads();
     flush_tile<R, LY>(A, sJ, oi, oj, ok);
     return true;
@@ -851,7 +881,7 @@ __device__ __forceinline__ void tile_loop(const StepArgs<R>& A, int* queue, unsi
         __syncthreads();  // E/B of t staged; s_tile[1] visible
         PIC_CHECK_OR(w.beg >= 0 && w.end <= A.np, A.err, 1, ((long long)w.beg << 32) | unsigned(w.end),
                      w.wbeg = w.wend = w.beg);
-        tile_particles<P, R, LY>(A, w, oi, oj, ok, sEB, sJ, next);
+        tile_particles<P, R, LY>(A, w, t, oi, oj, ok, sEB, sJ, next);
         __syncthreads();  // every warp is done with t's E/B block and deposits
         const int tn = s_tile[1];
         int ni = 0, nj = 0, nk = 0;
@@ -1094,8 +1124,9 @@ template <typename R, int P, class LY> cudaError_t tile_step_impl(pic_ctx* c) {
     const size_t smem = LY::template smem_bytes<R>();
     // the tile queue counter sits after the outsider count (zeroed with it)
     int* queue = reinterpret_cast<int*>(c->err + 5);
+    const bool filt = c->filter_passes > 0 && c->Fg;
     k_tile_step<P, R, LY><<<unsigned(tile_grid<R, P, LY>(c)), LY::kThreads, smem, c->stream>>>(
-        A, c->tmap_eb, c->tma ? 1 : 0, queue);
+        A, filt ? c->tmap_g : c->tmap_eb, (filt ? c->tma_g : c->tma) ? 1 : 0, queue);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_outsiders<P, R><<<152 * 4, kBlock, 0, c->stream>>>(A);

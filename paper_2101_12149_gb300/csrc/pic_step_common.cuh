@@ -97,8 +97,15 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
         a.dtc[d] = R(c->dt / c->g.d[d]);
         const int t1 = (d + 1) % 3, t2 = (d + 2) % 3;
         a.jc[d] = R(-c->q / (c->dt * c->g.d[t1] * c->g.d[t2]));
-        a.E[d] = static_cast<const R*>(c->F[d]);
-        a.B[d] = static_cast<const R*>(c->F[3 + d]);
+        // with the z filter on the particles gather the filtered copy (six
+        // arrays of C values in one allocation)
+        if (c->filter_passes > 0 && c->Fg) {
+            a.E[d] = static_cast<const R*>(c->Fg) + d * c->g.C;
+            a.B[d] = static_cast<const R*>(c->Fg) + (3 + d) * c->g.C;
+        } else {
+            a.E[d] = static_cast<const R*>(c->F[d]);
+            a.B[d] = static_cast<const R*>(c->F[3 + d]);
+        }
         a.J[d] = static_cast<R*>(c->F[6 + d]);
     }
     a.dt = c->dt;

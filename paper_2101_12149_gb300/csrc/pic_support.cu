@@ -716,6 +716,67 @@ cudaError_t launch_continuity(pic_ctx* c, const double* rho0, const double* rho1
                                : continuity_impl<float>(c, rho0, rho1, out);
 }
 
+// ---------------------------------------------------------------------------
+// z filter of the fields the particles gather (the Godfrey filter of the
+// paper's plasma-acceleration run, Sec. 4.2, in its compensated binomial
+// form): npass passes of (1/4, 1/2, 1/4) along z, then one compensation pass
+// (-npass/4, 1 + npass/2, -npass/4); each pass reads the previous one's output,
+// periodic along z or zero beyond the z ends when z is open.  One CTA per z
+// column of one component, the column ping-ponging between two shared-memory
+// rows of nz values.
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_filter_z(const R* __restrict__ F, R* __restrict__ out, int64_t C, int nz,
+                                                     int npass, int zopen) {
+    extern __shared__ __align__(16) unsigned char filt_raw[];
+    R* buf = reinterpret_cast<R*>(filt_raw);  // two rows of nz values
+    const int64_t col = blockIdx.x;           // (i ny + j) of the column
+    const int comp = blockIdx.y;              // 0..5: Ex..Bz
+    const R* src = F + comp * C + col * nz;
+    R* dst = out + comp * C + col * nz;
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) buf[k] = src[k];
+    __syncthreads();
+    int cur = 0;
+    for (int pass = 0; pass <= npass; ++pass) {
+        const R a = pass < npass ? R(0.25) : R(-0.25 * npass);
+        const R b = pass < npass ? R(0.5) : R(1.0 + 0.5 * npass);
+        const R* in = buf + cur * nz;
+        R* o = buf + (1 - cur) * nz;
+        for (int k = threadIdx.x; k < nz; k += blockDim.x) {
+            const R left = k > 0 ? in[k - 1] : (zopen ? R(0) : in[nz - 1]);
+            const R right = k + 1 < nz ? in[k + 1] : (zopen ? R(0) : in[0]);
+            o[k] = a * left + b * in[k] + a * right;
+        }
+        __syncthreads();
+        cur = 1 - cur;
+    }
+    for (int k = threadIdx.x; k < nz; k += blockDim.x) dst[k] = buf[cur * nz + k];
+}
+
+size_t filter_smem_bytes(const pic_ctx* c) { return 2 * size_t(c->g.n[2]) * c->rsize; }
+
+cudaError_t configure_filter(const pic_ctx* c) {
+    const int bytes = int(filter_smem_bytes(c));
+    return c->prec == PIC_FP64
+               ? cudaFuncSetAttribute(k_filter_z<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)
+               : cudaFuncSetAttribute(k_filter_z<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+cudaError_t launch_filter(pic_ctx* c) {
+    if (c->filter_passes <= 0 || !c->Fg) return cudaSuccess;
+    const dim3 grid(unsigned(int64_t(c->g.n[0]) * c->g.n[1]), 6);
+    const size_t smem = filter_smem_bytes(c);
+    if (c->prec == PIC_FP64)
+        k_filter_z<double><<<grid, kBlock, smem, c->stream>>>(static_cast<const double*>(c->F[0]),
+                                                              static_cast<double*>(c->Fg), c->g.C, c->g.n[2],
+                                                              c->filter_passes, c->g.zopen);
+    else
+        k_filter_z<float><<<grid, kBlock, smem, c->stream>>>(static_cast<const float*>(c->F[0]),
+                                                             static_cast<float*>(c->Fg), c->g.C, c->g.n[2],
+                                                             c->filter_passes, c->g.zopen);
+    return cudaGetLastError();
+}
+
 template <typename R> cudaError_t window_shift_impl(pic_ctx* c) {
     const int64_t columns = int64_t(c->g.n[0]) * c->g.n[1];
     const dim3 grid(unsigned((columns * 32 + kBlock - 1) / kBlock), 9);

@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH):
             "pic_continuity_mark": [P],
             "pic_continuity_residual": [P, P],
             "pic_set_fp64_gamma": [P, D],
+            "pic_set_gather_filter": [P, I32],
             "pic_measure_fma_peak": [I32, ct.POINTER(D)],
             "pic_batch_init": [I32, P, P, P, D, D, I32, P, ct.POINTER(P)],
             "pic_batch_load_particles": [P, D, D, P, P, P, P, P, P, P, P, ct.c_int],
@@ -314,6 +315,10 @@ class Context:
     def set_fp64_gamma(self, gamma):
         """FP32-mixed: Lorentz factor above which the push's rotation runs in FP64 (inf: never)."""
         _check(self.lib.pic_set_fp64_gamma(self.h, float(gamma)))
+
+    def set_gather_filter(self, passes):
+        """z filter of the gathered E, B: `passes` binomial passes + one compensation pass (0: off)."""
+        _check(self.lib.pic_set_gather_filter(self.h, int(passes)))
 
     def reserve_adjoint(self, nsteps, ckpt_every=20):
         """Keep the work space of step_adjoint(nsteps, ckpt_every) (0 releases it)."""

@@ -7,7 +7,8 @@ Esirkepov's W, a flipped curl sign, a flipped current sign, momentum used as
 velocity, an energy-conserving gather that keeps order p for one component,
 a Vay pusher without its explicit magnetic half, CKC with the wrong
 transverse weights, a field energy without the cell volume, a kinetic
-energy of gamma m instead of (gamma - 1) m, a charge density without 1/dV.  Every mutant must fail at
+energy of gamma m instead of (gamma - 1) m, a charge density without 1/dV, a
+z filter whose compensation pass has the wrong sign.  Every mutant must fail at
 least one pin.
 """
 import pytest
@@ -30,6 +31,7 @@ MUTANTS = {
     12: "field energy without the cell volume",
     13: "kinetic energy gamma m in place of (gamma - 1) m",
     14: "charge density without 1/dV",
+    15: "z filter compensation with the wrong sign",
 }
 
 
