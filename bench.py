@@ -247,6 +247,85 @@ def cpu_baseline_mt(seconds_target=15.0, workload=WORKLOAD, n=(64, 64, 64)):
                       f"{os.cpu_count()} host cores"}
 
 
+def cpu_baselines_per_config():
+    """CPU timings of the oracle (1 core) and the OpenMP baseline (every host
+    core) on each workload, as stated baselines (not tuned): the 32^3 parity
+    run in full (50 steps, serial oracle); the 256^3 x 8 ppc run, 2 full-size
+    steps (OpenMP); the 128 x 128 x 1024 wakefield grid, 2 full-size steps of
+    the step itself (OpenMP, z open, no window shift); the 96-box ensemble, 5
+    steps of every box (OpenMP); the 64^3 differentiation run's forward pass,
+    200 steps with the drive (OpenMP), and the serial oracle's adjoint of 20
+    steps on its 16^3 copy.  Prints one JSON line; several minutes."""
+    from oracle import Oracle, OracleMT
+    from paper_2101_12149_gb300 import inputs
+    M = OracleMT(os.cpu_count() or 1)
+    O = Oracle()
+    res = {"host_cores": os.cpu_count(), "threads": M.nthreads}
+
+    def timed(fn, steps, N, C, what):
+        t0 = time.perf_counter()
+        fn()
+        t = time.perf_counter() - t0
+        return {"particle_steps_per_s": N * steps / t, "cell_steps_per_s": C * steps / t, "seconds": t,
+                "steps": steps, "particles": N, "what": what}
+
+    w = inputs.WORKLOADS["uniform_32"]
+    n = w["n"]
+    parts = inputs.workload_particles("uniform_32")
+    F = np.zeros((9,) + n)
+    g = O.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+    res["uniform_32"] = timed(lambda: [O.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F, 0.0, 0.0, s * dt)
+                                       for s in range(w["steps"])], w["steps"], parts["x"].size, int(np.prod(n)),
+                              "oracle, 1 core, the full 50-step run")
+    for name in ("uniform_256",):
+        w = inputs.WORKLOADS[name]
+        n = w["n"]
+        parts = inputs.workload_particles(name)
+        F = np.zeros((9,) + n)
+        g = O.grid(n)
+        dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+        res[name] = timed(lambda: [M.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F) for _ in range(2)], 2,
+                          parts["x"].size, int(np.prod(n)), f"OpenMP, {M.nthreads} threads, 2 full-size steps")
+        del parts, F
+    cfg = inputs.WAKEFIELD
+    parts = inputs.wakefield_particles(cfg)
+    F = inputs.laser_fields(cfg)
+    g = O.grid(cfg["n"], zopen=True)
+    dt = inputs.dt_from_cfl((1, 1, 1), cfg["cfl"])
+    res["wakefield"] = timed(lambda: [M.pic_step(g, cfg["order"], dt, -1.0, 1.0, parts, F) for _ in range(2)], 2,
+                             parts["x"].size, int(np.prod(cfg["n"])),
+                             f"OpenMP, {M.nthreads} threads, 2 full-size steps (z open, no window shift)")
+    del parts, F
+    boxes = inputs.ensemble_boxes()
+    _, counts, bparts = inputs.ensemble_particles(boxes)
+    bF = [np.zeros((9,) + b["n"]) for b in boxes]
+    dt = inputs.dt_from_cfl((1, 1, 1), inputs.ENSEMBLE["cfl"])
+
+    def ens():
+        for _ in range(5):
+            for b, p_, f_ in zip(boxes, bparts, bF):
+                M.pic_step(O.grid(b["n"]), b["order"], dt, -1.0, 1.0, p_, f_)
+    res["ensemble"] = timed(ens, 5, int(counts.sum()), sum(int(np.prod(b["n"])) for b in boxes),
+                            f"OpenMP, {M.nthreads} threads, 5 steps of all 96 boxes")
+    w = inputs.WORKLOADS["adjoint_64"]
+    parts = inputs.workload_particles("adjoint_64")
+    F = np.zeros((9,) + w["n"])
+    g = O.grid(w["n"])
+    dt = inputs.dt_from_cfl((1, 1, 1), w["cfl"])
+    A, kd = inputs.drive_amplitude(w["seed"]), 2 * np.pi / w["n"][0]
+    res["adjoint_64_forward"] = timed(
+        lambda: [M.pic_step(g, w["order"], dt, -1.0, 1.0, parts, F, A, kd, s * dt) for s in range(w["steps"])],
+        w["steps"], parts["x"].size, int(np.prod(w["n"])), f"OpenMP, {M.nthreads} threads, the 200-step forward run")
+    n16 = (16, 16, 16)
+    p16 = inputs.uniform_plasma(w["seed"], n16, w["ppc"], sigma_u=w["sigma_u"])
+    g16 = O.grid(n16)
+    res["adjoint_16_copy"] = timed(
+        lambda: O.pic_adjoint(g16, w["order"], dt, -1.0, 1.0, p16, np.zeros((9,) + n16), 20, A, 2 * np.pi / 16),
+        20, p16["x"].size, int(np.prod(n16)), "oracle, 1 core, forward + adjoint of 20 steps on the 16^3 copy")
+    print(json.dumps({"cpu_baselines": res}), flush=True)
+
+
 def dist_env():
     """(rank, world size, local rank) from the launcher's environment."""
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
@@ -637,9 +716,20 @@ def main():
                     help="run the same recipe on an N^3 grid instead of 256^3 (small cases for profiling)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"],
                     help="precision of the timed headline run")
+    ap.add_argument("--sort-every", type=int, default=1, help="sort cadence of the timed run")
     ap.add_argument("--workload", default=WORKLOAD, choices=["uniform_256", "uniform_256_o1"],
                     help="recipe of the timed run (uniform_256: order 3, 8 ppc; uniform_256_o1: order 1, 2 ppc)")
+    ap.add_argument("--cpu-baselines", action="store_true",
+                    help="time the oracle and the OpenMP baseline on every workload (CPU only, several minutes)")
     args = ap.parse_args()
+    if args.cpu_baselines:
+        from oracle import build as obuild
+        from paper_2101_12149_gb300.inputs import build as ibuild
+        obuild.build()
+        obuild.build_mt()
+        ibuild()
+        cpu_baselines_per_config()
+        return
     if args.impl == "reference":
         run_reference(args)
         return
@@ -671,8 +761,8 @@ def main():
 
     stream = torch.cuda.Stream()
 
-    def make_ctx(prec):
-        ctx = pic.Context(n, cfl=w["cfl"], order=order, precision=prec, stream=stream)
+    def make_ctx(prec, sort_every=1):
+        ctx = pic.Context(n, cfl=w["cfl"], order=order, precision=prec, stream=stream, sort_every=sort_every)
         dev = {k: torch.from_numpy(v).to(f"cuda:{local}", non_blocking=False) for k, v in host.items()}
         ctx.load_particles(-1.0, 1.0, dev)
         del dev
@@ -681,7 +771,7 @@ def main():
 
     # ---- headline: FP32-mixed, device-resident inputs ---------------------
     head_prec = pic.FP32_MIXED if args.precision == "fp32" else pic.FP64
-    ctx = make_ctx(head_prec)
+    ctx = make_ctx(head_prec, args.sort_every)
     ctx.step(args.warmup)
     l0 = ctx.launch_count()
     uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid) if hasattr(
@@ -742,7 +832,7 @@ def main():
         "vs_baseline": None, "dtype": "f32-mixed" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": {"workload": args.workload if not args.grid else f"{args.workload} recipe at {args.grid}^3",
                    "grid": f"{n[0]}^3", "ppc": ppc, "particles": N, "order": order,
-                   "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": 1,
+                   "sigma_u": w["sigma_u"], "cfl": w["cfl"], "sort_every": args.sort_every,
                    "precision": "fp32_mixed" if args.precision == "fp32" else "fp64",
                    "l2": f"inputs larger than L2 ({N * 36 / 1e9:.1f} GB of particle state per step)",
                    "parallelism": f"replicas x{world}"},

