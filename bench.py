@@ -475,6 +475,7 @@ def hbm_leg_statement(torch, stream, peaks, steps=20, warmup=3):
             "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in tm.items()},
             "roofline": {"bound": "hbm", "kernel": "k_tile_step", "achieved": tile_gbs, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": tile_gbs / peaks["hbm_gbs"],
+                         "traffic": profiled_traffic("k_tile_step", "fp32", "uniform_256_o1"),
                          "bytes": "60 B a particle + 36 B a cell per launch"},
             "step_roofline": {"achieved": step_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": step_gbs / peaks["hbm_gbs"],
