@@ -178,6 +178,7 @@ cudaError_t launch_gather_push_global(pic_ctx* c);
 cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);
 cudaError_t launch_yee_e(pic_ctx* c);
+
 cudaError_t launch_step_counter(pic_ctx* c);
 // particles [base, base + n) from arrays that start at particle base
 cudaError_t launch_load_particles(pic_ctx* c, const double* const src[7], int64_t n, int64_t base = 0);

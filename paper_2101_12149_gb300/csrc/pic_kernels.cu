@@ -5,8 +5,8 @@
 //                     shared memory, J accumulated in shared memory, one
 //                     vectorised atomic flush per tile (Sec. 3.1 fuses gather
 //                     and push; Sec. 3.4 discusses shared-memory buffers).
-//  k_tile_step_batch  the same tile body for (box, tile) items of a batch of
-//                     boxes, pulled from a queue by a persistent grid.
+//  k_tile_step_batch  the same pipelined tile loop over (box, tile) items of a
+//                     batch of boxes, pulled from a queue by a persistent grid.
 //  k_outsiders        particles outside their tile (between sorts): global
 //                     gather and global atomics.
 //  k_gather_push      one particle per thread, fields read from global memory.
@@ -755,60 +755,6 @@ __device__ __forceinline__ void stage_all(const StepArgs<R>& A, R* sEB, int oi, 
         stage_box<R, LY>(A, sEB, oi, oj, ok, 0, ex, 0, ey, 0, ez);
 }
 
-// One tile t of the box described by A, by the whole CTA (the batch kernel);
-// `smem_raw` is the CTA's dynamic shared memory, whose J box is zero on entry
-// and is left zero; `tmap` the TMA descriptor of the box's E/B (null: staged
-// by loads).  Returns with the block converged; false if a TMA wait ran out
-// (the error word is set; the CTA must not use its shared memory again).
-template <int P, typename R, class LY>
-__device__ __forceinline__ bool tile_body(const StepArgs<R>& A, const int t, unsigned char* smem_raw,
-                                          const CUtensorMap* tmap = nullptr) {
-    R* sm = reinterpret_cast<R*>(smem_raw);
-    const Geom& g = A.g;
-    constexpr int kZShift = tma_layout<LY, R>() ? 4 - LY::H : 0;
-    R* sEB = sm + kZShift;        // 6 * eVol (addressed kZShift elements into the block)
-    R* sJ = sm + 6 * LY::eVol;    // FP64: 3 * jVol doubles; FP32-mixed: 6 * jVol int32 (lo, hi per component)
-
-    TileWork w;
-    plan_tile<R>(A, t, w);
-    if (w.end <= w.beg) return true;
-    PIC_CHECK_OR(w.beg >= 0 && w.end <= A.np, A.err, 1, ((long long)w.beg << 32) | unsigned(w.end), return true);
-    int oi, oj, ok;
-    tile_origin(g, t, oi, oj, ok);
-    RawParticle<R> next;
-    first_particle<R>(A, w, next);
-
-    // stage E, B of the tile and its halo (wrapped)
-    __shared__ __align__(8) unsigned long long s_bar;
-    const bool by_tma = tile_uses_tma<R, LY>(tmap, sm, ok);
-    if (by_tma) {
-        if (threadIdx.x == 0) mbar_init(&s_bar);
-        __syncthreads();
-        if (threadIdx.x == 0)
-            tma_load_eb(tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 4, oj - LY::H, oi - LY::H);
-        // every thread waits for the copy; if it did not land in time, all
-        // wait once more (it is still writing into this CTA's shared memory)
-        // and the caller stops using the block
-        const bool late = __syncthreads_or(!mbar_wait(&s_bar, 0u, kTmaSpinLimit));
-        if (late) {
-            if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
-            mbar_wait(&s_bar, 0u, kTmaSpinLimit);
-            __syncthreads();
-            return false;
-        }
-        restage_wrapped<R, LY>(A, sEB, oi, oj, ok);
-    } else {
-        stage_all<R, LY>(A, sEB, oi, oj, ok);
-    }
-    __syncthreads();
-    if (by_tma && threadIdx.x == 0) mbar_inval(&s_bar);  // every thread is past its wait
-
-    tile_particles<P, R, LY>(A, w, t, oi, oj, ok, sEB, sJ, next);
-    __syncthreads();
-    flush_tile<R, LY>(A, sJ, oi, oj, ok);
-    return true;
-}
-
 // Next tile with particles from the queue (one thread), or -1 when none is left.
 __device__ __forceinline__ int next_tile(const int* __restrict__ offsets, int cpt, int ntiles, int* queue) {
     for (;;) {
@@ -913,32 +859,117 @@ __global__ void __launch_bounds__(LY::kThreads, LY::kMinBlocks)
     tile_loop<P, R, LY>(A, queue, smem_raw, use_tma ? &tmap : nullptr);
 }
 
-// Batch of boxes: a persistent grid pulls (box, tile) items from a queue
-// counter (zeroed before the launch); each item's box arguments are copied
-// into shared memory first.  Items are ordered heaviest first.
+// Next (box, tile) work item with particles from the queue (one thread), or
+// -1 when none is left.
+template <typename R>
+__device__ __forceinline__ int next_item(const StepArgs<R>* __restrict__ boxes, const int2* __restrict__ items,
+                                         int nitems, int* queue) {
+    for (;;) {
+        const int it = atomicAdd(queue, 1);
+        if (it >= nitems) return -1;
+        const int2 bt = items[it];
+        const StepArgs<R>& B = boxes[bt.x];
+        const int cpt = B.g.cpt;
+        if (B.offsets[(int64_t)(bt.y + 1) * cpt] > B.offsets[(int64_t)bt.y * cpt]) return it;
+    }
+}
+
+// A box's arguments into a shared-memory slot (all threads).
+template <typename R> __device__ __forceinline__ void copy_args(const StepArgs<R>* src, StepArgs<R>* dst) {
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    for (int w = threadIdx.x; w < int(sizeof(StepArgs<R>) / 4); w += blockDim.x) d[w] = s[w];
+}
+
+// Batch of boxes: a persistent grid pulls (box, tile) items, heaviest first,
+// from a queue counter (zeroed before the launch) and pipelines them as
+// tile_loop does; the box arguments of the current and the next item sit in
+// two shared-memory slots, the next item's copied while the current one's
+// current is flushed.
 template <int P, typename R, class LY>
 __global__ void __launch_bounds__(LY::kThreads, LY::kMinBlocks)
     k_tile_step_batch(const StepArgs<R>* __restrict__ boxes, const int2* __restrict__ items, int nitems, int* queue) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(16) StepArgs<R> sA;
-    __shared__ int s_item;
-    zero_jbox<R, LY>(reinterpret_cast<R*>(smem_raw) + 6 * LY::eVol);
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(queue, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= nitems) break;
-        const int2 bt = items[it];
-        {
-            const int* src = reinterpret_cast<const int*>(boxes + bt.x);
-            int* dst = reinterpret_cast<int*>(&sA);
-            for (int w = threadIdx.x; w < int(sizeof(StepArgs<R>) / 4); w += blockDim.x) dst[w] = src[w];
-        }
-        __syncthreads();
-        const bool ok = tile_body<P, R, LY>(sA, bt.y, smem_raw, sA.tmap);
-        __syncthreads();
-        if (!ok) break;  // a TMA copy may still be landing in this CTA's block
+    __shared__ __align__(16) StepArgs<R> sA[2];
+    __shared__ __align__(8) unsigned long long s_bar;
+    __shared__ int s_item[2];
+    R* sm = reinterpret_cast<R*>(smem_raw);
+    constexpr int kZShift = tma_layout<LY, R>() ? 4 - LY::H : 0;
+    R* sEB = sm + kZShift;
+    R* sJ = sm + 6 * LY::eVol;
+
+    zero_jbox<R, LY>(sJ);
+    if (threadIdx.x == 0) {
+        mbar_init(&s_bar);
+        s_item[0] = next_item<R>(boxes, items, nitems, queue);
     }
+    __syncthreads();
+    int it = s_item[0];
+    if (it < 0) {
+        if (threadIdx.x == 0) mbar_inval(&s_bar);
+        return;
+    }
+    int slot = 0;
+    copy_args<R>(boxes + items[it].x, &sA[0]);
+    __syncthreads();
+    int t = items[it].y;
+    int oi, oj, ok;
+    tile_origin(sA[0].g, t, oi, oj, ok);
+    TileWork w;
+    plan_tile<R>(sA[0], t, w);
+    RawParticle<R> next;
+    first_particle<R>(sA[0], w, next);
+    bool by_tma = tile_uses_tma<R, LY>(sA[0].tmap, sm, ok);
+    if (by_tma) {
+        if (threadIdx.x == 0)
+            tma_load_eb(sA[0].tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), ok - 4, oj - LY::H, oi - LY::H);
+    } else {
+        stage_all<R, LY>(sA[0], sEB, oi, oj, ok);
+    }
+    unsigned phase = 0;
+    for (;;) {
+        const StepArgs<R>& A = sA[slot];
+        if (threadIdx.x == 0) s_item[1] = next_item<R>(boxes, items, nitems, queue);
+        if (by_tma) {
+            const bool late = __syncthreads_or(!mbar_wait(&s_bar, phase, kTmaSpinLimit));
+            if (late) {  // as in tile_loop: the CTA stops
+                if (threadIdx.x == 0) raise_error(A.err, ERRBIT_TIMEOUT);
+                mbar_wait(&s_bar, phase, kTmaSpinLimit);
+                __syncthreads();
+                return;
+            }
+            phase ^= 1u;
+            restage_wrapped<R, LY>(A, sEB, oi, oj, ok);
+        }
+        __syncthreads();  // E/B of t staged; s_item[1] visible
+        tile_particles<P, R, LY>(A, w, t, oi, oj, ok, sEB, sJ, next);
+        __syncthreads();  // every warp is done with t's block and deposits
+        const int itn = s_item[1];
+        int tn = -1, ni = 0, nj = 0, nk = 0;
+        bool tma_n = false;
+        if (itn >= 0) {
+            const int2 bt = items[itn];
+            const StepArgs<R>& An = boxes[bt.x];  // read from global until its slot is filled
+            tn = bt.y;
+            tile_origin(An.g, tn, ni, nj, nk);
+            tma_n = tile_uses_tma<R, LY>(An.tmap, sm, nk);
+            if (tma_n && threadIdx.x == 0)
+                tma_load_eb(An.tmap, sm, &s_bar, unsigned(6 * LY::eVol * sizeof(R)), nk - 4, nj - LY::H, ni - LY::H);
+            plan_tile<R>(An, tn, w);
+            first_particle<R>(An, w, next);
+            copy_args<R>(boxes + bt.x, &sA[1 - slot]);
+        }
+        flush_tile<R, LY>(A, sJ, oi, oj, ok);
+        if (itn >= 0 && !tma_n) stage_all<R, LY>(boxes[items[itn].x], sEB, ni, nj, nk);
+        if (itn < 0) break;
+        __syncthreads();  // J box clear, next slot filled, a load-staged block complete
+        slot = 1 - slot;
+        t = tn;
+        oi = ni, oj = nj, ok = nk;
+        by_tma = tma_n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_inval(&s_bar);
 }
 
 // One particle the tile kernel listed as outside its tile: gather from global

@@ -20,11 +20,10 @@ static inline unsigned blocks_for(int64_t n) { return unsigned((n + kBlock - 1) 
 // Yee FDTD
 // ---------------------------------------------------------------------------
 
-// B <- B - h curl E (forward differences: B sits half a cell above E), at cell c.
-template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>& Y, const int64_t c) {
-    const int k = int(c % Y.n[2]);
-    const int j = int((c / Y.n[2]) % Y.n[1]);
-    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+// B <- B - h curl E (forward differences: B sits half a cell above E), at
+// cell (i, j, k) = c.
+template <typename R>
+__device__ __forceinline__ void yee_b_ijk(const YeeArgs<R>& Y, const int64_t c, const int i, const int j, const int k) {
     const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
     const int64_t ip = c + (i + 1 == Y.n[0] ? -(int64_t)(Y.n[0] - 1) * sx : sx);
     const int64_t jp = c + (j + 1 == Y.n[1] ? -(int64_t)(Y.n[1] - 1) * sy : sy);
@@ -40,6 +39,19 @@ template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>&
     Y.B[0][c] -= Y.h * (dEz_dy - dEy_dz);
     Y.B[1][c] -= Y.h * (dEx_dz - dEz_dx);
     Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
+}
+
+// The cell's indices from its linear index (the batch kernels' one-dimensional blocks).
+template <typename R> __device__ __forceinline__ void cell_ijk(const YeeArgs<R>& Y, int64_t c, int& i, int& j, int& k) {
+    k = int(c % Y.n[2]);
+    j = int((c / Y.n[2]) % Y.n[1]);
+    i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+}
+
+template <typename R> __device__ __forceinline__ void yee_b_at(const YeeArgs<R>& Y, const int64_t c) {
+    int i, j, k;
+    cell_ijk(Y, c, i, j, k);
+    yee_b_ijk(Y, c, i, j, k);
 }
 
 // CKC (Cole-Karkkainen, the solver named for the plasma-acceleration run,
@@ -69,10 +81,9 @@ __device__ __forceinline__ R ckc_diff(const R* __restrict__ F, int axis, const i
     return acc * inv;
 }
 
-template <typename R> __device__ __forceinline__ void yee_b_ckc_at(const YeeArgs<R>& Y, const int64_t c) {
-    const int k = int(c % Y.n[2]);
-    const int j = int((c / Y.n[2]) % Y.n[1]);
-    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+template <typename R>
+__device__ __forceinline__ void yee_b_ckc_ijk(const YeeArgs<R>& Y, const int64_t c, const int i, const int j,
+                                              const int k) {
     const int cc[3] = {i, j, k};
     const int64_t st[3] = {(int64_t)Y.n[1] * Y.n[2], Y.n[2], 1};
     int64_t off[3][4];
@@ -96,11 +107,9 @@ template <typename R> __device__ __forceinline__ void yee_b_ckc_at(const YeeArgs
     Y.B[2][c] -= Y.h * (dEy_dx - dEx_dy);
 }
 
-// E <- E + dt (curl B - J) (backward differences), at cell c.
-template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>& Y, const int64_t c) {
-    const int k = int(c % Y.n[2]);
-    const int j = int((c / Y.n[2]) % Y.n[1]);
-    const int i = int(c / ((int64_t)Y.n[1] * Y.n[2]));
+// E <- E + dt (curl B - J) (backward differences), at cell (i, j, k) = c.
+template <typename R>
+__device__ __forceinline__ void yee_e_ijk(const YeeArgs<R>& Y, const int64_t c, const int i, const int j, const int k) {
     const int64_t sx = (int64_t)Y.n[1] * Y.n[2], sy = Y.n[2];
     const int64_t im = c - (i == 0 ? -(int64_t)(Y.n[0] - 1) * sx : sx);
     const int64_t jm = c - (j == 0 ? -(int64_t)(Y.n[1] - 1) * sy : sy);
@@ -118,26 +127,47 @@ template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>&
     Y.E[2][c] += Y.h * ((dBy_dx - dBx_dy) - Y.J[2][c]);
 }
 
+template <typename R> __device__ __forceinline__ void yee_e_at(const YeeArgs<R>& Y, const int64_t c) {
+    int i, j, k;
+    cell_ijk(Y, c, i, j, k);
+    yee_e_ijk(Y, c, i, j, k);
+}
+
+// Single-box grids: block x is a z-row (i, j) of the grid, block y a chunk of
+// kBlock cells along it, so no thread divides a 64-bit cell index.
+struct RowCell {
+    int i, j, k;
+    int64_t c;
+    bool ok;
+};
+template <typename R> __device__ __forceinline__ RowCell row_cell(const YeeArgs<R>& Y) {
+    RowCell r;
+    const int row = int(blockIdx.x);
+    r.i = row / Y.n[1];
+    r.j = row - r.i * Y.n[1];
+    r.k = int(blockIdx.y) * blockDim.x + threadIdx.x;
+    r.ok = r.k < Y.n[2];
+    r.c = (int64_t)row * Y.n[2] + r.k;
+    return r;
+}
+
 template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_b(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (Y.step && c == 0) *Y.step += 1;
-    if (c < C) yee_b_at(Y, c);
+    const RowCell r = row_cell(Y);
+    if (Y.step && r.c == 0) *Y.step += 1;
+    if (r.ok) yee_b_ijk(Y, r.c, r.i, r.j, r.k);
 }
 
 // The B half step with the CKC stencil (a kernel of its own: its register
 // needs must not lower the occupancy of the plain Yee update).
 template <typename R> __global__ void __launch_bounds__(kBlock, 3) k_yee_b_ckc(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (Y.step && c == 0) *Y.step += 1;
-    if (c < C) yee_b_ckc_at(Y, c);
+    const RowCell r = row_cell(Y);
+    if (Y.step && r.c == 0) *Y.step += 1;
+    if (r.ok) yee_b_ckc_ijk(Y, r.c, r.i, r.j, r.k);
 }
 
 template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<R> Y) {
-    const int64_t C = (int64_t)Y.n[0] * Y.n[1] * Y.n[2];
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c < C) yee_e_at(Y, c);
+    const RowCell r = row_cell(Y);
+    if (r.ok) yee_e_ijk(Y, r.c, r.i, r.j, r.k);
 }
 
 // Batch of boxes: block b updates cells [blocks[b].y, blocks[b].y + blocks[b].z)
@@ -481,15 +511,20 @@ cudaError_t launch_rekey(int* key, int64_t n, const Geom& from, const Geom& to, 
     return cudaGetLastError();
 }
 
+// z-rows x chunks of kBlock cells along z
+static dim3 yee_grid(const pic_ctx* c) {
+    return dim3(unsigned(int64_t(c->g.n[0]) * c->g.n[1]), unsigned((c->g.n[2] + kBlock - 1) / kBlock));
+}
+
 cudaError_t launch_yee_b(pic_ctx* c, double h) {
     if (c->prec == PIC_FP64) {
         auto Y = make_yee<double>(c, h);
-        if (c->solver) k_yee_b_ckc<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-        else k_yee_b<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        if (c->solver) k_yee_b_ckc<double><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
+        else k_yee_b<double><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
     } else {
         auto Y = make_yee<float>(c, h);
-        if (c->solver) k_yee_b_ckc<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
-        else k_yee_b<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        if (c->solver) k_yee_b_ckc<float><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
+        else k_yee_b<float><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
     }
     return cudaGetLastError();
 }
@@ -497,10 +532,10 @@ cudaError_t launch_yee_b(pic_ctx* c, double h) {
 cudaError_t launch_yee_e(pic_ctx* c) {
     if (c->prec == PIC_FP64) {
         auto Y = make_yee<double>(c, c->dt);
-        k_yee_e<double><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        k_yee_e<double><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
     } else {
         auto Y = make_yee<float>(c, c->dt);
-        k_yee_e<float><<<blocks_for(c->g.C), kBlock, 0, c->stream>>>(Y);
+        k_yee_e<float><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
     }
     return cudaGetLastError();
 }

@@ -242,3 +242,30 @@ def test_tiles_of_two_z_cells_mix_tma_and_loads(precision):
         assert max(e.values()) < 1e-12, e
     else:
         assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
+
+
+@pytest.mark.parametrize("precision,tol", [(pic.FP64, 1e-14), (pic.FP32_MIXED, 1e-6)])
+@pytest.mark.parametrize("n,zopen", [((12, 20, 96), False), ((9, 17, 70), False), ((8, 8, 64), True),
+                                     ((128, 128, 128), False)])
+def test_field_update_against_oracle(precision, tol, n, zopen):
+    """The field update alone (pic_yee_step: B half step, E step with J, B half
+    step) on random E, B, J against the oracle's Yee step: odd extents, open z
+    ends, and a grid of 2M cells, far more blocks than fit on the GPU at once
+    (an update that read neighbours already overwritten by other blocks would
+    show there); ten steps."""
+    from oracle import Oracle
+    F = inputs.random_fields(90 + n[0], n, 0.5)
+    kw = {"window_speed": 0.0} if zopen else {}
+    with pic.Context(n, cfl=0.99, order=1, precision=precision, **kw) as c:
+        c.set_fields(F)
+        for _ in range(10):
+            c.yee_step()
+        G = c.get_fields()
+    O = Oracle()
+    g = O.grid(n, zopen=zopen)
+    dt = inputs.dt_from_cfl((1.0, 1.0, 1.0), 0.99)
+    R = F.copy()
+    for _ in range(10):
+        O.yee_step(g, dt, R)
+    err = rel_l2(G[:6], R[:6])
+    assert err < tol, err
