@@ -385,8 +385,13 @@ template <typename R, int P> cudaError_t adj_particles_impl(pic_ctx* c, const Ad
                                                            double t) {
     StepArgs<R> A = make_args<R>(c);
     // the stored state replaces the live particles and fields
-    for (int i = 0; i < 7; ++i) A.pa[i] = static_cast<R*>(s.a[i]);
+    for (int i = 0; i < 7; ++i) {
+        A.pa[i] = static_cast<R*>(s.a[i]);
+        A.spa[i] = A.pa[i];
+    }
     A.key = s.key;
+    A.skey = s.key;
+    A.sid = A.did = s.id;
     for (int d = 0; d < 3; ++d) {
         A.E[d] = static_cast<const R*>(s.F[d]);
         A.B[d] = static_cast<const R*>(s.F[3 + d]);

@@ -54,6 +54,9 @@ void free_particles(pic_ctx* c) {
     c->sortbin = nullptr;
     cudaFree(c->outl);
     c->outl = nullptr;
+    cudaFree(c->perm);
+    c->perm = nullptr;
+    c->tile_perm = false;
     c->np = c->cap = 0;
     c->have_old = false;
 }
@@ -90,6 +93,8 @@ cudaError_t alloc_particles(pic_ctx* c, int64_t n) {
         c->P[b].id = reinterpret_cast<int*>(base + 7 * per + ints);
     }
     cudaError_t e = cudaMalloc(&c->outl, ints);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&c->perm, ints);
     if (e != cudaSuccess) return e;
     c->cap = int64_t(cap);
     return cudaSuccess;
@@ -130,6 +135,7 @@ cudaError_t grow_particles(pic_ctx* c, int64_t need) {
     c->cap = fresh.cap;
     c->np = np;
     c->cur = 0;
+    c->perm = fresh.perm;
     return cudaSuccess;
 }
 
@@ -245,12 +251,23 @@ cudaError_t run_yee(pic_ctx* c) {
     return counted(c, "k_step_counter", 1, pic::launch_step_counter);
 }
 
-// One full step as queued work.  `with_sort` runs the counting sort first.
+// One full step as queued work.  `with_sort` runs the counting sort first, as
+// a permutation: histogram, scan, then the slots as perm; the tile kernel
+// moves each particle from the other buffer into its sorted slot of the
+// current one while it pushes it (the data moves once a step).
 cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
     cudaError_t e;
-    if (with_sort && (e = run_sort(c)) != cudaSuccess) return e;
+    if (with_sort) {
+        if ((e = counted(c, "k_hist", 1, pic::launch_hist)) != cudaSuccess) return e;
+        if ((e = counted(c, "k_scan", 1, pic::launch_scan)) != cudaSuccess) return e;
+        if ((e = counted(c, "k_scatter_perm", 1, pic::launch_scatter_perm)) != cudaSuccess) return e;
+        c->cur = 1 - c->cur;
+        c->tile_perm = c->np > 0;
+    }
     if (c->filter_passes > 0 && (e = counted(c, "k_filter_z", 1, pic::launch_filter)) != cudaSuccess) return e;
-    if ((e = counted(c, "k_tile_step", 2, pic::launch_tile_step)) != cudaSuccess) return e;
+    e = counted(c, "k_tile_step", 2, pic::launch_tile_step);
+    c->tile_perm = false;
+    if (e != cudaSuccess) return e;
     return run_yee(c);
 }
 

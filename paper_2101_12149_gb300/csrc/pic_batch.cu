@@ -170,8 +170,13 @@ template <typename R> void fill_args(const pic_batch* b, std::vector<char>& host
             v.cur = r;
             pic::StepArgs<R> A = pic::make_args<R>(&v);
             // the tile kernel indexes particles globally (offsets of the pooled sort)
-            for (int a = 0; a < 7; ++a) A.pa[a] = static_cast<R*>(P.P[r].a[a]);
+            for (int a = 0; a < 7; ++a) {
+                A.pa[a] = static_cast<R*>(P.P[r].a[a]);
+                A.spa[a] = A.pa[a];
+            }
             A.key = P.P[r].key;
+            A.skey = A.key;  // in place: the source is the pooled buffer itself
+            A.sid = A.did = P.P[r].id;
             A.offsets = P.offsets + b->box[i].cbase;
             A.np = P.np;
             A.run = b->tune.run;

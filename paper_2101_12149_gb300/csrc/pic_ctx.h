@@ -82,6 +82,8 @@ struct pic_ctx {
     bool have_old = false;
 
     int* outl = nullptr;     // outsider list of the tile kernel [cap]
+    int* perm = nullptr;     // the step's sort order [cap] (k_scatter_perm)
+    bool tile_perm = false;  // the next tile kernel reads the other buffer through perm
     int layout = 0;          // shared-memory layout of the tile kernel: 0 = up to 8x8x8, 1 = 4x4x32,
                              // 2 = 4x4x32 with a halo of 1 (FP32-mixed, order 1)
     int sms = 1;             // streaming multiprocessors of the device (persistent grids)
@@ -311,6 +313,8 @@ cudaError_t configure_batch_kernels();
 cudaError_t launch_hist(pic_ctx* c);
 cudaError_t launch_scan(pic_ctx* c);
 cudaError_t launch_scatter(pic_ctx* c);
+// the step's sort as a permutation (perm), the particle data left in place
+cudaError_t launch_scatter_perm(pic_ctx* c);
 size_t scan_status_words(int64_t C);
 
 }  // namespace pic

@@ -658,6 +658,7 @@ __device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileW
                     const int slot = atomicAdd(A.outn, 1);
                     A.outl[slot] = p;
                 } else {
+                    if (A.perm) A.did[p] = raw.id;
                     R EB[6];
                     {
                         GatherW<P, R> G;
@@ -678,6 +679,7 @@ __device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileW
                     push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
                     if (!mv.ok) {
                         raise_error(A.err, ERRBIT_PARTICLE);
+                        keep_particle<R>(A, p, raw);
                     } else {
                         store_particle<R>(A, p, cell, mv);
                         EsirkAxis<P, R> ax[3];
@@ -979,7 +981,10 @@ __device__ __forceinline__ void outsider_body(const StepArgs<R>& A, const int p)
     int cell[3];
     R f0[3], u[3], wq;
     double xg0[3];
-    load_particle<R>(A, p, cell, f0, xg0, u, wq);
+    RawParticle<R> raw;
+    load_raw<R>(A, p, raw);
+    decode_particle<R>(A, raw, cell, f0, xg0, u, wq);
+    if (A.perm) A.did[p] = raw.id;
     R EB[6];
     {
         GatherW<P, R> G;
@@ -992,6 +997,7 @@ __device__ __forceinline__ void outsider_body(const StepArgs<R>& A, const int p)
     push_particle<P, R>(A, EB, cell, f0, xg0, u, mv);
     if (!mv.ok) {
         raise_error(A.err, ERRBIT_PARTICLE);
+        keep_particle<R>(A, p, raw);
         return;
     }
     EsirkAxis<P, R> ax[3];
@@ -1151,7 +1157,9 @@ template <typename R, int P, class LY> int tile_grid(const pic_ctx* c) {
 }
 
 template <typename R, int P, class LY> cudaError_t tile_step_impl(pic_ctx* c) {
-    StepArgs<R> A = make_args<R>(c);
+    // after a permutation sort the kernel moves the particles from the other
+    // buffer into the current one in sorted order (the step's sort handed over)
+    StepArgs<R> A = c->tile_perm ? make_args_perm<R>(c, 1 - c->cur, c->cur, c->perm) : make_args<R>(c);
     const size_t smem = LY::template smem_bytes<R>();
     // the tile queue counter sits after the outsider count (zeroed with it)
     int* queue = reinterpret_cast<int*>(c->err + 5);

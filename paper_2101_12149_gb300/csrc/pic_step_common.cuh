@@ -87,6 +87,15 @@ template <typename R> struct StepArgs {
     int64_t np;
     const CUtensorMap* tmap;  // batch of boxes: the box's E/B TMA descriptor in global memory, or null
     float g2_fp64;            // FP32-mixed: gamma^2 above which the push's rotation runs in FP64
+    // Sorted-order step: the tile kernel reads the particle perm[s] of the
+    // source buffer (spa, skey, sid) and writes it to slot s of the current
+    // buffer (pa, key, did).  perm == nullptr: in place (the source is the
+    // current buffer).
+    const int* perm;
+    const R* spa[7];
+    const int* skey;
+    const int* sid;
+    int* did;
 };
 
 template <typename R> StepArgs<R> make_args(pic_ctx* c) {
@@ -142,6 +151,29 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.np = c->np;
     a.tmap = nullptr;
     a.g2_fp64 = std::isfinite(c->gamma_fp64) ? float(c->gamma_fp64 * c->gamma_fp64) : INFINITY;
+    a.perm = nullptr;
+    for (int i = 0; i < 7; ++i) a.spa[i] = a.pa[i];
+    a.skey = a.key;
+    a.sid = P.id;
+    a.did = P.id;
+    return a;
+}
+
+// Arguments of a sorted-order step: the particles come from buffer `src` in
+// the order perm gives and go to buffer `dst`.
+template <typename R> StepArgs<R> make_args_perm(pic_ctx* c, int src, int dst, const int* perm) {
+    StepArgs<R> a = make_args<R>(c);
+    const PartBuf& S = c->P[src];
+    const PartBuf& D = c->P[dst];
+    for (int i = 0; i < 7; ++i) {
+        a.spa[i] = static_cast<const R*>(S.a[i]);
+        a.pa[i] = static_cast<R*>(D.a[i]);
+    }
+    a.skey = S.key;
+    a.sid = S.id;
+    a.key = D.key;
+    a.did = D.id;
+    a.perm = perm;
     return a;
 }
 
@@ -453,13 +485,28 @@ __device__ __forceinline__ void load_particle(const StepArgs<R>& A, int p, int c
 // kernel can issue the next particle's loads before it works on the current one.
 template <typename R> struct RawParticle {
     int key;
+    int id;  // sorted-order step only
     R a[7];
 };
 
-template <typename R> __device__ __forceinline__ void load_raw(const StepArgs<R>& A, int p, RawParticle<R>& r) {
-    r.key = sizeof(R) == 8 ? 0 : A.key[p];
+// Particle in slot s of the step's order: slot s of the current buffer, or
+// particle perm[s] of the source buffer in a sorted-order step.
+template <typename R> __device__ __forceinline__ void load_raw(const StepArgs<R>& A, int s, RawParticle<R>& r) {
+    const int p = A.perm ? A.perm[s] : s;
+    r.key = (sizeof(R) == 4 || A.perm) ? A.skey[p] : 0;
+    r.id = A.perm ? A.sid[p] : 0;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) r.a[i] = A.pa[i][p];
+    for (int i = 0; i < 7; ++i) r.a[i] = A.spa[i][p];
+}
+
+// A particle written back unchanged (a rejected move) into slot s: only a
+// sorted-order step has to copy it, in place it is already there.
+template <typename R> __device__ __forceinline__ void keep_particle(const StepArgs<R>& A, int s, const RawParticle<R>& r) {
+    if (!A.perm) return;
+#pragma unroll
+    for (int i = 0; i < 7; ++i) A.pa[i][s] = r.a[i];
+    A.key[s] = r.key;
+    A.did[s] = r.id;
 }
 
 // load_particle on data already loaded.
