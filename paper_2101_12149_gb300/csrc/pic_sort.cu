@@ -88,14 +88,28 @@ __global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ cou
     if (chunk >= nchunks) return;
     const int64_t base = (int64_t)chunk * kScanChunk + (int64_t)tid * kScanItems;
 
+    // a thread's kScanItems consecutive counts: four 16-byte loads when the
+    // group lies inside [0, C) and the arrays are 16-byte aligned (always for
+    // the library's own arrays), else one count at a time
+    const bool vec = base + kScanItems <= C &&
+                     ((reinterpret_cast<uintptr_t>(count) | reinterpret_cast<uintptr_t>(offsets)) & 15) == 0;
     int v[kScanItems];
     int tsum = 0;
+    if (vec) {
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const int64_t idx = base + i;
-        v[i] = idx < C ? count[idx] : 0;
-        tsum += v[i];
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const int4 c4 = reinterpret_cast<const int4*>(count + base)[q];
+            v[4 * q] = c4.x, v[4 * q + 1] = c4.y, v[4 * q + 2] = c4.z, v[4 * q + 3] = c4.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t idx = base + i;
+            v[i] = idx < C ? count[idx] : 0;
+        }
     }
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) tsum += v[i];
     // block exclusive scan of the per-thread sums
     int incl = tsum;
 #pragma unroll
@@ -163,11 +177,24 @@ __global__ void __launch_bounds__(kSortBlock) k_scan(const int* __restrict__ cou
     __syncthreads();
     int run = s_prefix + s_warp[warp] + (incl - tsum);
     PIC_CHECK_OR(run >= 0, err, 7, run, run = 0);
+    if (vec) {
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        const int64_t idx = base + i;
-        if (idx < C) offsets[idx] = run;
-        run += v[i];
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            int4 o;
+            o.x = run;
+            o.y = o.x + v[4 * q];
+            o.z = o.y + v[4 * q + 1];
+            o.w = o.z + v[4 * q + 2];
+            run = o.w + v[4 * q + 3];
+            reinterpret_cast<int4*>(offsets + base)[q] = o;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) {
+            const int64_t idx = base + i;
+            if (idx < C) offsets[idx] = run;
+            run += v[i];
+        }
     }
 }
 
@@ -211,6 +238,37 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = v[i];
     dst.key[dest] = key;
     dst.id[dest] = id;
+}
+
+// The step's sort without moving the particle data: perm[slot] = the index
+// of the particle that goes there (slots as k_scatter assigns them); the tile
+// kernel then reads each particle through perm and writes it in sorted order
+// into the other buffer, so the data moves once a step instead of twice.
+__global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restrict__ bin, int64_t np,
+                                                             const int* offsets, int* count, int64_t C, int* perm,
+                                                             unsigned* err) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int k = -1;
+    if (p < np) {
+        k = bin[p];
+        if (k < 0 || k >= C) k = -1;
+    }
+    const unsigned mask = run_mask(k);
+    if (k < 0) return;
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    const int ng = __popc(mask);
+    int old = 0;
+    if (lane == leader) old = atomicSub(count + k, ng);
+    old = __shfl_sync(mask, old, leader);
+    const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
+#ifdef PIC_CHECK
+    if (!(dest >= 0 && dest < np)) {
+        check_failed(err, 9, dest);
+        return;
+    }
+#endif
+    perm[dest] = int(p);
 }
 
 // SplitMix64 output function (Steele, Lea & Flood 2014): a bijective 64-bit mixer.
@@ -269,6 +327,14 @@ cudaError_t launch_scan(pic_ctx* c) {
     if (e != cudaSuccess) return e;
     k_scan<<<unsigned(c->scan_chunks), kSortBlock, 0, c->stream>>>(c->count, c->offsets, nbins(c), c->scan_status,
                                                                   c->scan_chunks, c->err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_perm(pic_ctx* c) {
+    if (c->np == 0) return cudaSuccess;
+    const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
+    k_scatter_perm<<<nb, kSortBlock, 0, c->stream>>>(bins(c), c->np, c->offsets, c->count, nbins(c), c->perm,
+                                                      c->err);
     return cudaGetLastError();
 }
 
