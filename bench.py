@@ -428,15 +428,14 @@ def field_error_statement(torch, steps=100):
 
 
 def step_bytes(np_, C, prec="fp32", sort=True):
-    """Algorithmic HBM bytes of one whole step: the tile kernel's (particle
-    state read and written once, E/B read and J written once per cell), the
-    field update's three passes (B half step: E, B read, B written; E step: E,
-    B, J read, E written; B half step again) and, when the particles are
-    sorted that step, the sort (key read by the histogram, every particle
-    array read and written by the scatter: FP32-mixed 76 B, FP64 144 B a
-    particle)."""
+    """Algorithmic HBM bytes of one whole step, as the method's minimum: the
+    tile kernel's (particle state read and written once, E/B read and J
+    written once per cell), the field update's (E, B, J read and E, B written
+    once per cell) and, when the particles are sorted that step, a sort
+    moving every particle once more (FP32-mixed 76 B, FP64 144 B a particle;
+    the library's permutation sort moves less)."""
     rs = 4 if prec == "fp32" else 8
-    yee = C * rs * (9 + 12 + 9)
+    yee = C * rs * (9 + 6)
     srt = np_ * (76 if prec == "fp32" else 144) if sort else 0
     return bytes_per_launch(np_, C, prec) + yee + srt
 
@@ -479,7 +478,7 @@ def hbm_leg_statement(torch, stream, peaks, steps=20, warmup=3):
                          "bytes": "60 B a particle + 36 B a cell per launch"},
             "step_roofline": {"achieved": step_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": step_gbs / peaks["hbm_gbs"],
-                              "bytes": "tile kernel + sort (76 B a particle) + field update (120 B a cell)"}}
+                              "bytes": "tile kernel + sort (76 B a particle) + field update (60 B a cell)"}}
 
 
 def ensemble_statement(torch, stream, steps=20):
