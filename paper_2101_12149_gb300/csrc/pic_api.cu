@@ -251,6 +251,27 @@ cudaError_t run_yee(pic_ctx* c) {
     return counted(c, "k_step_counter", 1, pic::launch_step_counter);
 }
 
+// The particle half and the field half of a step.  With two field sets the
+// tile kernel deposits J into the other set and the one-pass Yee update
+// writes E and B there from the current set's; the sets then swap roles.
+// With one set (CKC) J goes into the current set and the three in-place
+// passes follow.
+cudaError_t run_tile_and_fields(pic_ctx* c) {
+    cudaError_t e;
+    if (c->filter_passes > 0 && (e = counted(c, "k_filter_z", 1, pic::launch_filter)) != cudaSuccess) return e;
+    if (!c->Fo[0]) {
+        if ((e = counted(c, "k_tile_step", 2, pic::launch_tile_step)) != cudaSuccess) return e;
+        return run_yee(c);
+    }
+    c->j_other = true;
+    e = counted(c, "k_tile_step", 2, pic::launch_tile_step);
+    c->j_other = false;
+    if (e != cudaSuccess) return e;
+    if ((e = counted(c, "k_yee_fused", 1, pic::launch_yee_fused)) != cudaSuccess) return e;
+    pic::swap_field_sets(c);
+    return cudaSuccess;
+}
+
 // One full step as queued work.  `with_sort` runs the counting sort first, as
 // a permutation: histogram, scan, then the slots as perm; the tile kernel
 // moves each particle from the other buffer into its sorted slot of the
@@ -264,11 +285,9 @@ cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
         c->cur = 1 - c->cur;
         c->tile_perm = c->np > 0;
     }
-    if (c->filter_passes > 0 && (e = counted(c, "k_filter_z", 1, pic::launch_filter)) != cudaSuccess) return e;
-    e = counted(c, "k_tile_step", 2, pic::launch_tile_step);
+    e = run_tile_and_fields(c);
     c->tile_perm = false;
-    if (e != cudaSuccess) return e;
-    return run_yee(c);
+    return e;
 }
 
 // Particle count after a sort with open z: the removed ones went to the last bin.
@@ -289,9 +308,7 @@ cudaError_t inject(pic_ctx* c) { return pic::launch_inject(c); }
 // next cell, then a sort that also drops the removed particles.  The state
 // after the step is sorted and holds only live particles.
 pic_status run_window_step(pic_ctx* c) {
-    if (c->filter_passes > 0) PIC_CUDA(counted(c, "k_filter_z", 1, pic::launch_filter));
-    PIC_CUDA(counted(c, "k_tile_step", 2, pic::launch_tile_step));
-    PIC_CUDA(run_yee(c));
+    PIC_CUDA(run_tile_and_fields(c));
     c->step += 1;
     const double t = double(c->step) * c->dt;
     while (c->window_speed > 0.0 && c->window_speed * t >= double(c->shifts + 1) * c->g.d[2]) {
@@ -608,10 +625,16 @@ pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx**
         return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, what) : cuda_fail(e, what);
     };
     cudaError_t e;
-    char* fb = nullptr;
-    if ((e = cudaMalloc(&fb, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field allocation");
-    for (int i = 0; i < 9; ++i) c->F[i] = fb + i * C * c->rsize;
-    if ((e = cudaMemset(fb, 0, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field zeroing");
+    // Two field sets with the plain Yee solver (the one-pass update writes the
+    // other set), one with CKC (its three in-place passes).
+    for (int s = 0; s < (c->solver == 0 ? 2 : 1); ++s) {
+        char* fb = nullptr;
+        if ((e = cudaMalloc(&fb, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field allocation");
+        c->fblock[s] = fb;
+        for (int i = 0; i < 9; ++i) (s == 0 ? c->F : c->Fo)[i] = fb + i * C * c->rsize;
+        if ((e = cudaMemset(fb, 0, 9 * C * c->rsize)) != cudaSuccess) return bail(e, "field zeroing");
+    }
+    if (c->Fo[0] && (e = pic::configure_yee_fused()) != cudaSuccess) return bail(e, "Yee kernel configuration");
     // one bin more than cells (removed particles, open z) and its offset
     if ((e = cudaMalloc(&c->count, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "count allocation");
     if ((e = cudaMemset(c->count, 0, (C + 1) * sizeof(int))) != cudaSuccess) return bail(e, "count zeroing");
@@ -637,7 +660,8 @@ pic_status pic_destroy(pic_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
     free_particles(c);
-    cudaFree(c->F[0]);
+    cudaFree(c->fblock[0]);
+    cudaFree(c->fblock[1]);
     cudaFree(c->count);
     cudaFree(c->offsets);
     cudaFree(c->scan_status);
@@ -872,12 +896,12 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     const bool use_graph = c->stream != nullptr && !c->timing && c->sort_every == 1;
     if (use_graph) {
         while (left >= 2) {
-            if (!c->graph || c->graph_cur != c->cur) {
+            if (!c->graph || c->graph_cur != c->cur || c->graph_fpar != c->fpar) {
                 if (c->graph) {
                     cudaGraphExecDestroy(c->graph);
                     c->graph = nullptr;
                 }
-                const int cur0 = c->cur;
+                const int cur0 = c->cur, fpar0 = c->fpar;
                 PIC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 g_capturing = true;
                 g_capture_kernels = 0;
@@ -887,6 +911,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
                 cudaGraph_t graph = nullptr;
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);
                 c->cur = cur0;
+                if (c->fpar != fpar0) pic::swap_field_sets(c);  // a capture that stopped after one step
                 if (e1 != cudaSuccess) {
                     if (graph) cudaGraphDestroy(graph);
                     return cuda_fail(e1, "step capture");
@@ -896,6 +921,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
                 cudaGraphDestroy(graph);
                 if (e3 != cudaSuccess) return cuda_fail(e3, "graph instantiate");
                 c->graph_cur = cur0;
+                c->graph_fpar = fpar0;
                 c->graph_kernels = g_capture_kernels;
             }
             PIC_CUDA(cudaGraphLaunch(c->graph, c->stream));

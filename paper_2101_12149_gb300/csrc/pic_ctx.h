@@ -69,7 +69,15 @@ struct pic_ctx {
     int device = 0;
     size_t rsize = 8;  // bytes per real (8 FP64, 4 FP32-mixed)
 
-    void* F[9] = {nullptr};  // Ex Ey Ez Bx By Bz Jx Jy Jz
+    void* F[9] = {nullptr};  // Ex Ey Ez Bx By Bz Jx Jy Jz (the current set)
+    // The other set of the same nine arrays (plain Yee solver): a step's
+    // current is deposited into it and the one-pass field update writes the
+    // new E and B into it, then the two sets swap roles.  Both sets are one
+    // allocation each (fblock); fpar says which block is current.
+    void* Fo[9] = {nullptr};
+    void* fblock[2] = {nullptr, nullptr};
+    int fpar = 0;
+    bool j_other = false;  // the tile kernel deposits into Fo's J
 
     int64_t np = 0, cap = 0;
     double q = 0.0, m = 1.0;
@@ -91,6 +99,8 @@ struct pic_ctx {
     // is one tile's staged E/B block
     CUtensorMap tmap_eb;
     bool tma = false;
+    CUtensorMap tmap_eb_o;  // the other set's E/B
+    bool tma_o = false;
 
     int* count = nullptr;    // per-cell particle counts [C]
     int* offsets = nullptr;  // exclusive scan of count [C+1]; tile t owns [offsets[t*cpt], offsets[(t+1)*cpt])
@@ -147,6 +157,7 @@ struct pic_ctx {
 
     cudaGraphExec_t graph = nullptr;
     int graph_cur = 0;
+    int graph_fpar = 0;
     int graph_kernels = 0;
     int64_t launches = 0;
 
@@ -180,6 +191,12 @@ cudaError_t launch_gather_push_global(pic_ctx* c);
 cudaError_t launch_deposit_global(pic_ctx* c);
 cudaError_t launch_yee_b(pic_ctx* c, double h);
 cudaError_t launch_yee_e(pic_ctx* c);
+// One-pass field update from the current set (E, B) and the other set's J
+// into the other set's E, B, and the step counter advanced (plain Yee, the
+// other set allocated); the caller then swaps the sets (swap_field_sets).
+cudaError_t launch_yee_fused(pic_ctx* c);
+cudaError_t configure_yee_fused();
+void swap_field_sets(pic_ctx* c);
 
 cudaError_t launch_step_counter(pic_ctx* c);
 // particles [base, base + n) from arrays that start at particle base

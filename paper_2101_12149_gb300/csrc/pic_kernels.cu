@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <cstring>
 #include <type_traits>
+#include <utility>
 
 #include "pic_ctx.h"
 #include "pic_device.cuh"
@@ -1189,7 +1190,7 @@ template <typename R> cudaError_t tile_step_dispatch(pic_ctx* c) {
 cudaError_t launch_tile_step(pic_ctx* c) {
     // J is one allocation of three components (see pic_api.cu); the outsider
     // count and the tile queue counter sit after the four error words
-    cudaError_t e = cudaMemsetAsync(c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
+    cudaError_t e = cudaMemsetAsync(c->j_other ? c->Fo[6] : c->F[6], 0, 3 * c->g.C * c->rsize, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->err + 4, 0, 2 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) return e;
     return c->prec == PIC_FP64 ? tile_step_dispatch<double>(c) : tile_step_dispatch<float>(c);
@@ -1230,9 +1231,15 @@ bool encode_eb_tensor_map(CUtensorMap* map, const void* base, const int n[3], in
 }
 
 void setup_tile_tma(pic_ctx* c) {
-    c->tma = false;
-    std::memset(&c->tmap_eb, 0, sizeof(c->tmap_eb));
     c->tma = encode_eb_tensor_map(&c->tmap_eb, c->F[0], c->g.n, c->g.C, c->layout, c->prec);
+    c->tma_o = c->Fo[0] && encode_eb_tensor_map(&c->tmap_eb_o, c->Fo[0], c->g.n, c->g.C, c->layout, c->prec);
+}
+
+void swap_field_sets(pic_ctx* c) {
+    for (int i = 0; i < 9; ++i) std::swap(c->F[i], c->Fo[i]);
+    std::swap(c->tmap_eb, c->tmap_eb_o);
+    std::swap(c->tma, c->tma_o);
+    c->fpar ^= 1;
 }
 
 // The tile kernels need more than 48 KB of dynamic shared memory: raise the

@@ -115,7 +115,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
             a.E[d] = static_cast<const R*>(c->F[d]);
             a.B[d] = static_cast<const R*>(c->F[3 + d]);
         }
-        a.J[d] = static_cast<R*>(c->F[6 + d]);
+        a.J[d] = static_cast<R*>(c->j_other ? c->Fo[6 + d] : c->F[6 + d]);
     }
     a.dt = c->dt;
     const PartBuf& P = c->P[c->cur];

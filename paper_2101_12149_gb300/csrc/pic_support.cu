@@ -170,6 +170,209 @@ template <typename R> __global__ void __launch_bounds__(kBlock) k_yee_e(YeeArgs<
     if (r.ok) yee_e_ijk(Y, r.c, r.i, r.j, r.k);
 }
 
+// ---------------------------------------------------------------------------
+// The whole Yee step in one pass (plain Yee solver), from one field set into
+// the other, with the formulas of yee_b_ijk / yee_e_ijk: B half step, E step,
+// B half step.  Each block owns a y-z tile of kYTY x kYTZ cells and marches
+// along an x-chunk of kYXC cells; at x = i it
+//   - computes B'(i+1) = B(i+1) - dt/2 curl E on the tile plus a one-cell
+//     y-z halo (needs E at i+1 and i+2),
+//   - computes E'(i+1) = E(i+1) + dt (curl B' - J) on the tile plus the
+//     halo cell above in y and z (needs B' at i+1 and i),
+//   - computes B''(i) = B'(i) - dt/2 curl E' on the tile (needs E' at i and
+//     i+1) and writes E'(i) and B''(i) into the other field set.
+// Shared memory holds y-z planes only (E: ring of 4, B: ring of 3, J: ring of
+// 2), the next planes load with cp.async while the current ones compute, so
+// HBM sees E, B, J read once and E, B written once a cell (60 bytes in FP32
+// against the three in-place passes' 120); the y-z halos are re-read from L2
+// by the neighbouring tiles.  Reads and writes go to different arrays, so no
+// block sees another's new values.  With z open, fields beyond the z ends are
+// zero in every phase.
+//
+// Planes are stored row by row (y), 32 cells a row for E (z from k0 - 1), 31
+// for B, 30 for J (z from k0): warp w works row w, its lanes along z.
+// ---------------------------------------------------------------------------
+constexpr int kYTY = 7;                        // tile rows (y)
+constexpr int kYTZ = 29;                       // tile depth (z): E rows are 32 cells
+constexpr int kEY = kYTY + 3, kEZ = kYTZ + 3;  // E plane: y from -1, z from -1
+constexpr int kBY = kYTY + 2, kBZ = kYTZ + 2;  // B plane: y from -1, z from -1
+constexpr int kJY = kYTY + 1, kJZ = kYTZ + 1;  // J plane: y from 0, z from 0
+constexpr int kEP = kEY * kEZ, kBP = kBY * kBZ, kJP = kJY * kJZ;
+constexpr int kYWarps = kEY;                   // warp w stages row w of every plane
+constexpr int kYThreads = 32 * kYWarps;
+static_assert(kEZ == 32, "E rows are one warp wide");
+
+template <typename R> constexpr size_t yee_fused_smem() { return sizeof(R) * 3 * size_t(4 * kEP + 3 * kBP + 2 * kJP); }
+
+template <typename R> struct YeeFusedArgs {
+    const R* E[3];
+    const R* B[3];
+    const R* J[3];
+    R* Eo[3];  // the other set, written
+    R* Bo[3];
+    int n[3];
+    int nt[3];  // x-chunks, y tiles, z tiles
+    int xc;     // x-chunk length
+    R inv[3];
+    R h;   // dt / 2
+    R dt;
+    long long* step;
+    int zopen;
+};
+
+// One element copied global -> shared without passing through registers
+// (cp.async: every copy of a plane is in flight at once); a source size of 0
+// fills the element with zero, the source address stays a valid one.
+template <typename R> __device__ __forceinline__ void copy_elem_async(R* dst, const R* src, bool ok) {
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst));
+    const unsigned bytes = ok ? unsigned(sizeof(R)) : 0u;
+    if constexpr (sizeof(R) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ int step_wrap(int x, int n) { return x + 1 == n ? 0 : x + 1; }
+
+template <typename R> __global__ void __launch_bounds__(kYThreads) k_yee_fused(YeeFusedArgs<R> Y) {
+    extern __shared__ __align__(16) unsigned char yee_raw[];
+    R* const sm = reinterpret_cast<R*>(yee_raw);
+    R* const Eb = sm;                  // 4 planes x 3 components x kEP
+    R* const Bb = Eb + 12 * kEP;       // 3 planes x 3 x kBP
+    R* const Jb = Bb + 9 * kBP;        // 2 planes x 3 x kJP
+    // z fastest, then y, then the x-chunk: neighbouring tiles run together
+    const int bz = int(blockIdx.x % unsigned(Y.nt[2]));
+    const int rb = int(blockIdx.x / unsigned(Y.nt[2]));
+    const int by = rb % Y.nt[1], bx = rb / Y.nt[1];
+    const int x0 = bx * Y.xc, x1 = min(x0 + Y.xc, Y.n[0]);
+    const int j0 = by * kYTY, k0 = bz * kYTZ;
+    const int warp = int(threadIdx.x) >> 5, lane = int(threadIdx.x) & 31;
+    const int64_t sx = int64_t(Y.n[1]) * Y.n[2];
+    // this lane's z in the E / B planes (from k0 - 1) and in the J plane (from k0)
+    const int zlo = k0 - 1 + lane, zj = k0 + lane;
+    const bool zlo_in = unsigned(zlo) < unsigned(Y.n[2]), zj_in = unsigned(zj) < unsigned(Y.n[2]);
+    const bool zlo_ok = !Y.zopen || zlo_in, zj_ok = !Y.zopen || zj_in;
+    // this thread's row w of the E and B planes (y = j0 - 1 + w) and of the J
+    // plane (y = j0 + w): source offsets within an x-plane, wrapped
+    const int64_t off_eb = int64_t(wrap_any(j0 - 1 + warp, Y.n[1])) * Y.n[2] + wrap_any(zlo, Y.n[2]);
+    const int64_t off_j = int64_t(wrap_any(j0 + warp, Y.n[1])) * Y.n[2] + wrap_any(zj, Y.n[2]);
+    const bool ld_b = warp < kBY && lane < kBZ, ld_j = warp < kJY && lane < kJZ;
+    const int se = warp * kEZ + lane, sb = warp * kBZ + lane, sj = warp * kJZ + lane;
+
+    // E(xe) into plane eb, B(xb) into bb, J(xj) into jb (x wrapped; a null
+    // plane skips that field), row `warp` of every component
+    auto load_planes = [&](int xe, R* eb, int xb, R* bb, int xj, R* jb) {
+        if (eb) {
+            const int64_t o = xe * sx + off_eb;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) copy_elem_async(eb + c * kEP + se, Y.E[c] + o, zlo_ok);
+        }
+        if (bb && ld_b) {
+            const int64_t o = xb * sx + off_eb;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) copy_elem_async(bb + c * kBP + sb, Y.B[c] + o, zlo_ok);
+        }
+        if (jb && ld_j) {
+            const int64_t o = xj * sx + off_j;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) copy_elem_async(jb + c * kJP + sj, Y.J[c] + o, zj_ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    // ring roles: E'(i) / E(i+1) -> E'(i+1) / E(i+2) / E(i+3) loading;
+    // B'(i) / B(i+1) -> B'(i+1) / B(i+2) loading; J(i+1) / J(i+2) loading
+    int eP = 0, eC = 1, eN = 2, eL = 3, b0 = 0, b1 = 1, bL = 2, j1 = 0, jL = 1;
+    // the march starts at i = x0 - 2 with E(x0 - 1), E(x0) and B(x0 - 1) in
+    int xm = wrap_any(x0 - 1, Y.n[0]);  // x0 - 1, wrapped
+    int xz = step_wrap(xm, Y.n[0]);     // x0
+    load_planes(xm, Eb + 3 * eC * kEP, xm, Bb + 3 * b1 * kBP, 0, nullptr);
+    load_planes(xz, Eb + 3 * eN * kEP, 0, nullptr, 0, nullptr);
+    int xb = xz;                        // i + 2 at i = x0 - 2, wrapped
+    int xe = step_wrap(xb, Y.n[0]);     // i + 3
+    const R h = Y.h;
+    for (int i = x0 - 2; i < x1; ++i) {
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        __syncthreads();  // this step's planes are in; last step's readers are done
+        if (i + 1 < x1)   // E(i+3), B(i+2), J(i+2) for the next step
+            load_planes(xe, Eb + 3 * eL * kEP, xb, Bb + 3 * bL * kBP, xb, Jb + 3 * jL * kJP);
+        xb = xe;
+        xe = step_wrap(xe, Y.n[0]);
+        const R* Ec = Eb + 3 * eC * kEP;
+        const R* En = Eb + 3 * eN * kEP;
+        R* B1 = Bb + 3 * b1 * kBP;
+        // B'(i+1) on rows -1 .. kYTY, z -1 .. kYTZ
+        if (warp < kBY && lane < kBZ) {
+            const int c = se, jp = c + kEZ, kp = c + 1;
+            const int e = sb;
+            const R ex = Ec[c], ey = Ec[kEP + c], ez = Ec[2 * kEP + c];
+            const R dEz_dy = (Ec[2 * kEP + jp] - ez) * Y.inv[1];
+            const R dEy_dz = (Ec[kEP + kp] - ey) * Y.inv[2];
+            const R dEx_dz = (Ec[kp] - ex) * Y.inv[2];
+            const R dEz_dx = (En[2 * kEP + c] - ez) * Y.inv[0];
+            const R dEy_dx = (En[kEP + c] - ey) * Y.inv[0];
+            const R dEx_dy = (Ec[jp] - ex) * Y.inv[1];
+            const bool out = Y.zopen && !zlo_in;
+            B1[e] = out ? R(0) : B1[e] - h * (dEz_dy - dEy_dz);
+            B1[kBP + e] = out ? R(0) : B1[kBP + e] - h * (dEx_dz - dEz_dx);
+            B1[2 * kBP + e] = out ? R(0) : B1[2 * kBP + e] - h * (dEy_dx - dEx_dy);
+        }
+        __syncthreads();
+        // E'(i+1) on rows 0 .. kYTY, z 0 .. kYTZ (into E(i+1)'s plane)
+        if (i >= x0 - 1 && warp < kJY && lane < kJZ) {
+            const R* B0 = Bb + 3 * b0 * kBP;
+            const R* J1 = Jb + 3 * j1 * kJP;
+            R* Ew = Eb + 3 * eC * kEP;
+            const int cb = sb + kBZ + 1, jm = cb - kBZ, km = cb - 1;
+            const int ce = se + kEZ + 1;
+            const int e = sj;
+            const R bx_ = B1[cb], by_ = B1[kBP + cb], bz_ = B1[2 * kBP + cb];
+            const R dBz_dy = (bz_ - B1[2 * kBP + jm]) * Y.inv[1];
+            const R dBy_dz = (by_ - B1[kBP + km]) * Y.inv[2];
+            const R dBx_dz = (bx_ - B1[km]) * Y.inv[2];
+            const R dBz_dx = (bz_ - B0[2 * kBP + cb]) * Y.inv[0];
+            const R dBy_dx = (by_ - B0[kBP + cb]) * Y.inv[0];
+            const R dBx_dy = (bx_ - B1[jm]) * Y.inv[1];
+            const bool out = Y.zopen && !zj_in;
+            Ew[ce] = out ? R(0) : Ew[ce] + Y.dt * ((dBz_dy - dBy_dz) - J1[e]);
+            Ew[kEP + ce] = out ? R(0) : Ew[kEP + ce] + Y.dt * ((dBx_dz - dBz_dx) - J1[kJP + e]);
+            Ew[2 * kEP + ce] = out ? R(0) : Ew[2 * kEP + ce] + Y.dt * ((dBy_dx - dBx_dy) - J1[2 * kJP + e]);
+        }
+        __syncthreads();
+        // B''(i) on the tile; E'(i) and B''(i) into the other set
+        if (i >= x0 && warp < kYTY && lane < kYTZ && j0 + warp < Y.n[1] && zj_in) {
+            const R* Ep = Eb + 3 * eP * kEP;
+            const R* B0 = Bb + 3 * b0 * kBP;
+            const int ce = se + kEZ + 1, jp = ce + kEZ, kp = ce + 1;
+            const int cb = sb + kBZ + 1;
+            const R ex = Ep[ce], ey = Ep[kEP + ce], ez = Ep[2 * kEP + ce];
+            const R dEz_dy = (Ep[2 * kEP + jp] - ez) * Y.inv[1];
+            const R dEy_dz = (Ep[kEP + kp] - ey) * Y.inv[2];
+            const R dEx_dz = (Ep[kp] - ex) * Y.inv[2];
+            const R dEz_dx = (Ec[2 * kEP + ce] - ez) * Y.inv[0];
+            const R dEy_dx = (Ec[kEP + ce] - ey) * Y.inv[0];
+            const R dEx_dy = (Ep[jp] - ex) * Y.inv[1];
+            // the tile's own cells need no wrap: row j0 + warp, z = zj
+            const int64_t g = int64_t(i) * sx + int64_t(j0 + warp) * Y.n[2] + zj;
+            Y.Bo[0][g] = B0[cb] - h * (dEz_dy - dEy_dz);
+            Y.Bo[1][g] = B0[kBP + cb] - h * (dEx_dz - dEz_dx);
+            Y.Bo[2][g] = B0[2 * kBP + cb] - h * (dEy_dx - dEx_dy);
+            Y.Eo[0][g] = ex;
+            Y.Eo[1][g] = ey;
+            Y.Eo[2][g] = ez;
+        }
+        // rotate the rings
+        const int ep = eP;
+        eP = eC, eC = eN, eN = eL, eL = ep;
+        const int bp = b0;
+        b0 = b1, b1 = bL, bL = bp;
+        const int jq = j1;
+        j1 = jL, jL = jq;
+    }
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    if (Y.step && blockIdx.x == 0 && threadIdx.x == 0) *Y.step += 1;
+}
+
 // Batch of boxes: block b updates cells [blocks[b].y, blocks[b].y + blocks[b].z)
 // of box blocks[b].x (a block never spans two boxes).  `step`, when non-null,
 // is advanced once.
@@ -527,6 +730,51 @@ cudaError_t launch_yee_b(pic_ctx* c, double h) {
         else k_yee_b<float><<<yee_grid(c), kBlock, 0, c->stream>>>(Y);
     }
     return cudaGetLastError();
+}
+
+
+template <typename R> cudaError_t yee_fused_impl(pic_ctx* c) {
+    YeeFusedArgs<R> Y;
+    for (int d = 0; d < 3; ++d) {
+        Y.E[d] = static_cast<const R*>(c->F[d]);
+        Y.B[d] = static_cast<const R*>(c->F[3 + d]);
+        Y.J[d] = static_cast<const R*>(c->Fo[6 + d]);
+        Y.Eo[d] = static_cast<R*>(c->Fo[d]);
+        Y.Bo[d] = static_cast<R*>(c->Fo[3 + d]);
+        Y.n[d] = c->g.n[d];
+        Y.inv[d] = R(1.0 / c->g.d[d]);
+    }
+    Y.nt[1] = (c->g.n[1] + kYTY - 1) / kYTY;
+    Y.nt[2] = (c->g.n[2] + kYTZ - 1) / kYTZ;
+    // x-chunks of 32 cells, halved (down to 8) until the launch fills the GPU
+    // about four times over: each chunk pays two partial steps to start
+    const int64_t tiles = int64_t(Y.nt[1]) * Y.nt[2];
+    const int64_t want = 4 * int64_t(c->sms > 0 ? c->sms : 148) * (c->prec == PIC_FP64 ? 3 : 6);
+    Y.xc = 32;
+    while (Y.xc > 8 && tiles * ((c->g.n[0] + Y.xc - 1) / Y.xc) < want) Y.xc /= 2;
+    Y.nt[0] = (c->g.n[0] + Y.xc - 1) / Y.xc;
+    Y.h = R(0.5 * c->dt);
+    Y.dt = R(c->dt);
+    Y.step = c->d_step;
+    Y.zopen = c->g.zopen;
+    const int64_t blocks = int64_t(Y.nt[0]) * Y.nt[1] * Y.nt[2];
+    k_yee_fused<R><<<unsigned(blocks), kYThreads, yee_fused_smem<R>(), c->stream>>>(Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_yee_fused(pic_ctx* c) {
+    return c->prec == PIC_FP64 ? yee_fused_impl<double>(c) : yee_fused_impl<float>(c);
+}
+
+// The one-pass update's shared memory can exceed 48 KB (FP64): raised once,
+// before any stream capture.
+cudaError_t configure_yee_fused() {
+    cudaError_t e = cudaFuncSetAttribute(k_yee_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         int(yee_fused_smem<float>()));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_yee_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(yee_fused_smem<double>()));
+    return e;
 }
 
 cudaError_t launch_yee_e(pic_ctx* c) {

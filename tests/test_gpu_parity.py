@@ -244,6 +244,25 @@ def test_tiles_of_two_z_cells_mix_tma_and_loads(precision):
         assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
 
 
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+@pytest.mark.parametrize("n", [(70, 19, 61), (33, 9, 30), (4, 3, 5)])
+def test_one_pass_field_update_ragged(precision, n):
+    """Whole steps (the field half is the one-pass update from one field set
+    into the other: y-z tiles of 8 x 29 cells marching along x-chunks of 32)
+    on grids whose extents leave ragged x-chunks, y tiles and z tiles, and on
+    a grid smaller than one tile's halo in every axis; strong random fields
+    so that any wrong halo cell, plane or ring slot shows at O(1); three
+    steps, so the field sets swap roles and swap back."""
+    c = Case(n, 1, 1, 0.3, 131, precision=precision, field_scale=0.5)
+    c.ctx.step(3)
+    c.oracle_steps(3)
+    e = c.errors()
+    if precision == pic.FP64:
+        assert max(e.values()) < 1e-12, e
+    else:
+        assert e["EB"] < 1e-5 and e["J"] < 1e-4 and e["pos"] < 1e-6 and e["mom"] < 1e-5, e
+
+
 @pytest.mark.parametrize("precision,tol", [(pic.FP64, 1e-14), (pic.FP32_MIXED, 1e-6)])
 @pytest.mark.parametrize("n,zopen", [((12, 20, 96), False), ((9, 17, 70), False), ((8, 8, 64), True),
                                      ((128, 128, 128), False)])
