@@ -89,6 +89,37 @@ def bytes_per_launch(np_, C, prec):
     return np_ * 104 + C * (48 + 24)
 
 
+def kernel_bytes(name, np_, C, prec):
+    """Algorithmic HBM bytes of one launch of each kernel of the step, with a
+    statement of what they count; None for kernels without a fixed amount."""
+    rs = 4 if prec == "fp32" else 8
+    table = {
+        "k_tile_step": (bytes_per_launch(np_, C, prec), "particle state read and written once, E/B read and J "
+                        "written once per cell"),
+        "k_yee_fused": (C * rs * 15, "E, B, J read and E, B written once per cell"),
+        "k_yee_b": (C * rs * 9, "E, B read and B written once per cell"),
+        "k_yee_e": (C * rs * 12, "E, B, J read and E written once per cell"),
+        "k_hist": (np_ * 4 + C * 4, "keys read, counts written"),
+        "k_scan": (C * 8, "counts read, offsets written"),
+        "k_scatter_perm": (np_ * 8 + C * 4, "keys read, slots written, offsets read"),
+        "k_scatter": (np_ * (72 if prec == "fp32" else 128), "every particle array read and written once"),
+    }
+    return table.get(name)
+
+
+def kernel_rooflines(timings, np_, C, prec, hbm_gbs):
+    """Each timed kernel's algorithmic bytes over its mean launch time (CUDA
+    events on the launching stream) against the measured HBM copy rate."""
+    out = {}
+    for name, (ms, n) in timings.items():
+        kb = kernel_bytes(name, np_, C, prec)
+        if not kb or not n or ms <= 0:
+            continue
+        gbs = kb[0] / (ms / n / 1e3) / 1e9
+        out[name] = {"bytes_per_launch": kb[0], "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm_gbs, "bytes": kb[1]}
+    return out
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -472,6 +503,7 @@ def hbm_leg_statement(torch, stream, peaks, steps=20, warmup=3):
             "particle_steps_per_s": N * steps / t, "cell_steps_per_s": C * steps / t,
             "fom_per_gpu": C * (0.1 + 0.9 * ppc) / (t / steps),
             "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in tm.items()},
+            "kernel_rooflines": kernel_rooflines(tm, N, C, "fp32", peaks["hbm_gbs"]),
             "roofline": {"bound": "hbm", "kernel": "k_tile_step", "achieved": tile_gbs, "peak": peaks["hbm_gbs"],
                          "unit": "GB/s", "frac": tile_gbs / peaks["hbm_gbs"],
                          "traffic": profiled_traffic("k_tile_step", "fp32", "uniform_256_o1"),
@@ -842,6 +874,7 @@ def main():
         "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in timings.items()},
         "ms_per_step_with_kernel_events": 1e3 * t_evented / args.steps,
         "kernel_share": {k: v[0] / max(sum(x[0] for x in timings.values()), 1e-30) for k, v in timings.items()},
+        "kernel_rooflines": kernel_rooflines(timings, N, C, args.precision, peaks["hbm_gbs"]),
         "gpu_launches": int(launches),
         "clocks": clocks,
         "device_roofs": roofs,
