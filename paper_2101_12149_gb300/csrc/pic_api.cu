@@ -221,12 +221,29 @@ cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)
 
 // With PIC_DEBUG_SYNC set, every counted launch is followed by a stream
 // synchronisation and a failure names the kernel on stderr.
+// The particles' keys changed outside a counting tile step: a histogram the
+// count array holds no longer matches them.
+void keys_changed(pic_ctx* c) {
+    if (c->count_state == 1) c->count_state = 2;
+}
+
+// count := the histogram of the sort bins (all zero again first if stale).
+cudaError_t run_hist(pic_ctx* c) {
+    cudaError_t e;
+    if (c->count_state != 0 &&
+        (e = cudaMemsetAsync(c->count, 0, (size_t(c->g.C) + 1) * sizeof(int), c->stream)) != cudaSuccess)
+        return e;
+    return counted(c, "k_hist", 1, pic::launch_hist);
+}
+
+// A full sort (every particle array moved); count is zero afterwards.
 cudaError_t run_sort(pic_ctx* c) {
     cudaError_t e;
-    if ((e = counted(c, "k_hist", 1, pic::launch_hist)) != cudaSuccess) return e;
+    if ((e = run_hist(c)) != cudaSuccess) return e;
     if ((e = counted(c, "k_scan", 1, pic::launch_scan)) != cudaSuccess) return e;
     if ((e = counted(c, "k_scatter", 1, pic::launch_scatter)) != cudaSuccess) return e;
     c->cur = 1 - c->cur;
+    c->count_state = 0;
     return cudaSuccess;
 }
 
@@ -256,17 +273,20 @@ cudaError_t run_yee(pic_ctx* c) {
 // writes E and B there from the current set's; the sets then swap roles.
 // With one set (CKC) J goes into the current set and the three in-place
 // passes follow.
-cudaError_t run_tile_and_fields(pic_ctx* c) {
+// `count_next`: the tile kernel also counts its particles' new keys into the
+// (all-zero) count array, so that the next step's sort needs no histogram.
+cudaError_t run_tile_and_fields(pic_ctx* c, bool count_next = false) {
     cudaError_t e;
     if (c->filter_passes > 0 && (e = counted(c, "k_filter_z", 1, pic::launch_filter)) != cudaSuccess) return e;
-    if (!c->Fo[0]) {
-        if ((e = counted(c, "k_tile_step", 2, pic::launch_tile_step)) != cudaSuccess) return e;
-        return run_yee(c);
-    }
-    c->j_other = true;
+    c->count_into = count_next && c->count_state == 0;
+    c->j_other = c->Fo[0] != nullptr;
     e = counted(c, "k_tile_step", 2, pic::launch_tile_step);
     c->j_other = false;
+    if (c->count_into) c->count_state = 1;
+    else keys_changed(c);
+    c->count_into = false;
     if (e != cudaSuccess) return e;
+    if (!c->Fo[0]) return run_yee(c);
     if ((e = counted(c, "k_yee_fused", 1, pic::launch_yee_fused)) != cudaSuccess) return e;
     pic::swap_field_sets(c);
     return cudaSuccess;
@@ -276,16 +296,18 @@ cudaError_t run_tile_and_fields(pic_ctx* c) {
 // a permutation: histogram, scan, then the slots as perm; the tile kernel
 // moves each particle from the other buffer into its sorted slot of the
 // current one while it pushes it (the data moves once a step).
-cudaError_t enqueue_step(pic_ctx* c, bool with_sort) {
+cudaError_t enqueue_step(pic_ctx* c, bool with_sort, bool count_next) {
     cudaError_t e;
     if (with_sort) {
-        if ((e = counted(c, "k_hist", 1, pic::launch_hist)) != cudaSuccess) return e;
+        // the previous step's tile kernel may have counted the keys already
+        if (c->count_state != 1 && (e = run_hist(c)) != cudaSuccess) return e;
         if ((e = counted(c, "k_scan", 1, pic::launch_scan)) != cudaSuccess) return e;
         if ((e = counted(c, "k_scatter_perm", 1, pic::launch_scatter_perm)) != cudaSuccess) return e;
+        c->count_state = 0;
         c->cur = 1 - c->cur;
         c->tile_perm = c->np > 0;
     }
-    e = run_tile_and_fields(c);
+    e = run_tile_and_fields(c, count_next);
     c->tile_perm = false;
     return e;
 }
@@ -336,7 +358,8 @@ pic_status run_window_step(pic_ctx* c) {
 // One step of pic_step's direct path: sort at the cadence, tile kernel, Yee.
 cudaError_t run_one_step(pic_ctx* c) {
     const bool sort_now = c->since_sort >= c->sort_every;
-    cudaError_t e = enqueue_step(c, sort_now);
+    const int since_after = sort_now ? 1 : c->since_sort + 1;
+    cudaError_t e = enqueue_step(c, sort_now, since_after >= c->sort_every);
     if (e != cudaSuccess) return e;
     if (sort_now) c->since_sort = 0;
     c->since_sort += 1;
@@ -368,6 +391,7 @@ cudaError_t save_state(pic_ctx* c, const StateLayout& L, char* dst, StateMeta& m
 
 cudaError_t restore_state(pic_ctx* c, const StateLayout& L, const char* src, const StateMeta& m) {
     cudaError_t e;
+    keys_changed(c);
     if ((e = cudaMemcpyAsync(c->P[m.cur].a[0], src, L.part, cudaMemcpyDeviceToDevice, c->stream))) return e;
     if ((e = cudaMemcpyAsync(c->F[0], src + L.part, 9 * size_t(L.C) * L.rs, cudaMemcpyDeviceToDevice, c->stream)))
         return e;
@@ -449,6 +473,9 @@ pic_status read_error_word(pic_ctx* c) {
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     const unsigned h = hw[0];
     if (h == 0) return PIC_OK;
+    // after a failed step the count array may hold anything: the next sort
+    // clears it and counts afresh
+    c->count_state = 2;
     PIC_CUDA(cudaMemsetAsync(c->err, 0, sizeof(hw), c->stream));
     PIC_CUDA(cudaStreamSynchronize(c->stream));
     if (h & pic::ERRBIT_CHECK) {
@@ -834,6 +861,7 @@ pic_status pic_gather_push(pic_ctx* c) {
         return e == cudaErrorMemoryAllocation ? fail(PIC_ERR_OOM, "split-API scratch") : cuda_fail(e, "scratch");
     if (c->filter_passes > 0) PIC_CUDA(counted(c, "k_filter_z", 1, pic::launch_filter));
     PIC_CUDA(counted(c, "k_gather_push", 1, pic::launch_gather_push_global));
+    keys_changed(c);
     c->have_old = true;
     return PIC_OK;
 }
@@ -894,6 +922,11 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     // double buffer to its starting role, so a captured pair of steps can be
     // replayed as one graph launch.
     const bool use_graph = c->stream != nullptr && !c->timing && c->sort_every == 1;
+    if (use_graph && left >= 2 && c->count_state != 1) {
+        // the captured pair of steps takes the histogram from the step before
+        PIC_CUDA(run_hist(c));
+        c->count_state = 1;
+    }
     if (use_graph) {
         while (left >= 2) {
             if (!c->graph || c->graph_cur != c->cur || c->graph_fpar != c->fpar) {
@@ -905,8 +938,8 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
                 PIC_CUDA(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
                 g_capturing = true;
                 g_capture_kernels = 0;
-                cudaError_t e1 = enqueue_step(c, true);
-                if (e1 == cudaSuccess) e1 = enqueue_step(c, true);
+                cudaError_t e1 = enqueue_step(c, true, true);
+                if (e1 == cudaSuccess) e1 = enqueue_step(c, true, true);
                 g_capturing = false;
                 cudaGraph_t graph = nullptr;
                 cudaError_t e2 = cudaStreamEndCapture(c->stream, &graph);

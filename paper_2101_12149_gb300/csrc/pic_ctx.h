@@ -16,7 +16,7 @@ enum : unsigned {
     ERRBIT_PARTICLE = 1u,  // non-finite particle or a move of >= 1 cell
     ERRBIT_TIMEOUT = 2u,   // a bounded wait ran out
     ERRBIT_RANGE = 4u,     // a sort key outside [0, C)
-    ERRBIT_CHECK = 8u,     // a self-check of a checking build failed (see check word)
+    ERRBIT_CHECK = 8u,     // a device-side self-check failed (see check word); most run in checking builds only
 };
 
 // Checking builds (-DPIC_CHECK) verify indices before memory accesses; the
@@ -103,6 +103,12 @@ struct pic_ctx {
     bool tma_o = false;
 
     int* count = nullptr;    // per-cell particle counts [C]
+    // What count holds: 0 all zero (a scatter leaves it so), 1 the histogram
+    // of the current keys (a tile kernel counted its particles' new keys),
+    // 2 stale (non-zero, not the current keys: cleared before the next
+    // histogram).  count_into: the next tile-kernel launch counts.
+    int count_state = 0;
+    bool count_into = false;
     int* offsets = nullptr;  // exclusive scan of count [C+1]; tile t owns [offsets[t*cpt], offsets[(t+1)*cpt])
     unsigned long long* scan_status = nullptr;  // look-back words + ticket
     int scan_chunks = 0;

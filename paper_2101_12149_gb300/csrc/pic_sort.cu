@@ -228,12 +228,12 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     if (lane == leader) old = atomicSub(count + k, ng);
     old = __shfl_sync(mask, old, leader);
     const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
-#ifdef PIC_CHECK
+    // checked in every build: a histogram that does not match the keys
+    // (a step stopped part-way) must not send a particle outside the arrays
     if (!(dest >= 0 && dest < np)) {
         check_failed(err, 8, dest);
         return;
     }
-#endif
 #pragma unroll
     for (int i = 0; i < 7; ++i) static_cast<E*>(dst.a[i])[dest] = v[i];
     dst.key[dest] = key;
@@ -262,12 +262,12 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restri
     if (lane == leader) old = atomicSub(count + k, ng);
     old = __shfl_sync(mask, old, leader);
     const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
-#ifdef PIC_CHECK
+    // checked in every build: a histogram that does not match the keys
+    // (a step stopped part-way) must not send a particle outside the arrays
     if (!(dest >= 0 && dest < np)) {
         check_failed(err, 9, dest);
         return;
     }
-#endif
     perm[dest] = int(p);
 }
 

@@ -77,6 +77,7 @@ template <typename R> struct StepArgs {
     unsigned* err;
     int* outn;   // outsider count (device)
     int* outl;   // outsider particle indices
+    int* cnext;  // when set, count[new key] += 1 for every particle stored (the next sort's histogram)
     const long long* step;
     double drive_amp, drive_k;
     int run;            // tile kernel: particles per lane run (0 = about one cell's worth)
@@ -127,6 +128,7 @@ template <typename R> StepArgs<R> make_args(pic_ctx* c) {
     a.err = c->err;
     a.outn = reinterpret_cast<int*>(c->err + 4);
     a.outl = c->outl;
+    a.cnext = c->count_into ? c->count : nullptr;
     a.step = c->d_step;
     a.drive_amp = c->drive_amp;
     a.drive_k = c->drive_k;
@@ -502,6 +504,7 @@ template <typename R> __device__ __forceinline__ void load_raw(const StepArgs<R>
 // A particle written back unchanged (a rejected move) into slot s: only a
 // sorted-order step has to copy it, in place it is already there.
 template <typename R> __device__ __forceinline__ void keep_particle(const StepArgs<R>& A, int s, const RawParticle<R>& r) {
+    if (A.cnext) atomicAdd(A.cnext + (A.perm ? r.key : A.key[s]), 1);
     if (!A.perm) return;
 #pragma unroll
     for (int i = 0; i < 7; ++i) A.pa[i][s] = r.a[i];
@@ -572,7 +575,9 @@ __device__ __forceinline__ void store_particle(const StepArgs<R>& A, int p, cons
             A.pa[a][p] = R(nf);
         }
     }
-    A.key[p] = gone ? dead_key(g) : key_of(g, nc[0], nc[1], nc[2]);
+    const int nkey = gone ? dead_key(g) : key_of(g, nc[0], nc[1], nc[2]);
+    A.key[p] = nkey;
+    if (A.cnext) atomicAdd(A.cnext + nkey, 1);
 }
 
 // Gather + push + advance + Esirkepov for one tile of cells per CTA.
