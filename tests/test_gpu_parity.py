@@ -79,6 +79,36 @@ def test_graph_replay_matches_direct():
     assert a.ctx.launch_count() > 0
 
 
+@pytest.mark.parametrize("use_stream,sort_every", [(False, 1), (True, 1), (False, 3)])
+def test_counted_histogram_across_paths(use_stream, sort_every):
+    """The step's sort takes its histogram from the previous step's tile
+    kernel when that step counted the new keys.  Interleave everything that
+    changes keys outside such a step (the split API, a sort by coarse bins,
+    graph-replayed pairs and single direct steps, and with sort_every 3 steps
+    that do not count) and compare with the oracle after every phase."""
+    s = torch.cuda.Stream() if use_stream else None
+    c = Case((16, 16, 8), 2, 4, 0.4, 41, field_scale=0.03, stream=s, sort_every=sort_every)
+
+    def check(k):
+        c.oracle_steps(k)
+        e = c.errors()
+        assert max(e.values()) < 1e-11, e
+
+    c.ctx.step(3)            # a replayed pair (with a stream) and one direct step
+    check(3)
+    c.ctx.gather_push()      # the split API changes the keys without counting
+    c.ctx.deposit()
+    c.ctx.yee_step()
+    check(1)
+    c.ctx.step(2)
+    check(2)
+    c.ctx.sort_particles(3)  # a sort by bins of 8 cells, then the step re-sorts by cell
+    c.ctx.step(1)
+    check(1)
+    c.ctx.step(4)
+    check(4)
+
+
 def test_external_drive_fp64():
     c = Case((16, 8, 8), 2, 2, 0.05, 31)
     k = 2 * np.pi / 16
