@@ -23,7 +23,8 @@
  * step with -dt J, B half step.
  *
  * Ownership.  The context owns every device buffer; they are allocated by
- * pic_init_grid (fields, sort state, a 32 MiB host-copy staging buffer) and
+ * pic_init_grid (fields, with the Yee solver in two sets, sort state, a
+ * 32 MiB host-copy staging buffer) and
  * pic_load_particles (particle buffers), by the first call that needs an
  * optional one (the split API's scratch, the charge density of
  * pic_charge_density), and by pic_reserve_adjoint; none inside pic_step.
@@ -92,8 +93,11 @@ typedef struct {
 
 /* Create a context: validates the description (PIC_ERR_ARG, PIC_ERR_CFL),
  * allocates the nine field arrays (zeroed) on the current CUDA device and
- * binds `cuda_stream` (a cudaStream_t, may be NULL).  *out receives the
- * context; on failure *out is NULL. */
+ * binds `cuda_stream` (a cudaStream_t, may be NULL).  With the Yee solver a
+ * second set of nine arrays is allocated too: pic_step writes each step's
+ * new E and B (and deposits its J) into the other set, and the two sets then
+ * swap roles; getters and setters always address the current set.  *out
+ * receives the context; on failure *out is NULL. */
 pic_status pic_init_grid(const pic_grid_desc* desc, void* cuda_stream, pic_ctx** out);
 
 /* Load one species: charge q and mass m per unit weight, n particles with
