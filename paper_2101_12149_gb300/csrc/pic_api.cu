@@ -282,7 +282,8 @@ cudaError_t run_tile_and_fields(pic_ctx* c, bool count_next = false) {
     c->j_other = c->Fo[0] != nullptr;
     e = counted(c, "k_tile_step", 2, pic::launch_tile_step);
     c->j_other = false;
-    if (c->count_into) c->count_state = 1;
+    if (e != cudaSuccess) c->count_state = 2;  // whatever the launch left in count
+    else if (c->count_into) c->count_state = 1;
     else keys_changed(c);
     c->count_into = false;
     if (e != cudaSuccess) return e;
