@@ -201,6 +201,8 @@ bool debug_sync() {
     return on;
 }
 
+// With PIC_DEBUG_SYNC set, every counted launch is followed by a stream
+// synchronisation and a failure names the kernel on stderr.
 cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)(pic_ctx*)) {
     clear_stale(name);
     Launch l(c, name);
@@ -219,8 +221,6 @@ cudaError_t counted(pic_ctx* c, const char* name, int kernels, cudaError_t (*fn)
     return e;
 }
 
-// With PIC_DEBUG_SYNC set, every counted launch is followed by a stream
-// synchronisation and a failure names the kernel on stderr.
 // The particles' keys changed outside a counting tile step: a histogram the
 // count array holds no longer matches them.
 void keys_changed(pic_ctx* c) {

@@ -79,13 +79,15 @@ def test_graph_replay_matches_direct():
     assert a.ctx.launch_count() > 0
 
 
-@pytest.mark.parametrize("use_stream,sort_every", [(False, 1), (True, 1), (False, 3)])
+@pytest.mark.parametrize("use_stream,sort_every", [(False, 1), (True, 1), (False, 3), (True, 3)])
 def test_counted_histogram_across_paths(use_stream, sort_every):
     """The step's sort takes its histogram from the previous step's tile
     kernel when that step counted the new keys.  Interleave everything that
     changes keys outside such a step (the split API, a sort by coarse bins,
     graph-replayed pairs and single direct steps, and with sort_every 3 steps
-    that do not count) and compare with the oracle after every phase."""
+    that do not count) and compare with the oracle after every phase, with
+    and without a caller stream (captured pairs, and direct steps with
+    sort_every 3)."""
     s = torch.cuda.Stream() if use_stream else None
     c = Case((16, 16, 8), 2, 4, 0.4, 41, field_scale=0.03, stream=s, sort_every=sort_every)
 
