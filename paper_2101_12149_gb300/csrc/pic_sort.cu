@@ -219,6 +219,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
         for (int i = 0; i < 7; ++i) v[i] = static_cast<const E*>(src.a[i])[p];
         id = src.id[p];
     }
+    const int base = k >= 0 ? offsets[k] : 0;  // loaded before the atomic, as in k_scatter_perm
     const unsigned mask = run_mask(k);
     if (k < 0) return;
     const int lane = threadIdx.x & 31;
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     int old = 0;
     if (lane == leader) old = atomicSub(count + k, ng);
     old = __shfl_sync(mask, old, leader);
-    const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
+    const int dest = base + (old - ng) + __popc(mask & lanemask_lt());
     // checked in every build: a histogram that does not match the keys
     // (a step stopped part-way) must not send a particle outside the arrays
     if (!(dest >= 0 && dest < np)) {
@@ -253,6 +254,9 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restri
         k = bin[p];
         if (k < 0 || k >= C) k = -1;
     }
+    // the bin's first slot does not depend on the atomic: loaded before it,
+    // the two round trips overlap
+    const int base = k >= 0 ? offsets[k] : 0;
     const unsigned mask = run_mask(k);
     if (k < 0) return;
     const int lane = threadIdx.x & 31;
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restri
     int old = 0;
     if (lane == leader) old = atomicSub(count + k, ng);
     old = __shfl_sync(mask, old, leader);
-    const int dest = offsets[k] + (old - ng) + __popc(mask & lanemask_lt());
+    const int dest = base + (old - ng) + __popc(mask & lanemask_lt());
     // checked in every build: a histogram that does not match the keys
     // (a step stopped part-way) must not send a particle outside the arrays
     if (!(dest >= 0 && dest < np)) {
