@@ -248,31 +248,42 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
 __global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restrict__ bin, int64_t np,
                                                              const int* offsets, int* count, int64_t C, int* perm,
                                                              unsigned* err) {
-    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int k = -1;
-    if (p < np) {
-        k = bin[p];
-        if (k < 0 || k >= C) k = -1;
-    }
-    // the bin's first slot does not depend on the atomic: loaded before it,
-    // the two round trips overlap
-    const int base = k >= 0 ? offsets[k] : 0;
-    const unsigned mask = run_mask(k);
-    if (k < 0) return;
+    // two particles a thread (a block's 2 * kSortBlock consecutive
+    // particles, each half coalesced): both slot atomics are in flight at once
+    constexpr int U = 2;
+    const int64_t p0 = (int64_t)blockIdx.x * (U * kSortBlock) + threadIdx.x;
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(mask) - 1;
-    const int ng = __popc(mask);
-    int old = 0;
-    if (lane == leader) old = atomicSub(count + k, ng);
-    old = __shfl_sync(mask, old, leader);
-    const int dest = base + (old - ng) + __popc(mask & lanemask_lt());
-    // checked in every build: a histogram that does not match the keys
-    // (a step stopped part-way) must not send a particle outside the arrays
-    if (!(dest >= 0 && dest < np)) {
-        check_failed(err, 9, dest);
-        return;
+    int k[U], base[U], old[U];
+    unsigned mask[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int64_t p = p0 + u * kSortBlock;
+        k[u] = p < np ? bin[p] : -1;
+        if (k[u] < 0 || k[u] >= C) k[u] = -1;
+        // the bin's first slot does not depend on the atomic: loaded before it
+        base[u] = k[u] >= 0 ? offsets[k[u]] : 0;
     }
-    perm[dest] = int(p);
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        mask[u] = run_mask(k[u]);
+        const int leader = __ffs(mask[u]) - 1;
+        old[u] = 0;
+        if (lane == leader && k[u] >= 0) old[u] = atomicSub(count + k[u], __popc(mask[u]));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const int leader = __ffs(mask[u]) - 1;
+        old[u] = __shfl_sync(0xffffffffu, old[u], leader);
+        if (k[u] < 0) continue;
+        const int dest = base[u] + (old[u] - __popc(mask[u])) + __popc(mask[u] & lanemask_lt());
+        // checked in every build: a histogram that does not match the keys
+        // (a step stopped part-way) must not send a particle outside the arrays
+        if (!(dest >= 0 && dest < np)) {
+            check_failed(err, 9, dest);
+            continue;
+        }
+        perm[dest] = int(p0 + u * kSortBlock);
+    }
 }
 
 // SplitMix64 output function (Steele, Lea & Flood 2014): a bijective 64-bit mixer.
@@ -336,7 +347,7 @@ cudaError_t launch_scan(pic_ctx* c) {
 
 cudaError_t launch_scatter_perm(pic_ctx* c) {
     if (c->np == 0) return cudaSuccess;
-    const unsigned nb = unsigned((c->np + kSortBlock - 1) / kSortBlock);
+    const unsigned nb = unsigned((c->np + 2 * kSortBlock - 1) / (2 * kSortBlock));
     k_scatter_perm<<<nb, kSortBlock, 0, c->stream>>>(bins(c), c->np, c->offsets, c->count, nbins(c), c->perm,
                                                       c->err);
     return cudaGetLastError();
