@@ -241,6 +241,8 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
     dst.id[dest] = id;
 }
 
+constexpr int kPermPerThread = 4;
+
 // The step's sort without moving the particle data: perm[slot] = the index
 // of the particle that goes there (slots as k_scatter assigns them); the tile
 // kernel then reads each particle through perm and writes it in sorted order
@@ -248,9 +250,9 @@ __global__ void __launch_bounds__(kSortBlock) k_scatter(PartBuf src, PartBuf dst
 __global__ void __launch_bounds__(kSortBlock) k_scatter_perm(const int* __restrict__ bin, int64_t np,
                                                              const int* offsets, int* count, int64_t C, int* perm,
                                                              unsigned* err) {
-    // two particles a thread (a block's 2 * kSortBlock consecutive
-    // particles, each half coalesced): both slot atomics are in flight at once
-    constexpr int U = 2;
+    // kPermPerThread particles a thread (a block's consecutive particles in
+    // kPermPerThread coalesced rows): their slot atomics are in flight at once
+    constexpr int U = kPermPerThread;
     const int64_t p0 = (int64_t)blockIdx.x * (U * kSortBlock) + threadIdx.x;
     const int lane = threadIdx.x & 31;
     int k[U], base[U], old[U];
@@ -347,7 +349,7 @@ cudaError_t launch_scan(pic_ctx* c) {
 
 cudaError_t launch_scatter_perm(pic_ctx* c) {
     if (c->np == 0) return cudaSuccess;
-    const unsigned nb = unsigned((c->np + 2 * kSortBlock - 1) / (2 * kSortBlock));
+    const unsigned nb = unsigned((c->np + kPermPerThread * kSortBlock - 1) / (kPermPerThread * kSortBlock));
     k_scatter_perm<<<nb, kSortBlock, 0, c->stream>>>(bins(c), c->np, c->offsets, c->count, nbins(c), c->perm,
                                                       c->err);
     return cudaGetLastError();
