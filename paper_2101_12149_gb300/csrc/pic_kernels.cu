@@ -638,14 +638,21 @@ __device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileW
         const int p0 = w.wbeg + rr * w.run;
         const int len = rr < w.nrun ? min(w.run, w.wend - p0) : 0;
         const int maxlen = __reduce_max_sync(0xffffffffu, len);
-        // the next particle's loads are issued before the current one's work
-        if (rbase != w.rstart && len > 0) load_raw<R>(A, p0, next);
+        // the next particle's loads are issued before the current one's work;
+        // `next` holds this run's first particle (loaded by first_particle or
+        // during the previous run), and the last particle of a run prefetches
+        // the next run's first
+        const int rr_n = rr + w.rstride;
+        const int p0_n = w.wbeg + rr_n * w.run;
+        const bool has_n = rr_n < w.nrun && p0_n < w.wend;
+        if (len == 0 && has_n) load_raw<R>(A, p0_n, next);
         for (int it = 0; it < maxlen; ++it) {
             const int p = p0 + it;
             bool wide = false;
             TileMove<R> mine = TileMove<R>::zero();
             const RawParticle<R> raw = next;
             if (it + 1 < len) load_raw<R>(A, p + 1, next);
+            else if (it + 1 == len && has_n) load_raw<R>(A, p0_n, next);
             if (it < len) {
                 int cell[3];
                 R f0[3], u[3], wq;
