@@ -666,7 +666,12 @@ __device__ __forceinline__ void tile_particles(const StepArgs<R>& A, const TileW
                     const int slot = atomicAdd(A.outn, 1);
                     A.outl[slot] = p;
                 } else {
-                    if (A.perm) A.did[p] = raw.id;
+                    if (A.perm) {
+                        // a sorted-order step writes the whole particle into its
+                        // slot: id and weight here, the rest in store_particle
+                        A.did[p] = raw.id;
+                        A.pa[6][p] = raw.a[6];
+                    }
                     R EB[6];
                     {
                         GatherW<P, R> G;
@@ -992,7 +997,10 @@ __device__ __forceinline__ void outsider_body(const StepArgs<R>& A, const int p)
     RawParticle<R> raw;
     load_raw<R>(A, p, raw);
     decode_particle<R>(A, raw, cell, f0, xg0, u, wq);
-    if (A.perm) A.did[p] = raw.id;
+    if (A.perm) {  // id and weight into the slot (store_particle writes the rest)
+        A.did[p] = raw.id;
+        A.pa[6][p] = raw.a[6];
+    }
     R EB[6];
     {
         GatherW<P, R> G;

@@ -111,6 +111,45 @@ def test_counted_histogram_across_paths(use_stream, sort_every):
     check(4)
 
 
+@pytest.mark.parametrize("precision", [pic.FP64, pic.FP32_MIXED])
+@pytest.mark.parametrize("use_stream", [False, True])
+def test_unequal_weights_through_sorted_steps(precision, use_stream):
+    """Particles of unequal weights through six steps with a sort every step:
+    each sorted-order step moves every particle, weight included, into its
+    slot of the other buffer.  With equal weights a weight left behind would
+    go unnoticed (the slot's old value would be the same)."""
+    from oracle import Oracle
+    n, order, steps = (16, 16, 8), 2, 6
+    parts = inputs.uniform_plasma(51, n, 4, sigma_u=0.3)
+    rng = np.random.default_rng(52)
+    parts["w"] = parts["w"] * (0.25 + 1.5 * rng.random(parts["w"].size))
+    F = np.zeros((9,) + n)
+    F[:6] = inputs.random_fields(53, n, 0.03)[:6]
+    dt = inputs.dt_from_cfl((1.0, 1.0, 1.0), 0.99)
+    s = torch.cuda.Stream() if use_stream else None
+    with pic.Context(n, dt=dt, order=order, precision=precision, stream=s) as c:
+        c.set_fields(F)
+        c.load_particles(-1.0, 1.0, parts)
+        c.step(steps)
+        G = c.get_fields()
+        q = c.get_particles()
+    O = Oracle()
+    g = O.grid(n)
+    ref = {k: v.copy() for k, v in parts.items()}
+    Fr = F.copy()
+    for s_ in range(steps):
+        O.pic_step(g, order, dt, -1.0, 1.0, ref, Fr, 0.0, 0.0, s_ * dt)
+    o = np.argsort(q["id"])
+    assert np.array_equal(np.asarray(q["id"])[o], np.arange(parts["w"].size))
+    w_err = np.abs(np.asarray(q["w"])[o] - parts["w"]).max() / parts["w"].max()
+    if precision == pic.FP64:
+        assert w_err == 0.0
+        assert rel_l2(G[:6], Fr[:6]) < 1e-11 and rel_l2(G[6:], Fr[6:]) < 1e-11
+    else:
+        assert w_err < 1e-7
+        assert rel_l2(G[:6], Fr[:6]) < 1e-5 and rel_l2(G[6:], Fr[6:]) < 1e-4
+
+
 def test_external_drive_fp64():
     c = Case((16, 8, 8), 2, 2, 0.05, 31)
     k = 2 * np.pi / 16
