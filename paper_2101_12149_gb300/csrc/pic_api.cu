@@ -325,13 +325,30 @@ cudaError_t read_live_count(pic_ctx* c) {
 cudaError_t window_shift(pic_ctx* c) { return pic::launch_window_shift(c); }
 cudaError_t inject(pic_ctx* c) { return pic::launch_inject(c); }
 
-// One step with the moving window: tile kernel (particles leaving z get the
-// removed key), Yee, then the window shifts (fields and particles down one
-// cell, front slab filled with plasma) as often as speed * t has passed the
-// next cell, then a sort that also drops the removed particles.  The state
-// after the step is sorted and holds only live particles.
+// One step with the moving window.  Unless the particles are sorted and
+// compact already (after a load or a call's final sort), the step begins
+// with the counting sort as a permutation: the removed particles (last bin)
+// are left out of it, the live count is read back (the step's one wait), and
+// the tile kernel carries only live particles into the sorted buffer.  Then
+// the tile kernel (particles leaving z get the removed key), Yee, and the
+// window shifts (fields and particles down one cell, front slab filled with
+// plasma) as often as speed * t has passed the next cell.  The particles are
+// left unsorted, with the removed ones still in place; finish_window_steps
+// sorts and compacts them once at the end of pic_step.
 pic_status run_window_step(pic_ctx* c) {
-    PIC_CUDA(run_tile_and_fields(c));
+    if (!c->sorted) {
+        PIC_CUDA(run_hist(c));
+        PIC_CUDA(counted(c, "k_scan", 1, pic::launch_scan));
+        PIC_CUDA(counted(c, "k_scatter_perm", 1, pic::launch_scatter_perm));
+        c->count_state = 0;
+        c->cur = 1 - c->cur;
+        PIC_CUDA(read_live_count(c));
+        c->tile_perm = c->np > 0;
+    }
+    const cudaError_t et = run_tile_and_fields(c);
+    c->tile_perm = false;
+    PIC_CUDA(et);
+    c->sorted = false;
     c->step += 1;
     const double t = double(c->step) * c->dt;
     while (c->window_speed > 0.0 && c->window_speed * t >= double(c->shifts + 1) * c->g.d[2]) {
@@ -349,6 +366,15 @@ pic_status run_window_step(pic_ctx* c) {
             c->next_id += total;
         }
     }
+    c->since_sort = 1;
+    return PIC_OK;
+}
+
+// After a call's window steps: one full sort that also drops the removed
+// particles, so that between calls the particles are sorted, compact and
+// only live ones.
+pic_status finish_window_steps(pic_ctx* c) {
+    if (c->sorted) return PIC_OK;
     PIC_CUDA(run_sort(c));
     PIC_CUDA(read_live_count(c));
     c->since_sort = 1;
@@ -916,6 +942,7 @@ pic_status pic_step(pic_ctx* c, int32_t nsteps) {
     if (c->window) {
         for (; left > 0; --left)
             if (pic_status s = run_window_step(c)) return s;
+        if (pic_status s = finish_window_steps(c)) return s;
         c->have_old = false;
         return read_error_word(c);
     }
