@@ -152,12 +152,14 @@ pic_status pic_sort_particles(pic_ctx* ctx, int32_t bin_shift);
  * per tile), Yee update.  Checks the device error word at the end.
  * With a moving window (Sec. 4.2: the domain moves with the beam at c, new
  * plasma enters at the front, particles leaving at the back are removed),
- * each step is: tile kernel, Yee update, then as often as
- * window_speed * t_{n+1} has reached the next cell the window shift (all
- * fields move down one cell along z with a zero front slab, particles move
- * by -dz and those below z = 0 are removed) and the injection of the front
- * slab's plasma (pic_set_window_plasma), then a sort that also drops removed
- * particles; the step waits for the live particle count. */
+ * each step is: a sort that leaves out the particles removed by the step
+ * before (the step waits for the live particle count), tile kernel, Yee
+ * update, then as often as window_speed * t_{n+1} has reached the next cell
+ * the window shift (all fields move down one cell along z with a zero front
+ * slab, particles move by -dz and those below z = 0 are removed) and the
+ * injection of the front slab's plasma (pic_set_window_plasma).  The call
+ * ends with one more sort, so that between calls the particles are sorted
+ * and only live ones remain. */
 pic_status pic_step(pic_ctx* ctx, int32_t nsteps);
 
 /* Plasma injected into each new front slab of a moving-window context:
