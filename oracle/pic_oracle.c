@@ -570,7 +570,11 @@ static void step_impl(const orc_grid* g, int p, double dt, double q, double m, i
         double x0[3] = {x[n], y[n], z[n]};
         double x1[3] = {x[n], y[n], z[n]};
         orc_advance(dt, u, x1);
+#if ORC_MUTANT == 16
+        orc_deposit_esirkepov(g, p, dt, q * w[n > 0 ? n - 1 : n], x0, x1, J); /* another particle's weight */
+#else
         orc_deposit_esirkepov(g, p, dt, q * w[n], x0, x1, J);
+#endif
         x[n] = orc_wrap(x1[0], L[0]);
         y[n] = orc_wrap(x1[1], L[1]);
         z[n] = g->zopen ? x1[2] : orc_wrap(x1[2], L[2]); /* z open: left unwrapped, the caller removes it */

@@ -684,3 +684,52 @@ def pin_filter_open_z(O):
 
 
 ALL_PINS.extend([pin_filter_transfer_function, pin_filter_open_z])
+
+
+def pin_continuity_unequal_weights(O):
+    """Discrete continuity over a full PIC step with unequal particle weights
+    (orders 1-3): the charge density before and after uses each particle's
+    own weight, so a current that took another particle's weight would leave
+    a residual of the order of the weights' spread."""
+    n = (8, 8, 8)
+    g = O.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), 0.99)
+    rng = np.random.default_rng(61)
+    for p in (1, 2, 3):
+        parts = inputs.uniform_plasma(60 + p, n, 2, sigma_u=0.5)
+        parts["w"] = parts["w"] * (0.25 + 1.5 * rng.random(parts["w"].size))
+        F = np.zeros((9,) + n)
+        r0 = O.rho(g, p, -1.0, parts["x"], parts["y"], parts["z"], parts["w"])
+        O.pic_step(g, p, dt, -1.0, 1.0, parts, F)
+        r1 = O.rho(g, p, -1.0, parts["x"], parts["y"], parts["z"], parts["w"])
+        res = r1 - r0 + dt * O.div_edge(g, F[6:9])
+        assert np.max(np.abs(res)) < 1e-13 * np.max(np.abs(r0)), p
+
+
+def pin_current_linear_in_weights(O):
+    """With no fields, the step's current is a sum over particles of w times
+    a weight-free term: scaling every weight by 3 scales J by 3, and the
+    currents of two halves of the particles add up to that of all."""
+    n = (8, 8, 8)
+    g = O.grid(n)
+    dt = inputs.dt_from_cfl((1, 1, 1), 0.99)
+    parts = inputs.uniform_plasma(71, n, 2, sigma_u=0.4)
+    rng = np.random.default_rng(72)
+    parts["w"] = parts["w"] * (0.5 + rng.random(parts["w"].size))
+
+    def current(sel, scale=1.0):
+        q = {k: np.ascontiguousarray(v[sel]) for k, v in parts.items()}
+        q["w"] = q["w"] * scale
+        F = np.zeros((9,) + n)
+        O.pic_step(g, 3, dt, -1.0, 1.0, q, F)
+        return F[6:9]
+
+    every = np.arange(parts["w"].size)
+    J = current(every)
+    tol = 1e-13 * np.abs(J).max()
+    assert np.max(np.abs(current(every, 3.0) - 3.0 * J)) < tol
+    half = parts["w"].size // 2
+    assert np.max(np.abs(current(every[:half]) + current(every[half:]) - J)) < tol
+
+
+ALL_PINS.extend([pin_continuity_unequal_weights, pin_current_linear_in_weights])

@@ -8,8 +8,9 @@ velocity, an energy-conserving gather that keeps order p for one component,
 a Vay pusher without its explicit magnetic half, CKC with the wrong
 transverse weights, a field energy without the cell volume, a kinetic
 energy of gamma m instead of (gamma - 1) m, a charge density without 1/dV, a
-z filter whose compensation pass has the wrong sign.  Every mutant must fail at
-least one pin.
+z filter whose compensation pass has the wrong sign, a deposit that takes the
+previous particle's weight (invisible with equal weights).  Every mutant must
+fail at least one pin.
 """
 import pytest
 
@@ -32,6 +33,7 @@ MUTANTS = {
     13: "kinetic energy gamma m in place of (gamma - 1) m",
     14: "charge density without 1/dV",
     15: "z filter compensation with the wrong sign",
+    16: "deposit with the previous particle's weight",
 }
 
 
